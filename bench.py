@@ -1,0 +1,417 @@
+"""Benchmark of the BSP graph hot path on one GB300 (or N replicas under torchrun).
+
+Workload (default): RMAT scale 25, edge factor 16, (A,B,C) = (0.57, 0.19, 0.19), seeded,
+symmetrised, deduplicated, vertex ids permuted; uint32 weights uniform in [1, 255];
+degree split at T = 2048 (hub / leaf partitions with outbox/inbox). One step is the whole
+hot path on the resident graph: BFS from one seeded source (levels and parents), SSSP
+from the same source, and 20 iterations of FP32 PageRank (damping 0.85). The graph load
+and partition are preprocessing (Section 5: only algorithm time is measured) and are
+reported separately.
+
+value = traversed edges of the step / step time, in GTEPS, with traversed edges counted
+as in Section 5: BFS and SSSP the degree sum of the reached vertices, PageRank m per
+iteration. Per-algorithm rates, the FP64 / FP16 PageRank variants, the roofline of the
+dominant kernel, the CPU oracle baseline and the end-to-end number (host result buffers,
+device-to-host copies inside the timed region) are added to the same JSON line.
+
+`--impl reference` times the CPU oracle (the reference arm of this build) on the same
+workload and prints the same kind of line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS/SSSP GTEPS, PageRank Gedges/s/iter (FP32 vs FP64), % HBM peak, 1×GB300"
+UNIT = "GTEPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=25)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--wmax", type=int, default=255)
+    ap.add_argument("--pr-iters", type=int, default=20)
+    ap.add_argument("--threshold", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_name(a):
+    return (f"rmat{a.scale}-ef{a.edge_factor} bfs+sssp(w1..{a.wmax})+pagerank-fp32x{a.pr_iters}"
+            f" degree-split T={a.threshold}")
+
+
+def make_graph(a):
+    import synth
+    t = time.time()
+    g = synth.rmat(a.scale, a.edge_factor, seed=1)
+    synth.weights(g, a.wmax, seed=3)
+    return g, time.time() - t
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(a):
+    """CPU oracle on the same workload: bounded per-step samples, rank 0 only."""
+    world, rank, _ = dist_setup(a)
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    g, gen_s = make_graph(a)
+    srcs = synth.sources(g, max(a.steps + a.warmup, 1), seed=2)
+    steps, warm = a.steps, a.warmup
+    per_step_budget = max(1.0, 150.0 / max(steps + warm, 1))
+    # A step alternates the oracle's BFS from the step's source and one FP64 PageRank
+    # iteration (Dijkstra on the full graph exceeds the per-step budget and is left out).
+    edges, secs = 0, 0.0
+    for k in range(warm + steps):
+        t = time.perf_counter()
+        if k % 2 == 0:
+            lv, _ = oracle.bfs(g.n, g.offsets, g.cols, int(srcs[k % len(srcs)]),
+                               want_parents=True)
+            e = oracle.traversed(g.n, g.offsets, lv)
+        else:
+            oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=1)
+            e = g.m
+        dt = time.perf_counter() - t
+        if k >= warm:
+            edges += e
+            secs += dt
+    v = edges / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": secs * 1e3 / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+        "data": "synthetic (seeded RMAT, Table 2 parameters)",
+        "config": {"workload": workload_name(a), "n": g.n, "m": g.m,
+                   "sample": "per step: oracle BFS from one source (even steps) or one FP64 "
+                             "PageRank iteration (odd steps) on the full graph",
+                   "generation_s": round(gen_s, 1)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "alternating oracle BFS / one PageRank iteration, "
+                                   "single-threaded C"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "budget_s_per_step": per_step_budget,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, src, budget_s):
+    """Oracle (single-threaded C) on a bounded sample of the step: one BFS from the step's
+    source and one FP64 PageRank iteration; SSSP's Dijkstra is timed only if the sample is
+    still below the budget."""
+    import oracle
+    t = time.perf_counter()
+    lv, _ = oracle.bfs(g.n, g.offsets, g.cols, int(src))
+    tb = time.perf_counter() - t
+    eb = oracle.traversed(g.n, g.offsets, lv)
+    t = time.perf_counter()
+    oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=1)
+    tp = time.perf_counter() - t
+    edges, secs, parts = eb + g.m, tb + tp, "BFS (1 source) + 1 FP64 PageRank iteration"
+    # Dijkstra costs roughly 6x a BFS on these graphs; include it when it fits the budget.
+    if secs + 6 * tb < budget_s:
+        t = time.perf_counter()
+        d = oracle.sssp(g.n, g.offsets, g.cols, g.weights, int(src))
+        ts = time.perf_counter() - t
+        edges += oracle.traversed(g.n, g.offsets, d)
+        secs += ts
+        parts += " + SSSP (Dijkstra, 1 source)"
+    return {"value": edges / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{parts} on the full graph, {secs:.1f} s single-threaded"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    world, rank, local = dist_setup(a)
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import paper_1312_3018_gb300 as G
+    import synth
+
+    hbm_peak, peak_kind = peaks()
+    g, gen_s = make_graph(a)
+    srcs = synth.sources(g, 64, seed=2 + 1000 * rank)  # replicas draw their own sources
+    stream = torch.cuda.current_stream()
+
+    t = time.perf_counter()
+    H = G.graph_load_csr(g.offsets, g.cols, g.weights)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t
+    t = time.perf_counter()
+    info = G.graph_partition(H, "degree", degree_threshold=a.threshold)
+    torch.cuda.synchronize()
+    part_s = time.perf_counter() - t
+
+    n, m = g.n, g.m
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa = torch.empty(n, dtype=torch.int32, device="cuda")
+    dd = torch.empty(n, dtype=torch.int32, device="cuda")
+    rr = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(k, out="device", bufs=None):
+        s = int(srcs[k % len(srcs)])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        if out == "device":
+            _, _, sb = G.bfs(H, s, lv, pa, out="device", timing=True)
+            ev[1].record(stream)
+            _, ss = G.sssp(H, s, dd, out="device", timing=True)
+            ev[2].record(stream)
+            _, sp = G.pagerank(H, max_iter=a.pr_iters, precision="fp32", ranks=rr,
+                               out="device", timing=True)
+        else:
+            hl, hp, hd, hr = bufs
+            _, _, sb = G.bfs(H, s, hl, hp, out="host")
+            ev[1].record(stream)
+            _, ss = G.sssp(H, s, hd, out="host")
+            ev[2].record(stream)
+            _, sp = G.pagerank(H, max_iter=a.pr_iters, precision="fp32", ranks=hr, out="host")
+        ev[3].record(stream)
+        return ev, sb, ss, sp
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(a.warmup):
+        step(k)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    recs = [step(a.warmup + k) for k in range(a.steps)]
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    bfs_ms = sum(e[0].elapsed_time(e[1]) for e, *_ in recs)
+    sssp_ms = sum(e[1].elapsed_time(e[2]) for e, *_ in recs)
+    pr_ms = sum(e[2].elapsed_time(e[3]) for e, *_ in recs)
+    bfs_e = sum(sb["edges_traversed"] for _, sb, _, _ in recs)
+    sssp_e = sum(ss["edges_traversed"] for _, _, ss, _ in recs)
+    pr_e = sum(sp["edges_traversed"] for _, _, _, sp in recs)
+    launches = sum(sb["launches"] + ss["launches"] + sp["launches"] for _, sb, ss, sp in recs)
+    step_edges = (bfs_e + sssp_e + pr_e) / a.steps
+    value = world * step_edges * a.steps / (total_ms / 1e3) / 1e9
+
+    # Kernel-level times from the library's CUDA events on the same stream.
+    pr_compute_ms = sum(sp["ms_compute"] for *_, sp in recs)
+    pr_iters = sum(sp["supersteps"] for *_, sp in recs)
+    sssp_compute_ms = sum(ss["ms_compute"] for _, _, ss, _ in recs)
+    sssp_rounds = sum(ss["supersteps"] for _, _, ss, _ in recs)
+    sssp_insp = sum(ss["edges_inspected"] for _, _, ss, _ in recs)
+    bfs_compute_ms = sum(sb["ms_compute"] for _, sb, _, _ in recs)
+    bfs_insp = sum(sb["edges_inspected"] for _, sb, _, _ in recs)
+    bfs_levels = sum(sb["supersteps"] for _, sb, _, _ in recs)
+
+    # Algorithmic bytes (per launch x launches): PageRank FP32 pull 8m + 20n per iteration;
+    # SSSP 12 B per relaxed edge (id, weight, target distance) + 20 B per active vertex;
+    # BFS 4 B per inspected edge + 16 B per vertex + a bitmap pass per level.
+    pr_bytes = (8 * m + 20 * n) * pr_iters
+    sssp_bytes = 12 * sssp_insp
+    bfs_bytes = 4 * bfs_insp + 16 * n * a.steps + bfs_levels * n // 8
+    kern = {
+        "k_pr_compute<fp32>": (pr_bytes, pr_compute_ms, pr_iters),
+        "k_sssp_relax": (sssp_bytes, sssp_compute_ms, sssp_rounds),
+        "k_bfs_topdown/bottomup": (bfs_bytes, bfs_compute_ms, bfs_levels),
+    }
+    dom = max(kern, key=lambda k: kern[k][1])
+    rl = {}
+    for name, (b, ms, launches_k) in kern.items():
+        ach = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        rl[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+                    "launches": launches_k, "avg_launch_ms": round(ms / max(launches_k, 1), 4),
+                    "peak_kind": peak_kind}
+
+    # FP64 and FP16-stored PageRank rates (same graph, same iteration count).
+    variants = {}
+    for prec in ("fp64", "fp16"):
+        G.pagerank(H, max_iter=a.pr_iters, precision=prec, ranks=rr, out="device")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sp = G.pagerank(H, max_iter=a.pr_iters, precision=prec, ranks=rr, out="device",
+                           timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        per_it = sp["ms_compute"] / a.pr_iters
+        byt = ((12 * m + 32 * n) if prec == "fp64" else (6 * m + 18 * n))
+        variants[prec] = {"gedges_per_s_iter": m * a.pr_iters / (ms / 1e3) / 1e9,
+                          "compute_ms_per_iter": per_it,
+                          "hbm_frac_compute": byt / (per_it / 1e3) / 1e9 / hbm_peak}
+
+    # End to end through the public API with pinned host result buffers.
+    e2e = None
+    if not a.no_e2e:
+        pin = lambda dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
+        bufs = (pin(torch.int32).view(np.uint32), pin(torch.int32).view(np.uint32),
+                pin(torch.int32).view(np.uint32), pin(torch.float64))
+        for k in range(a.warmup):
+            step(k, "host", bufs)
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        erecs = [step(a.warmup + k, "host", bufs) for k in range(a.steps)]
+        s1.record(stream)
+        barrier()
+        ems = s0.elapsed_time(s1)
+        ee = sum(sb["edges_traversed"] + ss["edges_traversed"] + sp["edges_traversed"]
+                 for _, sb, ss, sp in erecs)
+        e2e = {"value": world * ee / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 20 * n,
+               "note": "resident graph; per step the two source ids go in as call arguments "
+                       "and levels, parents, distances (uint32) and ranks (FP64) come back "
+                       "to pinned host memory inside the timed region"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(g, srcs[0], a.cpu_budget_s)
+    nproc = os.cpu_count()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
+        "data": "synthetic (seeded RMAT, Table 2 parameters; weights seeded)",
+        "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
+                   "n": n, "m": m, "partition": {"strategy": "degree", "T": a.threshold,
+                                                  "nv": info["nv"], "ne": info["ne"],
+                                                  "nout": info["nout"]},
+                   "l2": "inputs larger than L2 (edge array 4m bytes >> 129 MB); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "host_cores": nproc},
+        "breakdown": {
+            "bfs_gteps": bfs_e / (bfs_ms / 1e3) / 1e9,
+            "sssp_gteps": sssp_e / (sssp_ms / 1e3) / 1e9,
+            "pagerank_fp32_gedges_per_s_iter": pr_e / (pr_ms / 1e3) / 1e9,
+            "pagerank_fp64_gedges_per_s_iter": variants["fp64"]["gedges_per_s_iter"],
+            "pagerank_fp16_gedges_per_s_iter": variants["fp16"]["gedges_per_s_iter"],
+            "pagerank_fp32_hbm_frac_compute": rl["k_pr_compute<fp32>"]["frac"],
+            "pagerank_fp64_hbm_frac_compute": variants["fp64"]["hbm_frac_compute"],
+            "pagerank_fp16_hbm_frac_compute": variants["fp16"]["hbm_frac_compute"],
+            "ms": {"bfs": bfs_ms / a.steps, "sssp": sssp_ms / a.steps, "pagerank": pr_ms / a.steps},
+            "bfs_levels_per_search": bfs_levels / a.steps,
+            "sssp_rounds_per_search": sssp_rounds / a.steps,
+            "bfs_edges_inspected_per_search": bfs_insp / a.steps,
+            "sssp_edges_relaxed_per_search": sssp_insp / a.steps,
+        },
+        "roofline": dict(rl[dom], kernel=dom),
+        "rooflines": rl,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),
+                         "partition": round(part_s, 3)},
+    }
+    print(json.dumps(line), flush=True)
+    H.free()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * graph.h -- C ABI of the GB300 BSP graph library.
+ *
+ * The library runs the bulk-synchronous superstep of the TOTEM engine (Section 4.1) on one
+ * GPU: a compute phase over each partition's CSR, a communication phase that moves boundary
+ * messages from outbox to inbox buffers (Section 4.3.2), and a termination vote. Breadth-
+ * first search (Section 6.3.2, Figure 11), pull PageRank (Section 7.1, Figure 14) and
+ * Bellman-Ford shortest paths (Section 7.3, Figure 20) run on it.
+ *
+ * Conventions shared by every call:
+ *  - Vertex ids are uint32 in [0, n), n < 2^31 (bit 31 of a partitioned edge marks a
+ *    boundary edge, Section 4.3.1). Edge offsets are int64.
+ *  - INF (GRAPH_INF = 0xFFFFFFFF) marks unreached vertices in levels, parents and distances.
+ *  - Results are written in the caller's global vertex order, into caller-owned arrays of
+ *    length n, in host or device memory as the attribute `out_mem` says. Host output arrays
+ *    should be pinned for full copy speed; any host memory works.
+ *  - Every call returns a graph_status (0 = success, negative = error) and never aborts.
+ *    graph_strerror() names a status; graph_last_error() gives the detail of the most
+ *    recent failure on the calling thread.
+ *  - Work is issued on the stream given at load time (graph_runtime.stream) and the call
+ *    returns after its results are complete. Calls on one handle must not overlap; distinct
+ *    handles are independent. Handles are not thread-safe.
+ */
+#ifndef GB300_GRAPH_H
+#define GB300_GRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct graph graph_t; /* opaque; owns device copies of the graph and workspaces */
+typedef int graph_status;
+
+#define GRAPH_OK 0
+#define GRAPH_EINVAL (-1)   /* bad argument: NULL pointer, id out of range, bad CSR, ... */
+#define GRAPH_ENOMEM (-2)   /* device or pinned-host allocation failed */
+#define GRAPH_ECUDA (-3)    /* a CUDA runtime call failed; see graph_last_error() */
+#define GRAPH_ETIMEOUT (-4) /* a bounded device wait or the superstep cap ran out */
+#define GRAPH_ERANGE (-5)   /* a result does not fit its type (distance >= 2^32 - 1) */
+#define GRAPH_ESTATE (-6)   /* call out of order (e.g. an algorithm before partitioning) */
+
+#define GRAPH_INF 0xFFFFFFFFu
+
+#define GRAPH_MEM_HOST 0
+#define GRAPH_MEM_DEVICE 1
+
+/* Device memory and stream used by a graph handle. alloc/free may be NULL (then the
+ * library uses cudaMalloc/cudaFree). alloc must return memory aligned to at least 256 bytes
+ * or NULL; free receives the pointer and the size that alloc was asked for. stream is a
+ * cudaStream_t (NULL = the legacy default stream). The struct is copied at load time. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* ctx;
+  void* stream;
+} graph_runtime;
+
+/* ---------------------------------------------------------------------------------------
+ * graph_load_csr -- copy a CSR graph into device memory (the graph representation of
+ * Section 4.3.1: V = offsets, E = destination ids).
+ *   n        number of vertices, 0 < n < 2^31
+ *   m        number of directed edge entries (offsets[n] must equal m)
+ *   offsets  int64[n+1], non-decreasing, offsets[0] = 0
+ *   cols     uint32[m], each < n. Undirected graphs store both directions. BFS parents
+ *            and the SSSP certificate assume the stored graph is symmetric; PageRank
+ *            pulls along the stored entries (in-neighbours = stored neighbours).
+ *   weights  uint32[m] edge weights >= 1 for SSSP, or NULL
+ *   mem      GRAPH_MEM_HOST or GRAPH_MEM_DEVICE: where offsets/cols/weights live
+ *   rt       allocator and stream, or NULL for cudaMalloc and the default stream
+ *   out      receives the new handle
+ * The inputs are validated on the device (monotone offsets, ids < n) and copied; the
+ * caller keeps ownership of its arrays. Errors: EINVAL (bad sizes, NULL, invalid CSR),
+ * ENOMEM, ECUDA. The graph starts unpartitioned: call graph_partition before algorithms.
+ * ------------------------------------------------------------------------------------- */
+graph_status graph_load_csr(uint32_t n, int64_t m, const int64_t* offsets,
+                            const uint32_t* cols, const uint32_t* weights, int mem,
+                            const graph_runtime* rt, graph_t** out);
+
+/* Partition strategies (Section 6.2-6.3.1). */
+#define GRAPH_PART_NONE 0     /* one partition: every vertex in partition 1, none in 0 */
+#define GRAPH_PART_DEGREE 1   /* HIGH: partition 0 = vertices with degree >= T (hubs),  \
+                                 partition 1 = the rest (leaves) */
+#define GRAPH_PART_EXPLICIT 2 /* caller-given partition id per vertex (e.g. RAND) */
+
+typedef struct {
+  int strategy;
+  uint32_t degree_threshold; /* DEGREE: T, used when edge_share <= 0 */
+  double edge_share;         /* DEGREE: if > 0, T = largest t such that the vertices of
+                                degree >= t hold at least edge_share * m edge entries */
+  const uint8_t* assignment; /* EXPLICIT: n host bytes, each 0 or 1 */
+} graph_partition_attr;
+
+/* ---------------------------------------------------------------------------------------
+ * graph_partition -- split the vertices into two partitions and build, on the device,
+ * each partition's data structures (Section 4.3.1-4.3.2, Figure 6):
+ *  - local ids 0..|V_p|-1, ordered by degree class (bit length of the degree) descending,
+ *    then by global id; l2g maps local to global ids (used to collect results);
+ *  - CSR per partition, each vertex's local neighbours first (Section 4.3.1), then its
+ *    boundary neighbours, original order within each group;
+ *  - a boundary edge stores 0x80000000 | (index into the partition's outbox);
+ *  - the outbox lists the distinct remote targets in ascending local id of their owner,
+ *    which makes it element-for-element the owner's inbox (messages are reduced at the
+ *    source: one slot per remote vertex, Section 3.4).
+ * Re-partitioning replaces the previous partition. Errors: EINVAL (bad strategy,
+ * assignment values > 1, missing assignment), ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+graph_status graph_partition(graph_t* g, const graph_partition_attr* attr);
+
+typedef struct {
+  uint32_t n;
+  int64_t m;
+  uint32_t threshold;   /* T used by DEGREE (0 otherwise) */
+  uint32_t nv[2];       /* |V_p| */
+  int64_t ne[2];        /* |E_p| */
+  uint32_t nout[2];     /* |V_o| of partition p = |V_i| of the other partition */
+  uint32_t cls_end[2][34]; /* local ids of degree class c are [cls_end[c+1], cls_end[c]) */
+  int64_t bytes_graph;  /* device bytes of the partitioned graph per the space formula of
+                           Section 4.3.3 (offsets, edges, weights, in/outbox vertex ids) */
+} graph_partition_info;
+
+/* Sizes of the current partition. Errors: EINVAL, ESTATE (not partitioned). */
+graph_status graph_get_partition_info(const graph_t* g, graph_partition_info* info);
+
+/* Copies partition p's arrays to host buffers sized from graph_get_partition_info: l2g
+ * [nv], off [nv+1], E [ne], W [ne] (NULL to skip; requires weights), outbox [nout],
+ * g2l [n] ((p << 31) | local id; NULL to skip). Any other pointer may be NULL to skip.
+ * Meant for inspection and tests. Errors: EINVAL, ESTATE, ECUDA. */
+graph_status graph_export_partition(const graph_t* g, int p, uint32_t* l2g, int64_t* off,
+                                    uint32_t* E, uint32_t* W, uint32_t* outbox,
+                                    uint32_t* g2l);
+
+/* Per-call statistics (all optional; pass NULL). Times are CUDA-event times on the
+ * handle's stream, filled when the attribute `timing` is non-zero. */
+typedef struct {
+  int supersteps;          /* BSP rounds executed (BFS levels, SSSP rounds, PR iterations) */
+  int topdown_steps;       /* BFS: rounds run top-down */
+  int bottomup_steps;      /* BFS: rounds run bottom-up */
+  int64_t edges_traversed; /* TEPS numerator (Section 5): BFS/SSSP the degree sum of the
+                              reached vertices; PageRank m * iterations */
+  int64_t edges_inspected; /* edge entries the compute kernels actually read */
+  int64_t messages;        /* outbox entries delivered through the exchange */
+  double residual;         /* PageRank: L1 change of the last iteration (FP64) */
+  double ms_total;         /* whole call, including result copy-out */
+  double ms_compute;       /* compute-phase kernels */
+  double ms_exchange;      /* communication-phase kernels (outbox -> inbox) */
+  int64_t launches;        /* CUDA kernels the call launched */
+} graph_stats;
+
+/* ---------------------------------------------------------------------------------------
+ * bfs -- level-synchronous breadth-first search from `source` (Section 6.3.2, Figure 11;
+ * the Appendix's entry point takes a graph, a source and an output level array).
+ *   levels   n uint32: hop distance from source, INF if unreached (required)
+ *   parents  n uint32: a BFS tree, parent[source] = source, INF if unreached, or NULL.
+ *            Parents are one valid choice among the neighbours one level up.
+ * Each round expands the frontier top-down (push through the visited bitmap, boundary
+ * discoveries reduced in the outbox) or bottom-up (unvisited vertices look for a frontier
+ * neighbour; the owner publishes its frontier to the other partition's ghost bitmap), as
+ * the direction-optimising rule of Beamer et al. selects. Errors: EINVAL (source >= n,
+ * NULL levels), ESTATE (not partitioned), ETIMEOUT (max_supersteps reached), ENOMEM,
+ * ECUDA.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_BFS_AUTO 0      /* direction-optimising */
+#define GRAPH_BFS_TOPDOWN 1   /* top-down every round */
+#define GRAPH_BFS_BOTTOMUP 2  /* bottom-up every round after the first */
+
+typedef struct {
+  int out_mem;        /* GRAPH_MEM_HOST or GRAPH_MEM_DEVICE for levels/parents */
+  int direction;      /* GRAPH_BFS_* */
+  double alpha;       /* top-down -> bottom-up when frontier edges > unexplored edges /
+                         alpha (<= 0: 15) */
+  double beta;        /* bottom-up -> top-down when the frontier shrinks below n / beta
+                         (<= 0: 18) */
+  int max_supersteps; /* <= 0: no cap other than n + 1 */
+  int timing;         /* fill per-phase times in graph_stats */
+} bfs_attr;
+
+graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint32_t* parents,
+                 const bfs_attr* attr, graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
+ * sssp -- single-source shortest paths by Bellman-Ford with an active set (Section 7.3,
+ * Figure 20): each round relaxes the edges of the vertices whose distance improved,
+ * atomic minimum on the target (boundary targets reduce into their outbox slot), and the
+ * exchange applies the outbox minima to the owner. Rounds end when no vertex is active.
+ *   dist   n uint32: shortest distance, INF if unreachable. Requires weights.
+ * Sums saturate below INF; if a true distance would reach 2^32 - 1 the call returns
+ * ERANGE. Errors: EINVAL (source >= n, NULL dist, no weights), ESTATE, ETIMEOUT, ERANGE,
+ * ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int out_mem;
+  int max_supersteps; /* <= 0: no cap other than n + 1 */
+  int timing;
+} sssp_attr;
+
+graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* attr,
+                  graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
+ * pagerank -- pull PageRank (Section 7.1, Figure 14). Each iteration every vertex sums
+ * its neighbours' contributions x[u] = r[u] / deg(u) and sets
+ *     r'[v] = (1 - d)/n + d * (sum + D/n)
+ * where D is the rank held by degree-zero vertices (dangling = 1) or 0 (dangling = 0,
+ * Figure 14 taken literally). Ranks start at 1/n. Boundary contributions are read from
+ * ghost slots the owner publishes in the communication phase (pull direction, Section
+ * 4.3.2). D and the L1 residual sum |r' - r| are reduced in FP64 on the device.
+ * Precision of the stored contributions and of the per-vertex sum:
+ *   GRAPH_PR_FP32  FP32 x, FP32 accumulation, FP32 ranks
+ *   GRAPH_PR_FP64  FP64 throughout
+ *   GRAPH_PR_FP16  x stored as FP16 scaled by n (n*r/deg), FP32 accumulation, FP32 ranks
+ *   ranks   n doubles: the ranks after the last iteration
+ * Runs max_iter iterations, or stops after the first iteration whose residual < tol
+ * (tol <= 0: never). Errors: EINVAL (damping outside [0,1], max_iter < 1, NULL ranks, bad
+ * precision), ESTATE, ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_PR_FP32 0
+#define GRAPH_PR_FP64 1
+#define GRAPH_PR_FP16 2
+
+typedef struct {
+  double damping; /* d, e.g. 0.85 */
+  int max_iter;
+  double tol;
+  int precision;  /* GRAPH_PR_* */
+  int dangling;   /* 1 = spread degree-zero rank uniformly, 0 = drop it */
+  int out_mem;
+  int timing;
+} pagerank_attr;
+
+graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* ranks,
+                      graph_stats* stats);
+
+/* Releases every device and host resource of the handle (NULL is a no-op). Waits for the
+ * handle's stream first. */
+void graph_free(graph_t* g);
+
+/* Static string naming a status. */
+const char* graph_strerror(graph_status s);
+
+/* Detail of the most recent failure on the calling thread ("" if none). */
+const char* graph_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_GRAPH_H */

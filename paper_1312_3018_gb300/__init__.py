@@ -1,0 +1,238 @@
+"""GB300 BSP graph library: Python binding of the C ABI in include/graph.h.
+
+The functions below have the names of the C entry points and only marshal arguments:
+every step (load validation, partitioning, BFS, SSSP, PageRank, exchange, collect) runs in
+the CUDA library. PyTorch supplies device memory (its caching allocator, through the
+allocator hooks of graph_runtime) and the stream. There is no CPU fallback: if the
+compiled library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_INF,
+                   GRAPH_MEM_DEVICE, GRAPH_MEM_HOST, GRAPH_PART_DEGREE, GRAPH_PART_EXPLICIT,
+                   GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
+
+__all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
+           "graph_export_partition", "bfs", "sssp", "pagerank", "graph_free", "Graph",
+           "GraphError", "INF", "library_path"]
+
+INF = GRAPH_INF
+_PREC = {"fp32": GRAPH_PR_FP32, "fp64": GRAPH_PR_FP64, "fp16": GRAPH_PR_FP16}
+_DIR = {"auto": GRAPH_BFS_AUTO, "topdown": GRAPH_BFS_TOPDOWN, "bottomup": GRAPH_BFS_BOTTOMUP}
+
+
+def library_path() -> str:
+    return _lib.lib_path()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device available: this library has no CPU path")
+    return torch
+
+
+def _ptr(a):
+    """Data pointer and memory kind of a numpy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data, GRAPH_MEM_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), (GRAPH_MEM_DEVICE if a.is_cuda else GRAPH_MEM_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+@dataclass
+class Graph:
+    """Owns a graph_t handle and the allocator callbacks it uses."""
+    handle: int
+    n: int
+    m: int
+    stream: int
+    keep: list = field(default_factory=list)
+
+    def free(self):
+        if self.handle:
+            _lib.load().graph_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _torch_runtime(torch, stream):
+    dev = torch.cuda.current_device()
+
+    @_lib.ALLOC_FN
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream)
+        except Exception:
+            return None
+
+    @_lib.FREE_FN
+    def free(ptr, nbytes, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    rt = _lib.graph_runtime(alloc, free, None, stream)
+    return rt, [alloc, free]
+
+
+def graph_load_csr(offsets, cols, weights=None, *, n: int | None = None, stream=None,
+                   allocator: str = "torch") -> Graph:
+    """Copy a CSR graph (int64 offsets[n+1], uint32 cols[m], optional uint32 weights[m])
+    from host numpy arrays or device tensors into the library. allocator: "torch" (the
+    caching allocator) or "cuda" (cudaMalloc inside the library)."""
+    torch = _torch()
+    if isinstance(offsets, np.ndarray):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.uint32)
+        if weights is not None:
+            weights = np.ascontiguousarray(weights, dtype=np.uint32)
+    nn = (len(offsets) - 1) if n is None else n
+    m = int(offsets[-1]) if isinstance(offsets, np.ndarray) else int(offsets[-1].item())
+    po, mem = _ptr(offsets)
+    pc, memc = _ptr(cols)
+    pw, memw = _ptr(weights)
+    if memc != mem or (weights is not None and memw != mem):
+        raise ValueError("offsets, cols and weights must live in the same memory")
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    keep = []
+    if allocator == "torch":
+        rt, keep = _torch_runtime(torch, s)
+    elif allocator == "cuda":
+        rt = _lib.graph_runtime(_lib.ALLOC_FN(), _lib.FREE_FN(), None, s)
+    else:
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    out = C.c_void_p(0)
+    st = _lib.load().graph_load_csr(nn, m, po, pc, pw, mem, C.byref(rt), C.byref(out))
+    _lib.check(st, "graph_load_csr")
+    return Graph(out.value, nn, m, s, keep)
+
+
+def graph_partition(g: Graph, strategy: str = "degree", *, degree_threshold: int = 2048,
+                    edge_share: float = 0.0, assignment=None) -> dict:
+    """strategy: "none" (one partition), "degree" (HIGH: partition 0 = degree >= T; T from
+    degree_threshold, or from edge_share when > 0), "explicit" (uint8 assignment per vertex,
+    e.g. a seeded random split)."""
+    attr = _lib.graph_partition_attr()
+    attr.strategy = {"none": GRAPH_PART_NONE, "degree": GRAPH_PART_DEGREE,
+                     "explicit": GRAPH_PART_EXPLICIT}[strategy]
+    attr.degree_threshold = int(degree_threshold)
+    attr.edge_share = float(edge_share)
+    keep = None
+    if assignment is not None:
+        keep = np.ascontiguousarray(assignment, dtype=np.uint8)
+        attr.assignment = keep.ctypes.data
+    _lib.check(_lib.load().graph_partition(g.handle, C.byref(attr)), "graph_partition")
+    return graph_get_partition_info(g)
+
+
+def graph_get_partition_info(g: Graph) -> dict:
+    info = _lib.graph_partition_info()
+    _lib.check(_lib.load().graph_get_partition_info(g.handle, C.byref(info)),
+               "graph_get_partition_info")
+    return dict(n=info.n, m=info.m, threshold=info.threshold, nv=list(info.nv),
+                ne=list(info.ne), nout=list(info.nout),
+                cls_end=[np.array(list(info.cls_end[p]), dtype=np.uint32) for p in (0, 1)],
+                bytes_graph=info.bytes_graph)
+
+
+def graph_export_partition(g: Graph, p: int, weights: bool = False) -> dict:
+    info = graph_get_partition_info(g)
+    nv, ne, nout = info["nv"][p], info["ne"][p], info["nout"][p]
+    l2g = np.zeros(max(nv, 1), np.uint32)
+    off = np.zeros(nv + 1, np.int64)
+    E = np.zeros(max(ne, 1), np.uint32)
+    W = np.zeros(max(ne, 1), np.uint32) if weights else None
+    ob = np.zeros(max(nout, 1), np.uint32)
+    g2l = np.zeros(g.n, np.uint32)
+    st = _lib.load().graph_export_partition(g.handle, p, l2g.ctypes.data, off.ctypes.data,
+                                            E.ctypes.data,
+                                            None if W is None else W.ctypes.data,
+                                            ob.ctypes.data, g2l.ctypes.data)
+    _lib.check(st, "graph_export_partition")
+    return dict(nv=nv, ne=ne, l2g=l2g[:nv], off=off, E=E[:ne],
+                W=None if W is None else W[:ne], outbox=ob[:nout],
+                cls_end=info["cls_end"][p], g2l=g2l)
+
+
+def _out_u32(torch, n, out, given):
+    if given is not None:
+        return given
+    if out == "device":
+        return torch.empty(n, dtype=torch.int32, device="cuda")
+    return np.empty(n, dtype=np.uint32)
+
+
+def as_numpy_u32(a) -> np.ndarray:
+    if isinstance(a, np.ndarray):
+        return a.view(np.uint32)
+    return a.cpu().numpy().view(np.uint32)
+
+
+def bfs(g: Graph, source: int, levels=None, parents=None, *, want_parents: bool = True,
+        direction: str = "auto", alpha: float = 0.0, beta: float = 0.0, out: str = "device",
+        max_supersteps: int = 0, timing: bool = False):
+    """Levels and parents (uint32, INF unreached) in global vertex order, and stats."""
+    torch = _torch()
+    levels = _out_u32(torch, g.n, out, levels)
+    if want_parents:
+        parents = _out_u32(torch, g.n, out, parents)
+    pl, mem = _ptr(levels)
+    pp, memp = _ptr(parents) if want_parents else (None, mem)
+    if memp != mem:
+        raise ValueError("levels and parents must live in the same memory")
+    attr = _lib.bfs_attr(mem, _DIR[direction], alpha, beta, max_supersteps, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().bfs(g.handle, int(source), pl, pp, C.byref(attr), C.byref(stats))
+    _lib.check(st, "bfs")
+    return levels, (parents if want_parents else None), stats.as_dict()
+
+
+def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_supersteps: int = 0,
+         timing: bool = False):
+    """Shortest distances (uint32, INF unreachable) in global vertex order, and stats."""
+    torch = _torch()
+    dist = _out_u32(torch, g.n, out, dist)
+    pd, mem = _ptr(dist)
+    attr = _lib.sssp_attr(mem, max_supersteps, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().sssp(g.handle, int(source), pd, C.byref(attr), C.byref(stats))
+    _lib.check(st, "sssp")
+    return dist, stats.as_dict()
+
+
+def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float = 0.0,
+             precision: str = "fp32", dangling: bool = True, ranks=None, out: str = "device",
+             timing: bool = False):
+    """FP64 ranks in global vertex order, and stats (residual = last L1 change)."""
+    torch = _torch()
+    if ranks is None:
+        ranks = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"
+                 else np.empty(g.n, dtype=np.float64))
+    pr_, mem = _ptr(ranks)
+    attr = _lib.pagerank_attr(float(damping), int(max_iter), float(tol), _PREC[precision],
+                              int(bool(dangling)), mem, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().pagerank(g.handle, C.byref(attr), pr_, C.byref(stats))
+    _lib.check(st, "pagerank")
+    return ranks, stats.as_dict()
+
+
+def graph_free(g: Graph) -> None:
+    g.free()

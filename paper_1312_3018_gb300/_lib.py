@@ -1,0 +1,137 @@
+"""ctypes declarations mirroring include/graph.h (argument marshalling only).
+
+Loading fails loudly when the compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+GRAPH_OK = 0
+GRAPH_EINVAL = -1
+GRAPH_ENOMEM = -2
+GRAPH_ECUDA = -3
+GRAPH_ETIMEOUT = -4
+GRAPH_ERANGE = -5
+GRAPH_ESTATE = -6
+GRAPH_INF = 0xFFFFFFFF
+GRAPH_MEM_HOST = 0
+GRAPH_MEM_DEVICE = 1
+GRAPH_PART_NONE = 0
+GRAPH_PART_DEGREE = 1
+GRAPH_PART_EXPLICIT = 2
+GRAPH_BFS_AUTO = 0
+GRAPH_BFS_TOPDOWN = 1
+GRAPH_BFS_BOTTOMUP = 2
+GRAPH_PR_FP32 = 0
+GRAPH_PR_FP64 = 1
+GRAPH_PR_FP16 = 2
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class graph_runtime(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
+class graph_partition_attr(C.Structure):
+    _fields_ = [("strategy", C.c_int), ("degree_threshold", C.c_uint32),
+                ("edge_share", C.c_double), ("assignment", C.c_void_p)]
+
+
+class graph_partition_info(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m", C.c_int64), ("threshold", C.c_uint32),
+                ("nv", C.c_uint32 * 2), ("ne", C.c_int64 * 2), ("nout", C.c_uint32 * 2),
+                ("cls_end", (C.c_uint32 * 34) * 2), ("bytes_graph", C.c_int64)]
+
+
+class graph_stats(C.Structure):
+    _fields_ = [("supersteps", C.c_int), ("topdown_steps", C.c_int),
+                ("bottomup_steps", C.c_int), ("edges_traversed", C.c_int64),
+                ("edges_inspected", C.c_int64), ("messages", C.c_int64),
+                ("residual", C.c_double), ("ms_total", C.c_double),
+                ("ms_compute", C.c_double), ("ms_exchange", C.c_double),
+                ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bfs_attr(C.Structure):
+    _fields_ = [("out_mem", C.c_int), ("direction", C.c_int), ("alpha", C.c_double),
+                ("beta", C.c_double), ("max_supersteps", C.c_int), ("timing", C.c_int)]
+
+
+class sssp_attr(C.Structure):
+    _fields_ = [("out_mem", C.c_int), ("max_supersteps", C.c_int), ("timing", C.c_int)]
+
+
+class pagerank_attr(C.Structure):
+    _fields_ = [("damping", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double),
+                ("precision", C.c_int), ("dangling", C.c_int), ("out_mem", C.c_int),
+                ("timing", C.c_int)]
+
+
+# Every symbol include/graph.h declares, with (restype, argtypes).
+_vp, _u32, _i64, _int = C.c_void_p, C.c_uint32, C.c_int64, C.c_int
+SIGNATURES = {
+    "graph_load_csr": (_int, [_u32, _i64, _vp, _vp, _vp, _int, C.POINTER(graph_runtime),
+                              C.POINTER(_vp)]),
+    "graph_partition": (_int, [_vp, C.POINTER(graph_partition_attr)]),
+    "graph_get_partition_info": (_int, [_vp, C.POINTER(graph_partition_info)]),
+    "graph_export_partition": (_int, [_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bfs": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
+    "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
+    "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
+    "graph_free": (None, [_vp]),
+    "graph_strerror": (C.c_char_p, [_int]),
+    "graph_last_error": (C.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """The loaded library. Raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                if build_if_missing:
+                    _build.build()
+                else:
+                    raise RuntimeError(
+                        f"CUDA library {path} is not built; run "
+                        "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class GraphError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.graph_strerror(status).decode()
+        detail = lib.graph_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}): {detail}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != GRAPH_OK:
+        raise GraphError(status, where)

@@ -1,0 +1,534 @@
+// Level-synchronous BFS on the partitioned graph (Section 6.3.2, Figure 11; Appendix).
+//
+// One BSP superstep per level:
+//  - compute: top-down (push): each frontier vertex claims unvisited neighbours in the
+//    visited bitmap and writes level+1 and its parent; a boundary neighbour is claimed in
+//    the outbox's own bitmap instead, so all messages to one remote vertex reduce into one
+//    outbox slot (Section 3.4, the Appendix's get_dst_ptr). Or bottom-up (pull): each
+//    unvisited vertex stops at its first neighbour in the frontier; boundary neighbours
+//    are tested in a ghost bitmap that the owner filled in the communication phase.
+//  - communication: top-down sends the outbox entries claimed this level to the owner
+//    (scatter with min: only an unvisited owner vertex takes the level and parent);
+//    bottom-up publishes the frontier of each partition to the other's ghost bitmap.
+//  - termination: the host reads how many vertices the level discovered; zero ends the
+//    search (every partition voted finished).
+// Frontiers are kept both as bucketed queues (degree-class buckets, for top-down work
+// dispatch) and as bitmaps (for bottom-up tests).
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gg {
+
+struct BfsCounters {
+  uint32_t tail[2][kNBucket];  // next-queue length per partition and bucket
+  uint32_t dirty_tail[2];      // outbox entries claimed this level
+  uint32_t nf;                 // vertices discovered this level
+  uint32_t pad;
+  unsigned long long mf;       // their degree sum
+  unsigned long long inspected;
+  unsigned long long messages;
+};
+
+struct BfsWs {
+  DevBuf level[2], parent[2], visited[2], front[2][2], queue[2][2];
+  DevBuf oseen[2], olevel[2], oparent[2], dirty[2], ghost[2];
+  size_t words[2] = {0, 0}, owords[2] = {0, 0};
+};
+
+void free_bfs(graph* g) {
+  if (!g->bfs) return;
+  BfsWs* w = g->bfs;
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->level[p], &w->parent[p], &w->visited[p], &w->front[p][0],
+                     &w->front[p][1], &w->queue[p][0], &w->queue[p][1], &w->oseen[p],
+                     &w->olevel[p], &w->oparent[p], &w->dirty[p], &w->ghost[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  delete w;
+  g->bfs = nullptr;
+}
+
+namespace {
+
+struct BfsSide {
+  PartView P;
+  uint32_t* level;
+  uint32_t* parent;
+  uint32_t* visited;
+  const uint32_t* front;  // current frontier bitmap
+  uint32_t* next;         // next frontier bitmap
+  const uint32_t* queue;  // current queue (bucketed)
+  uint32_t* nqueue;       // next queue (bucketed)
+  uint32_t* oseen;        // outbox claims
+  uint32_t* olevel;
+  uint32_t* oparent;
+  uint32_t* dirty;        // outbox indices claimed this level
+  uint32_t* ghost;        // frontier bits of the outbox targets (bottom-up)
+};
+
+struct BfsArgs {
+  BfsSide side[2];
+  BfsCounters* ctr;
+  uint32_t L;  // level being expanded
+};
+
+struct LocalCounts {
+  uint32_t nf = 0;
+  unsigned long long mf = 0, insp = 0, msg = 0;
+};
+
+__device__ void flush_counts(LocalCounts c, BfsCounters* ctr) {
+  __shared__ unsigned long long s[4];
+  if (threadIdx.x < 4) s[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long nf = warp_sum((unsigned long long)c.nf), mf = warp_sum(c.mf),
+                     in = warp_sum(c.insp), ms = warp_sum(c.msg);
+  if (lane_id() == 0) {
+    if (nf) atomicAdd(&s[0], nf);
+    if (mf) atomicAdd(&s[1], mf);
+    if (in) atomicAdd(&s[2], in);
+    if (ms) atomicAdd(&s[3], ms);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s[0]) atomicAdd(&ctr->nf, (uint32_t)s[0]);
+    if (s[1]) atomicAdd(&ctr->mf, s[1]);
+    if (s[2]) atomicAdd(&ctr->inspected, s[2]);
+    if (s[3]) atomicAdd(&ctr->messages, s[3]);
+  }
+}
+
+// Top-down edge loop of one vertex (warp-uniform trip count). Edges e, e+stride, ... < t.
+__device__ __forceinline__ void td_edges(const BfsSide& S, int p, uint32_t L, uint32_t vgid,
+                                         int64_t e, int64_t t, int stride, BfsCounters* ctr,
+                                         LocalCounts& c) {
+  while (__any_sync(kFull, e < t)) {
+    bool dis = false, msg = false;
+    uint32_t u = 0, idx = 0;
+    if (e < t) {
+      c.insp++;
+      const uint32_t x = S.P.E[e];
+      if (!(x & kRemote)) {
+        if (bitmap_claim(S.visited, x)) {
+          dis = true;
+          u = x;
+          S.level[x] = L + 1;
+          S.parent[x] = vgid;
+          atomicOr(&S.next[x >> 5], 1u << (x & 31u));
+          c.nf++;
+          c.mf += (unsigned long long)(S.P.off[x + 1] - S.P.off[x]);
+        }
+      } else {
+        idx = x & kIdMask;
+        if (bitmap_claim(S.oseen, idx)) {
+          msg = true;
+          S.olevel[idx] = L + 1;
+          S.oparent[idx] = vgid;
+        }
+      }
+    }
+    warp_append_bucketed(dis, u, dis ? bucket_of(S.P, u) : 0, ctr->tail[p], S.nqueue, S.P);
+    warp_append(msg, idx, &ctr->dirty_tail[p], S.dirty);
+    e += stride;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bfs_topdown(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs A) {
+  const Seg& G = plan.seg[find_seg(plan)];
+  const int p = G.part;
+  const BfsSide& S = A.side[p];
+  const uint32_t rel = blockIdx.x - G.blk0;
+  LocalCounts c;
+  if (G.gshift >= 8) {
+    const uint32_t v = G.items[rel];
+    td_edges(S, p, A.L, S.P.l2g[v], S.P.off[v] + threadIdx.x, S.P.off[v + 1], kThreads, A.ctr,
+             c);
+  } else {
+    const int gs = G.gshift;
+    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+    int64_t s = 0, t = 0;
+    uint32_t vg = 0;
+    if (gi < G.count) {
+      const uint32_t v = G.items[gi];
+      s = S.P.off[v];
+      t = S.P.off[v + 1];
+      vg = S.P.l2g[v];
+    }
+    const int gl = threadIdx.x & ((1 << gs) - 1);
+    td_edges(S, p, A.L, vg, s + gl, t, 1 << gs, A.ctr, c);
+  }
+  flush_counts(c, A.ctr);
+}
+
+// Communication phase after a top-down level: deliver claimed outbox entries of p to the
+// owner partition q = 1 - p (min-scatter through the inbox order; Appendix scatter_inbox_min).
+__global__ void __launch_bounds__(kThreads) k_bfs_exchange(const __grid_constant__ BfsArgs A) {
+  LocalCounts c;
+  const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int p = 0; p < 2; ++p) {
+    const BfsSide& S = A.side[p];
+    const BfsSide& Q = A.side[1 - p];
+    const int q = 1 - p;
+    const uint32_t cnt = *(volatile uint32_t*)&A.ctr->dirty_tail[p];
+    for (uint32_t i0 = warp_global * 32; i0 < cnt; i0 += nwarps * 32) {
+      const uint32_t i = i0 + lane_id();
+      bool dis = false;
+      uint32_t u = 0;
+      if (i < cnt) {
+        const uint32_t idx = S.dirty[i];
+        u = S.P.outbox[idx];
+        c.msg++;
+        if (bitmap_claim(Q.visited, u)) {
+          dis = true;
+          Q.level[u] = S.olevel[idx];
+          Q.parent[u] = S.oparent[idx];
+          atomicOr(&Q.next[u >> 5], 1u << (u & 31u));
+          c.nf++;
+          c.mf += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
+        }
+      }
+      warp_append_bucketed(dis, u, dis ? bucket_of(Q.P, u) : 0, A.ctr->tail[q], Q.nqueue, Q.P);
+    }
+  }
+  flush_counts(c, A.ctr);
+}
+
+// Communication phase before a bottom-up level: ghost bit i of p = frontier bit of
+// outbox target i (pull direction, Section 4.3.2).
+__global__ void k_bfs_publish_frontier(const __grid_constant__ BfsArgs A, uint32_t words0) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int p = w < words0 ? 0 : 1;
+  const uint32_t word = p == 0 ? w : w - words0;
+  const BfsSide& S = A.side[p];
+  const BfsSide& Q = A.side[1 - p];
+  if (word * 32 >= S.P.nout) return;  // warp-uniform
+  const uint32_t i = word * 32 + lane_id();
+  bool bit = false;
+  if (i < S.P.nout) bit = bitmap_test(Q.front, S.P.outbox[i]);
+  const unsigned m = __ballot_sync(kFull, bit);
+  if (lane_id() == 0) S.ghost[word] = m;
+}
+
+// Bottom-up level over every unvisited vertex with edges (dense bucket segments).
+__global__ void __launch_bounds__(kThreads)
+k_bfs_bottomup(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs A) {
+  const Seg& G = plan.seg[find_seg(plan)];
+  const int p = G.part;
+  const BfsSide& S = A.side[p];
+  const BfsSide& Q = A.side[1 - p];
+  const uint32_t rel = blockIdx.x - G.blk0;
+  const int gs = G.gshift;  // <= 5 here
+  const int gsz = 1 << gs;
+  const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+  const int gl = threadIdx.x & (gsz - 1);
+  const unsigned gmask = (gsz == 32) ? kFull : (((1u << gsz) - 1) << (lane_id() & ~(gsz - 1)));
+  LocalCounts c;
+  uint32_t v = 0;
+  int64_t s = 0, t = 0;
+  bool active = false;
+  if (gi < G.count) {
+    v = G.v0 + gi;
+    if (!bitmap_test(S.visited, v)) {
+      active = true;
+      s = S.P.off[v];
+      t = S.P.off[v + 1];
+    }
+  }
+  bool found = false;
+  uint32_t pg = 0;
+  int64_t e = s + gl;
+  while (__any_sync(kFull, active)) {
+    bool hit = false;
+    uint32_t x = 0;
+    if (active && e < t) {
+      c.insp++;
+      x = S.P.E[e];
+      hit = (x & kRemote) ? bitmap_test(S.ghost, x & kIdMask) : bitmap_test(S.front, x);
+    }
+    const unsigned hits = __ballot_sync(kFull, hit) & gmask;
+    if (active) {
+      if (hits) {
+        const int src = __ffs(hits) - 1;
+        const uint32_t xs = __shfl_sync(gmask, x, src);
+        if (gl == 0) {
+          found = true;
+          pg = (xs & kRemote) ? Q.P.l2g[S.P.outbox[xs & kIdMask]] : S.P.l2g[xs];
+        }
+        active = false;
+      } else {
+        e += gsz;
+        if (e - gl >= t) active = false;
+      }
+    }
+  }
+  if (found) {
+    S.level[v] = A.L + 1;
+    S.parent[v] = pg;
+    atomicOr(&S.visited[v >> 5], 1u << (v & 31u));
+    atomicOr(&S.next[v >> 5], 1u << (v & 31u));
+    c.nf++;
+    c.mf += (unsigned long long)(t - s);
+  }
+  warp_append_bucketed(found, v, found ? G.bucket : 0, A.ctr->tail[p], S.nqueue, S.P);
+  flush_counts(c, A.ctr);
+}
+
+__global__ void k_bfs_init(const __grid_constant__ BfsArgs A, const uint32_t* g2l,
+                           uint32_t source, uint32_t* queue0, uint32_t* queue1) {
+  const uint32_t gl = g2l[source];
+  const int p = gl >> 31;
+  const uint32_t lid = gl & kIdMask;
+  const BfsSide& S = A.side[p];
+  S.level[lid] = 0;
+  S.parent[lid] = source;
+  S.visited[lid >> 5] |= 1u << (lid & 31u);
+  ((uint32_t*)S.front)[lid >> 5] |= 1u << (lid & 31u);
+  const int b = bucket_of(S.P, lid);
+  A.ctr->nf = 1;
+  A.ctr->mf = (unsigned long long)(S.P.off[lid + 1] - S.P.off[lid]);
+  if (b < kNBucket) {
+    (p == 0 ? queue0 : queue1)[S.P.bstart[b]] = lid;
+    A.ctr->tail[p][b] = 1;
+  }
+}
+
+__global__ void k_bfs_collect(const __grid_constant__ BfsArgs A, uint32_t nv0, uint32_t n,
+                              uint32_t* levels, uint32_t* parents) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = i < nv0 ? 0 : 1;
+  const uint32_t lid = p == 0 ? i : i - nv0;
+  const BfsSide& S = A.side[p];
+  const uint32_t gid = S.P.l2g[lid];
+  levels[gid] = S.level[lid];
+  if (parents) parents[gid] = S.parent[lid];
+}
+
+graph_status ensure_ws(graph* g) {
+  if (g->bfs) return GRAPH_OK;
+  BfsWs* w = new BfsWs();
+  g->bfs = w;
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    w->words[p] = (P.nv + 31) / 32;
+    w->owords[p] = (P.nout + 31) / 32;
+    const size_t nv = P.nv, words = w->words[p], owords = w->owords[p];
+    GG_TRY(dalloc(g, w->level[p], 4 * nv));
+    GG_TRY(dalloc(g, w->parent[p], 4 * nv));
+    GG_TRY(dalloc(g, w->visited[p], 4 * words));
+    GG_TRY(dalloc(g, w->front[p][0], 4 * words));
+    GG_TRY(dalloc(g, w->front[p][1], 4 * words));
+    GG_TRY(dalloc(g, w->queue[p][0], 4 * nv));
+    GG_TRY(dalloc(g, w->queue[p][1], 4 * nv));
+    GG_TRY(dalloc(g, w->oseen[p], 4 * owords));
+    GG_TRY(dalloc(g, w->olevel[p], 4 * (size_t)P.nout));
+    GG_TRY(dalloc(g, w->oparent[p], 4 * (size_t)P.nout));
+    GG_TRY(dalloc(g, w->dirty[p], 4 * (size_t)P.nout));
+    GG_TRY(dalloc(g, w->ghost[p], 4 * owords));
+  }
+  if (g->counters.bytes < sizeof(BfsCounters) || !g->counters.p) {
+    dfree(g, g->counters);
+    GG_TRY(dalloc(g, g->counters, 1024));
+  }
+  return ensure_host_counters(g, 1024);
+}
+
+BfsArgs make_args(graph* g, int cur, uint32_t L) {
+  BfsWs* w = g->bfs;
+  BfsArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int p = 0; p < 2; ++p) {
+    BfsSide& S = A.side[p];
+    S.P = g->part[p].view();
+    S.level = (uint32_t*)w->level[p].p;
+    S.parent = (uint32_t*)w->parent[p].p;
+    S.visited = (uint32_t*)w->visited[p].p;
+    S.front = (const uint32_t*)w->front[p][cur].p;
+    S.next = (uint32_t*)w->front[p][1 - cur].p;
+    S.queue = (const uint32_t*)w->queue[p][cur].p;
+    S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
+    S.oseen = (uint32_t*)w->oseen[p].p;
+    S.olevel = (uint32_t*)w->olevel[p].p;
+    S.oparent = (uint32_t*)w->oparent[p].p;
+    S.dirty = (uint32_t*)w->dirty[p].p;
+    S.ghost = (uint32_t*)w->ghost[p].p;
+  }
+  A.ctr = (BfsCounters*)g->counters.p;
+  A.L = L;
+  return A;
+}
+
+}  // namespace
+}  // namespace gg
+
+using namespace gg;
+
+extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint32_t* parents,
+                            const bfs_attr* attr, graph_stats* stats) {
+  if (!g || !levels) {
+    set_error("graph or levels is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (source >= g->n) {
+    set_error("source %u >= n %u", source, g->n);
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before bfs");
+    return GRAPH_ESTATE;
+  }
+  bfs_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) {
+    set_error("bad out_mem");
+    return GRAPH_EINVAL;
+  }
+  const double alpha = at.alpha > 0 ? at.alpha : 15.0;
+  const double beta = at.beta > 0 ? at.beta : 18.0;
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  GG_TRY(ensure_ws(g));
+  BfsWs* w = g->bfs;
+  cudaStream_t st = g->stream;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  // Reset state.
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->level[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->parent[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->visited[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->front[p][0].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->oseen[p].p, 0, 4 * w->owords[p], st));
+  }
+  GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(BfsCounters), st));
+  int cur = 0;
+  {
+    BfsArgs A = make_args(g, cur, 0);
+    k_bfs_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
+                                (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p);
+    GG_CUDA(cudaGetLastError());
+  }
+  BfsCounters* hc = (BfsCounters*)g->host_counters;
+  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(BfsCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
+  int64_t traversed = 0, inspected = 0, messages = 0, explored = 0, launches = 1;
+  int td_steps = 0, bu_steps = 0;
+  bool bottom_up = false;
+  uint32_t nf_prev = 0;
+  int64_t L = 0;
+  for (;; ++L) {
+    BfsCounters c = *hc;
+    if (c.nf == 0) break;
+    if (L >= cap) {
+      set_error("bfs reached the superstep cap (%lld)", (long long)cap);
+      timer.finish(nullptr);
+      return GRAPH_ETIMEOUT;
+    }
+    traversed += (int64_t)c.mf;
+    // Direction choice (Beamer et al.): edges out of the frontier vs edges left unexplored.
+    const int64_t unexplored = g->m - explored - (int64_t)c.mf;
+    if (at.direction == GRAPH_BFS_TOPDOWN) {
+      bottom_up = false;
+    } else if (at.direction == GRAPH_BFS_BOTTOMUP) {
+      bottom_up = L > 0;
+    } else if (!bottom_up) {
+      bottom_up = L > 0 && (double)c.mf > (double)unexplored / alpha;
+    } else {
+      bottom_up = !((double)c.nf < (double)g->n / beta && c.nf < nf_prev);
+    }
+    explored += (int64_t)c.mf;
+    nf_prev = c.nf;
+    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(BfsCounters), st));
+    for (int p = 0; p < 2; ++p)
+      GG_CUDA(cudaMemsetAsync(w->front[p][1 - cur].p, 0, 4 * w->words[p], st));
+    BfsArgs A = make_args(g, cur, (uint32_t)L);
+    timer.mark(2);
+    if (!bottom_up) {
+      Plan pl;
+      memset(&pl, 0, sizeof(pl));
+      const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+      for (int p = 0; p < 2; ++p) {
+        const PartView V = g->part[p].view();
+        for (int b = 0; b < kNBucket; ++b)
+          plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
+                   gsh[b], b);
+      }
+      if (pl.nblocks) k_bfs_topdown<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      k_bfs_exchange<<<152 * 4, kThreads, 0, st>>>(A);
+      launches += 1 + (pl.nblocks ? 1 : 0);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      td_steps++;
+    } else {
+      const uint32_t words0 = (uint32_t)((g->part[0].nout + 31) / 32);
+      const uint32_t words1 = (uint32_t)((g->part[1].nout + 31) / 32);
+      const uint64_t tw = (uint64_t)words0 + words1;
+      if (tw) k_bfs_publish_frontier<<<grid_for(tw * 32, 256), 256, 0, st>>>(A, words0);
+      launches += tw ? 1 : 0;
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      Plan pl;
+      memset(&pl, 0, sizeof(pl));
+      const int gsh[kNBucket] = {5, 5, kSubShift, 0};
+      for (int p = 0; p < 2; ++p) {
+        const PartView V = g->part[p].view();
+        for (int b = 0; b < kNBucket; ++b)
+          plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+      }
+      if (pl.nblocks) k_bfs_bottomup<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+      launches += pl.nblocks ? 1 : 0;
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      bu_steps++;
+    }
+    GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(BfsCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
+    messages += (int64_t)hc->messages;
+    cur = 1 - cur;
+  }
+  // Collect (local -> global order).
+  graph_status s = GRAPH_OK;
+  uint32_t* dl = levels;
+  uint32_t* dp = parents;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 8ull * g->n));
+    dl = (uint32_t*)g->stage.p;
+    dp = parents ? dl + g->n : nullptr;
+  }
+  {
+    BfsArgs A = make_args(g, cur, 0);
+    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, dl, dp);
+    launches++;
+    GG_CUDA(cudaGetLastError());
+  }
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
+    if (parents) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
+  }
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)L;
+    stats->topdown_steps = td_steps;
+    stats->bottomup_steps = bu_steps;
+    stats->edges_traversed = traversed;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+  }
+  timer.finish(stats);
+  return s;
+}
