@@ -32,7 +32,10 @@ constexpr int kClassHub = 12;
 constexpr int kClassWarp = 6;
 constexpr int kClassSub = 3;
 constexpr int kSubShift = 2;                // 4 lanes
-constexpr int kHubChunk = 4096;             // edges per CTA for dense hub work
+constexpr int kHubChunk = 2048;             // edges per hub chunk (dense work)
+constexpr int kTileE = 2048;                // max edges staged per dense tile
+constexpr int kTileV = 1024;                // max vertices per dense tile
+constexpr int kLeafEdges = 1024;            // class-c tile holds kLeafEdges >> (c-1) vertices
 
 // ------------------------------------------------------------------------------------
 // Device views (passed by value to kernels)

@@ -558,7 +558,8 @@ graph_status build_partition(graph* g, int mode, uint32_t T, const uint8_t* expl
   for (int p = 0; p < 2; ++p) {
     STEP(dalloc(g, NP[p].l2g, sizeof(uint32_t) * (size_t)NP[p].nv));
     STEP(dalloc(g, deg[p], sizeof(int64_t) * ((size_t)NP[p].nv + 1)));
-    STEP(dalloc(g, NP[p].off, sizeof(int64_t) * ((size_t)NP[p].nv + 1)));
+    // +2 entries: bulk copies of offset slices read whole 16-byte granules
+    STEP(dalloc(g, NP[p].off, sizeof(int64_t) * ((size_t)NP[p].nv + 3)));
     STEP(dalloc(g, nloc[p], sizeof(uint32_t) * (size_t)NP[p].nv));
     STEP(dalloc(g, mark[p], (size_t)NP[p].nv + 1));
     STEP(dalloc(g, oidx[p], sizeof(uint32_t) * ((size_t)NP[p].nv + 1)));

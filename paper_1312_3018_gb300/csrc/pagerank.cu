@@ -6,17 +6,29 @@
 //    only messages move, the vertex-id arrays are symmetric).
 //  - compute: every vertex sums the contributions of its neighbours (local ones from x,
 //    boundary ones from the ghost slots) and sets r' = (1-d)/n + d (sum + D/n), then its
-//    own contribution x' = r'/deg. Hub vertices (degree >= 2048) are split into chunks of
-//    4096 edges, one CTA each; the chunk's edge ids are staged into shared memory by a bulk
-//    (TMA engine) copy, the CTA sums its gathers, and the last CTA of a vertex adds the
-//    chunk sums in chunk order and updates the vertex. Other vertices use one warp, four
-//    lanes or one lane each, by degree class.
-//  - reduction: FP64 block partials of the L1 residual and of the rank on degree-zero
-//    vertices are summed in a fixed order by one CTA, which also forms the next
-//    iteration's constant term.
+//    own contribution x' = r'/deg.
+//  - reduction: per-block partial sums of the L1 residual; the last block to finish adds
+//    them in block order in FP64 and forms the next iteration's constant term (no extra
+//    launch).
+//
+// Work items (one CTA each): hub chunks (degree >= 2048; kHubChunk edges; the last chunk
+// of a hub adds the chunk sums in chunk order), class tiles (kLeafEdges >> (c-1) vertices
+// of degree class c, so at most kTileE edges; one lane, a lane group or a warp per
+// vertex), and tiles of degree-zero vertices. A CTA stages its item's edge ids and offsets
+// into shared memory with bulk copies (TMA engine) completing on an mbarrier, issues all of
+// its gathers before consuming any, then reduces per vertex from shared memory.
+//
+// Degree-zero vertices: their neighbour sum is empty, so each of them holds exactly the
+// iteration's constant term. Their share of the dangling mass D and of the residual is
+// therefore (count x constant) and (count x |change of the constant|), formed in FP64 by
+// the last block; no per-vertex FP64 work is done (this GPU's FP64 rate is far below its
+// FP32 rate).
+//
 // Precision variants: FP32 contributions and sums; FP64 throughout; FP16 contributions
 // scaled by n (x = n r/deg keeps them away from FP16's subnormal range) with FP32 sums.
 #include <string.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -27,7 +39,7 @@ struct PrWs {
   size_t esize = 0;  // bytes per stored contribution
   size_t rsize = 0;  // bytes per stored rank
   DevBuf r[2], x[2][2], ghost[2], hubsum[2], ticket[2];
-  DevBuf partials, scal, resid;
+  DevBuf partials, scal, resid, done;
   uint32_t nblocks = 0;
   int max_iter = 0;
 };
@@ -43,13 +55,15 @@ void free_pr(graph* g) {
   dfree(g, w->partials);
   dfree(g, w->scal);
   dfree(g, w->resid);
+  dfree(g, w->done);
   delete w;
   g->pr = nullptr;
 }
 
 namespace {
 
-// Scalars on the device: [0] constant term (1-d)/n + d D/n, [1] D, [2] last residual.
+constexpr int kPerThread = kTileE / kThreads;  // gathers a thread issues per tile
+
 struct PrSide {
   PartView P;
   void* r;
@@ -63,12 +77,19 @@ struct PrSide {
   const uint32_t* hub_chunk0;
 };
 
+// Device scalars (doubles): [0] constant term of this iteration, (1-d)/n + d D/n;
+// [1] D; [2] last residual; [3] rank of degree-zero vertices before this iteration;
+// [4] the constant term rounded to FP32 (stored as a float in the first half).
 struct PrArgs {
   PrSide side[2];
   double* scal;
-  double2* partials;  // per block: (residual, dangling)
-  double damping;
-  double n;
+  float* partials;    // per block residual partial (FP32; FP64 mode: double, see below)
+  double* partials64;
+  double* resid;      // residual history
+  uint32_t* done;     // blocks finished this iteration
+  double damping, n;
+  float damping_f, n_f, d_over_n_f;
+  double nzero;       // number of degree-zero vertices
   int* err;
 };
 
@@ -99,138 +120,308 @@ using PrecF32 = Prec<float, float, float, false>;
 using PrecF64 = Prec<double, double, double, false>;
 using PrecF16 = Prec<__half, float, float, true>;
 
-template <class PR>
-__device__ __forceinline__ typename PR::AT gather(const PrSide& S, uint32_t x) {
-  const typename PR::XT* base =
-      (x & kRemote) ? (const typename PR::XT*)S.ghost : (const typename PR::XT*)S.x;
-  return (typename PR::AT)XConv<typename PR::XT>::load(base + (x & kIdMask));
-}
+template <class AT> struct Consts;
+template <> struct Consts<float> {
+  __device__ static float base(const PrArgs& A) { return ((const float*)(A.scal + 4))[0]; }
+  __device__ static float d(const PrArgs& A) { return A.damping_f; }
+  __device__ static float n(const PrArgs& A) { return A.n_f; }
+  __device__ static float d_over_n(const PrArgs& A) { return A.d_over_n_f; }
+};
+template <> struct Consts<double> {
+  __device__ static double base(const PrArgs& A) { return A.scal[0]; }
+  __device__ static double d(const PrArgs& A) { return A.damping; }
+  __device__ static double n(const PrArgs& A) { return A.n; }
+  __device__ static double d_over_n(const PrArgs& A) { return A.damping / A.n; }
+};
 
-// Vertex update from its neighbour sum; returns (|r' - r|, dangling share) in FP64.
+// Update of a vertex with degree deg > 0 from its neighbour sum and its previous rank ro;
+// returns |r' - r|.
 template <class PR>
-__device__ __forceinline__ double2 update_vertex(const PrSide& S, const PrArgs& A, uint32_t v,
-                                                 typename PR::AT sum, int64_t deg) {
+__device__ __forceinline__ typename PR::AT update_vertex(const PrSide& S, const PrArgs& A,
+                                                         uint32_t v, typename PR::AT sum,
+                                                         int deg, typename PR::AT ro) {
   using AT = typename PR::AT;
   using RT = typename PR::RT;
-  const AT base = (AT)A.scal[0];
-  const AT d = (AT)A.damping;
-  AT rn;
-  if (PR::SCALED) rn = base + (d / (AT)A.n) * sum;
-  else rn = base + d * sum;
-  RT* r = (RT*)S.r;
-  const AT ro = (AT)r[v];
-  r[v] = (RT)rn;
+  using C = Consts<AT>;
+  const AT rn = PR::SCALED ? C::base(A) + C::d_over_n(A) * sum : C::base(A) + C::d(A) * sum;
+  ((RT*)S.r)[v] = (RT)rn;
   typename PR::XT* xn = (typename PR::XT*)S.xn;
-  if (deg > 0) {
-    if (PR::SCALED) XConv<typename PR::XT>::store(xn + v, (rn * (AT)A.n) / (AT)deg);
-    else XConv<typename PR::XT>::store(xn + v, rn / (AT)deg);
-  } else {
-    XConv<typename PR::XT>::store(xn + v, (AT)0);
-  }
-  const AT diff = rn > ro ? rn - ro : ro - rn;
-  return make_double2((double)diff, deg == 0 ? (double)rn : 0.0);
+  if (PR::SCALED) XConv<typename PR::XT>::store(xn + v, (rn * C::n(A)) / (AT)deg);
+  else XConv<typename PR::XT>::store(xn + v, rn / (AT)deg);
+  return rn > ro ? rn - ro : ro - rn;
 }
 
-__device__ void block_partial(double2 acc, double2* out) {
-  __shared__ double sr[kThreads / 32], sd[kThreads / 32];
-  acc.x = warp_sum(acc.x);
-  acc.y = warp_sum(acc.y);
-  const int w = threadIdx.x >> 5;
-  if (lane_id() == 0) {
-    sr[w] = acc.x;
-    sd[w] = acc.y;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int i = 0; i < kThreads / 32; ++i) {
-      a += sr[i];
-      b += sd[i];
+// ---------------------------------------------------------------------------------------
+// Work items of one iteration (see the file comment).
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxRange = 28;
+enum { kItemHub = 0, kItemLeaf = 1, kItemZero = 2 };
+
+struct PrRange {
+  uint32_t item0;  // first item index of the range
+  uint32_t first;  // first chunk (hub) or first vertex (leaf, zero)
+  uint32_t end;    // end chunk or end vertex
+  uint32_t per;    // vertices per tile (leaf, zero)
+  uint8_t kind, part, gshift, pad;
+};
+
+struct PrPlan {
+  PrRange r[kMaxRange];
+  int nr;
+  uint32_t nitems;
+};
+
+struct Desc {
+  int64_t e0, e1;     // edge range (hub, leaf)
+  uint32_t v0, v1;    // vertex range (leaf, zero) or hub vertex in v0
+  uint32_t chunk;     // hub chunk index
+  uint32_t eshift;    // e0 - start of the staged granule
+  uint32_t oshift;    // v0 - start of the staged offsets
+  uint32_t rshift;    // v0 - start of the staged ranks
+  uint8_t kind, part, gshift, pad;
+};
+
+__device__ __forceinline__ int find_range(const PrPlan& P, uint32_t item) {
+  int lo = 0;
+  #pragma unroll 1
+  for (int i = 1; i < P.nr; ++i)
+    if (item >= P.r[i].item0) lo = i;
+  return lo;
+}
+
+// Thread 0: describe `item` and start the bulk copies of its edge ids (and offsets, for
+// class tiles) into shared memory; `bar` completes when the bytes have landed.
+template <class RT>
+__device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc& d,
+                           uint32_t* sE, int64_t* sOff, RT* sR, uint64_t* bar) {
+  const PrRange& R = P.r[find_range(P, item)];
+  const PrSide& S = A.side[R.part];
+  d.kind = R.kind;
+  d.part = R.part;
+  d.gshift = R.gshift;
+  d.pad = 0;
+  d.eshift = d.oshift = d.rshift = 0;
+  d.chunk = 0;
+  const uint32_t j = item - R.item0;
+  if (R.kind == kItemHub) {
+    d.chunk = R.first + j;
+    d.v0 = S.chunk_vertex[d.chunk];
+    d.v1 = d.v0 + 1;
+    d.e0 = S.chunk_first[d.chunk];
+    d.e1 = min(d.e0 + (int64_t)kHubChunk, S.P.off[d.v0 + 1]);
+  } else {
+    d.v0 = R.first + j * R.per;
+    d.v1 = min(d.v0 + R.per, R.end);
+    d.e0 = d.e1 = 0;
+    if (R.kind == kItemLeaf) {
+      d.e0 = S.P.off[d.v0];
+      d.e1 = S.P.off[d.v1];
     }
-    out[blockIdx.x] = make_double2(a, b);
   }
+  uint32_t ebytes = 0, obytes = 0, rbytes = 0, o0 = 0, q0 = 0;
+  int64_t a0 = 0;
+  if (R.kind != kItemZero) {
+    a0 = d.e0 & ~(int64_t)3;
+    const int64_t a1 = (d.e1 + 3) & ~(int64_t)3;
+    d.eshift = (uint32_t)(d.e0 - a0);
+    ebytes = (uint32_t)((a1 - a0) * 4);
+  }
+  if (R.kind == kItemLeaf) {
+    o0 = d.v0 & ~1u;
+    const uint32_t o1 = (d.v1 + 2) & ~1u;
+    d.oshift = d.v0 - o0;
+    obytes = (o1 - o0) * 8;
+    // previous ranks of the tile's vertices, in whole 16-byte granules
+    constexpr uint32_t g = 16 / sizeof(RT);
+    q0 = d.v0 & ~(g - 1);
+    const uint32_t q1 = (d.v1 + g - 1) & ~(g - 1);
+    d.rshift = d.v0 - q0;
+    rbytes = (q1 - q0) * (uint32_t)sizeof(RT);
+  }
+  mbar_expect_tx(bar, ebytes + obytes + rbytes);
+  if (ebytes) bulk_g2s(sE, S.P.E + a0, ebytes, bar);
+  if (obytes) bulk_g2s(sOff, S.P.off + o0, obytes, bar);
+  if (rbytes) bulk_g2s(sR, (const RT*)S.r + q0, rbytes, bar);
+}
+
+template <class PR>
+__device__ __forceinline__ typename PR::AT gather(const PrSide& S, uint32_t e) {
+  using XT = typename PR::XT;
+  const XT* base = (e & kRemote) ? (const XT*)S.ghost : (const XT*)S.x;
+  return (typename PR::AT)XConv<XT>::load(base + (e & kIdMask));
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  if (lane_id() == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = 0;
+  #pragma unroll
+  for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// Values gathered for a class tile: in place over the staged edge ids when the
+// accumulator is 4 bytes wide, else in a separate buffer.
+template <class PR>
+__host__ __device__ constexpr size_t vals_bytes() {
+  return sizeof(typename PR::AT) == 4 ? 0 : sizeof(typename PR::AT) * kTileE;
+}
+template <class PR>
+__host__ __device__ constexpr size_t ranks_offset() {
+  return 4 * (kTileE + 8) + 8 * (kTileV + 4) + vals_bytes<PR>();
+}
+template <class PR>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return ranks_offset<PR>() + sizeof(typename PR::RT) * (kTileV + 8);
 }
 
 template <class PR>
 __global__ void __launch_bounds__(kThreads)
-k_pr_compute(const __grid_constant__ Plan plan, const __grid_constant__ PrArgs A) {
+k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs A, int iter,
+             int dangling) {
   using AT = typename PR::AT;
-  const Seg& G = plan.seg[find_seg(plan)];
-  const PrSide& S = A.side[G.part];
-  const uint32_t rel = blockIdx.x - G.blk0;
-  double2 acc = make_double2(0.0, 0.0);
-  if (G.gshift >= 8) {
-    // One hub chunk per CTA.
-    __shared__ alignas(16) uint32_t sE[kHubChunk + 8];
-    __shared__ uint64_t bar;
-    __shared__ AT wsum[kThreads / 32];
-    __shared__ int last;
-    const uint32_t k = G.v0 + rel;  // chunk index
-    const uint32_t v = S.chunk_vertex[k];
-    const int64_t e0 = S.chunk_first[k];
-    const int64_t vend = S.P.off[v + 1];
-    const int64_t e1 = min(e0 + (int64_t)kHubChunk, vend);
-    const int64_t a0 = e0 & ~(int64_t)3, a1 = (e1 + 3) & ~(int64_t)3;
-    if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t bytes = (uint32_t)((a1 - a0) * 4);
-      mbar_expect_tx(&bar, bytes);
-      bulk_g2s(sE, S.P.E + a0, bytes, &bar);
-    }
-    const bool ok = mbar_wait_bounded(&bar, 0, A.err);
-    AT s = 0;
-    if (ok) {
-      const uint32_t* src = sE + (e0 - a0);
-      const int cnt = (int)(e1 - e0);
-      #pragma unroll 4
-      for (int i = threadIdx.x; i < cnt; i += kThreads) s += gather<PR>(S, src[i]);
-    }
-    s = warp_sum(s);
-    if (lane_id() == 0) wsum[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      AT t = 0;
-      for (int i = 0; i < kThreads / 32; ++i) t += wsum[i];
-      ((AT*)S.hubsum)[k] = t;
-      __threadfence();
-      const int64_t deg = vend - S.P.off[v];
-      const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
-      const uint32_t tk = atomicAdd(&S.ticket[v], 1u);
-      last = (tk == nch - 1);
-      if (last) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* sE = reinterpret_cast<uint32_t*>(smem);
+  int64_t* sOff = reinterpret_cast<int64_t*>(smem + 4 * (kTileE + 8));
+  AT* vals = vals_bytes<PR>() ? reinterpret_cast<AT*>(smem + 4 * (kTileE + 8) + 8 * (kTileV + 4))
+                              : reinterpret_cast<AT*>(smem);
+  using RT = typename PR::RT;
+  RT* sR = reinterpret_cast<RT*>(smem + ranks_offset<PR>());
+  __shared__ uint64_t bar;
+  __shared__ Desc dsh;
+  __shared__ AT red[kThreads / 32];
+  __shared__ int flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    issue_item<RT>(plan, A, blockIdx.x, dsh, sE, sOff, sR, &bar);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, A.err);
+  AT res = 0;
+  if (__syncthreads_and(ok)) {
+    const Desc d = dsh;
+    const PrSide& S = A.side[d.part];
+    if (d.kind == kItemHub) {
+      const int cnt = (int)(d.e1 - d.e0);
+      const uint32_t* src = sE + d.eshift;
+      uint32_t e[kPerThread];
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        e[u] = i < cnt ? src[i] : 0u;
+      }
+      AT s = 0;
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u)
+        if (threadIdx.x + u * kThreads < cnt) s += gather<PR>(S, e[u]);
+      const AT t = block_sum<AT>(s, red);
+      if (threadIdx.x == 0) {
+        ((AT*)S.hubsum)[d.chunk] = t;
         __threadfence();
-        const uint32_t c0 = S.hub_chunk0[v];
-        AT sum = 0;
-        for (uint32_t c = 0; c < nch; ++c) sum += __ldcg((const AT*)S.hubsum + c0 + c);
-        acc = update_vertex<PR>(S, A, v, sum, deg);
-        S.ticket[v] = 0;
+        const int64_t deg = S.P.off[d.v0 + 1] - S.P.off[d.v0];
+        const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
+        flag = (atomicAdd(&S.ticket[d.v0], 1u) == nch - 1) ? (int)nch : 0;
+      }
+      __syncthreads();
+      const int nch = flag;
+      if (nch) {
+        // Last chunk of this hub: add the chunk sums in chunk order.
+        __threadfence();
+        const uint32_t c0 = S.hub_chunk0[d.v0];
+        AT p = 0;
+        for (int c = threadIdx.x; c < nch; c += kThreads) p += __ldcg((const AT*)S.hubsum + c0 + c);
+        const AT sum = block_sum<AT>(p, red);
+        if (threadIdx.x == 0) {
+          res += update_vertex<PR>(S, A, d.v0, sum, (int)(S.P.off[d.v0 + 1] - S.P.off[d.v0]),
+                                   (AT)((const RT*)S.r)[d.v0]);
+          S.ticket[d.v0] = 0;
+        }
+      }
+    } else if (d.kind == kItemLeaf) {
+      const int cnt = (int)(d.e1 - d.e0);
+      const uint32_t* src = sE + d.eshift;
+      uint32_t e[kPerThread];
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        e[u] = i < cnt ? src[i] : 0u;
+      }
+      AT v[kPerThread];
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u)
+        v[u] = (threadIdx.x + u * kThreads < cnt) ? gather<PR>(S, e[u]) : (AT)0;
+      // In-place values overwrite only the edge ids this thread itself read.
+      const int shift = vals_bytes<PR>() == 0 ? (int)d.eshift : 0;
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        if (i < cnt) vals[shift + i] = v[u];
+      }
+      __syncthreads();
+      const AT* vv = vals + shift;
+      const int gs = d.gshift;
+      const int gl = lane_id() & ((1 << gs) - 1);
+      const int per_warp = 32 >> gs;
+      const int nvt = (int)(d.v1 - d.v0);
+      const int64_t* so = sOff + d.oshift;
+      for (int jb = (threadIdx.x >> 5) * per_warp; jb < nvt; jb += (kThreads / 32) * per_warp) {
+        const int j = jb + (int)(lane_id() >> gs);
+        AT s = 0;
+        int es = 0, ee = 0;
+        if (j < nvt) {
+          es = (int)(so[j] - d.e0);
+          ee = (int)(so[j + 1] - d.e0);
+          for (int i = es + gl; i < ee; i += (1 << gs)) s += vv[i];
+        }
+        s = group_sum(s, gs);
+        if (j < nvt && gl == 0)
+          res += update_vertex<PR>(S, A, d.v0 + j, s, ee - es, (AT)sR[d.rshift + j]);
+      }
+    } else {
+      // Degree-zero vertices: the rank is the constant term, the contribution zero.
+      const typename PR::RT b = (typename PR::RT)Consts<AT>::base(A);
+      for (uint32_t v = d.v0 + threadIdx.x; v < d.v1; v += kThreads) {
+        ((typename PR::RT*)S.r)[v] = b;
+        XConv<typename PR::XT>::store((typename PR::XT*)S.xn + v, (AT)0);
       }
     }
-    block_partial(acc, A.partials);
-    return;
   }
-  const int gs = G.gshift;
-  const int gsz = 1 << gs;
-  const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-  const int gl = threadIdx.x & (gsz - 1);
-  AT s = 0;
-  int64_t deg = 0;
-  uint32_t v = 0;
-  const bool valid = gi < G.count;
-  if (valid) {
-    v = G.v0 + gi;
-    const int64_t b = S.P.off[v], t = S.P.off[v + 1];
-    deg = t - b;
-    #pragma unroll 4
-    for (int64_t e = b + gl; e < t; e += gsz) s += gather<PR>(S, S.P.E[e]);
+  // Residual partial of this block; the last block adds all of them in block order.
+  res = block_sum<AT>(res, red);
+  if (threadIdx.x == 0) {
+    if (sizeof(AT) == 4) A.partials[blockIdx.x] = (float)res;
+    else A.partials64[blockIdx.x] = (double)res;
+    __threadfence();
+    flag = (atomicAdd(A.done, 1u) == gridDim.x - 1);
   }
-  s = group_sum(s, gs);
-  if (valid && gl == 0) acc = update_vertex<PR>(S, A, v, s, deg);
-  block_partial(acc, A.partials);
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+  __shared__ double rd[kThreads / 32];
+  double a = 0;
+  if (sizeof(AT) == 4) {
+    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) a += (double)__ldcg(A.partials + i);
+  } else {
+    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) a += __ldcg(A.partials64 + i);
+  }
+  a = block_sum<double>(a, rd);
+  if (threadIdx.x == 0) {
+    const double zr = A.scal[0];  // rank every degree-zero vertex now holds
+    a += A.nzero * fabs(zr - A.scal[3]);
+    const double D = dangling ? A.nzero * zr : 0.0;
+    const double base = (1.0 - A.damping) / A.n + A.damping * D / A.n;
+    A.scal[1] = D;
+    A.scal[2] = a;
+    A.scal[3] = zr;
+    A.scal[0] = base;
+    ((float*)(A.scal + 4))[0] = (float)base;
+    A.resid[iter] = a;
+    *A.done = 0;
+  }
 }
 
 // Communication phase: ghost_p[i] = x_q[outbox_p[i]].
@@ -246,38 +437,6 @@ __global__ void k_pr_publish(const __grid_constant__ PrArgs A) {
   ((XT*)S.ghost)[j] = ((const XT*)Q.x)[S.P.outbox[j]];
 }
 
-// Fixed-order FP64 sum of the block partials; sets the next constant term.
-__global__ void __launch_bounds__(1024) k_pr_finalize(double2* partials, uint32_t nblocks,
-                                                      double* scal, double* resid_hist,
-                                                      int iter, double damping, double n,
-                                                      int dangling) {
-  __shared__ double sr[32], sd[32];
-  double a = 0, b = 0;
-  for (uint32_t i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    a += partials[i].x;
-    b += partials[i].y;
-  }
-  a = warp_sum(a);
-  b = warp_sum(b);
-  if (lane_id() == 0) {
-    sr[threadIdx.x >> 5] = a;
-    sd[threadIdx.x >> 5] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double ra = 0, da = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      ra += sr[i];
-      da += sd[i];
-    }
-    const double D = dangling ? da : 0.0;
-    scal[1] = D;
-    scal[0] = (1.0 - damping) / n + damping * D / n;
-    scal[2] = ra;
-    resid_hist[iter] = ra;
-  }
-}
-
 template <class PR>
 __global__ void k_pr_init(const __grid_constant__ PrArgs A, uint32_t nv0, uint32_t ntot) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,7 +447,7 @@ __global__ void k_pr_init(const __grid_constant__ PrArgs A, uint32_t nv0, uint32
   using AT = typename PR::AT;
   const AT r0 = (AT)(1.0 / A.n);
   ((typename PR::RT*)S.r)[v] = (typename PR::RT)r0;
-  const int64_t deg = S.P.off[v + 1] - S.P.off[v];
+  const int deg = (int)(S.P.off[v + 1] - S.P.off[v]);
   typename PR::XT* x = (typename PR::XT*)S.x;
   if (deg > 0) {
     if (PR::SCALED) XConv<typename PR::XT>::store(x + v, (AT)1 / (AT)deg);
@@ -309,25 +468,53 @@ __global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t nv0, uin
   out[S.P.l2g[v]] = (double)((const RT*)S.r)[v];
 }
 
-Plan make_plan(graph* g) {
-  Plan pl;
+PrPlan make_plan(graph* g) {
+  PrPlan pl;
   memset(&pl, 0, sizeof(pl));
+  auto add = [&](uint32_t count_items, uint32_t first, uint32_t end, uint32_t per, int kind,
+                 int part, int gshift) {
+    if (count_items == 0) return;
+    PrRange& R = pl.r[pl.nr++];
+    R.item0 = pl.nitems;
+    R.first = first;
+    R.end = end;
+    R.per = per;
+    R.kind = (uint8_t)kind;
+    R.part = (uint8_t)part;
+    R.gshift = (uint8_t)gshift;
+    pl.nitems += count_items;
+  };
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
-    const PartView V = P.view();
-    plan_add(pl, nullptr, 0, P.nchunk, p, 8, 0);
-    plan_add(pl, nullptr, V.bstart[1], V.bstart[2] - V.bstart[1], p, 5, 1);
-    plan_add(pl, nullptr, V.bstart[2], V.bstart[3] - V.bstart[2], p, kSubShift, 2);
-    plan_add(pl, nullptr, V.bstart[3], P.nv - V.bstart[3], p, 0, 3);  // incl. degree zero
+    add(P.nchunk, 0, P.nchunk, 1, kItemHub, p, 8);
+    for (int c = kClassHub - 1; c >= 1; --c) {
+      const uint32_t v0 = P.cls_end[c + 1], v1 = P.cls_end[c];
+      const uint32_t per = std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1));
+      add((v1 - v0 + per - 1) / per, v0, v1, per, kItemLeaf, p, std::min(c - 1, 5));
+    }
+    const uint32_t z0 = P.cls_end[1], z1 = P.nv;
+    add((z1 - z0 + kTileV - 1) / kTileV, z0, z1, kTileV, kItemZero, p, 0);
   }
   return pl;
+}
+
+template <class PR>
+graph_status prepare_kernel() {
+  static bool done = false;
+  if (!done) {
+    GG_CUDA(cudaFuncSetAttribute(k_pr_compute<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<PR>()));
+    done = true;
+  }
+  return GRAPH_OK;
 }
 
 graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
   const size_t es = prec == GRAPH_PR_FP64 ? 8 : (prec == GRAPH_PR_FP16 ? 2 : 4);
   const size_t rs = prec == GRAPH_PR_FP64 ? 8 : 4;
   const size_t as = prec == GRAPH_PR_FP64 ? 8 : 4;
-  if (g->pr && (g->pr->prec != prec || g->pr->max_iter < max_iter)) free_pr(g);
+  if (g->pr && (g->pr->prec != prec || g->pr->max_iter < max_iter || g->pr->nblocks < nblocks))
+    free_pr(g);
   if (g->pr) return GRAPH_OK;
   PrWs* w = new PrWs();
   g->pr = w;
@@ -338,17 +525,17 @@ graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
   w->nblocks = nblocks;
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
-    GG_TRY(dalloc(g, w->r[p], rs * P.nv));
+    GG_TRY(dalloc(g, w->r[p], rs * ((size_t)P.nv + 8)));  // bulk copies read 16-B granules
     GG_TRY(dalloc(g, w->x[p][0], es * P.nv));
     GG_TRY(dalloc(g, w->x[p][1], es * P.nv));
     GG_TRY(dalloc(g, w->ghost[p], es * P.nout));
     GG_TRY(dalloc(g, w->hubsum[p], as * P.nchunk));
     GG_TRY(dalloc(g, w->ticket[p], 4ull * P.nhub));
-    GG_CUDA(cudaMemsetAsync(w->ticket[p].p, 0, 4ull * P.nhub, g->stream));
   }
-  GG_TRY(dalloc(g, w->partials, sizeof(double2) * (size_t)(nblocks + 1)));
+  GG_TRY(dalloc(g, w->partials, as * (size_t)(nblocks + 1)));
   GG_TRY(dalloc(g, w->scal, 8 * sizeof(double)));
   GG_TRY(dalloc(g, w->resid, sizeof(double) * (size_t)(max_iter + 1)));
+  GG_TRY(dalloc(g, w->done, sizeof(uint32_t)));
   return GRAPH_OK;
 }
 
@@ -356,6 +543,7 @@ PrArgs make_args(graph* g, int cur, double damping) {
   PrWs* w = g->pr;
   PrArgs A;
   memset(&A, 0, sizeof(A));
+  uint64_t zero = 0;
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
     PrSide& S = A.side[p];
@@ -369,11 +557,19 @@ PrArgs make_args(graph* g, int cur, double damping) {
     S.chunk_vertex = (const uint32_t*)P.chunk_vertex.p;
     S.chunk_first = (const int64_t*)P.chunk_first.p;
     S.hub_chunk0 = (const uint32_t*)P.hub_chunk0.p;
+    zero += P.nv - P.cls_end[1];
   }
   A.scal = (double*)w->scal.p;
-  A.partials = (double2*)w->partials.p;
+  A.partials = (float*)w->partials.p;
+  A.partials64 = (double*)w->partials.p;
+  A.resid = (double*)w->resid.p;
+  A.done = (uint32_t*)w->done.p;
   A.damping = damping;
   A.n = (double)g->n;
+  A.damping_f = (float)damping;
+  A.n_f = (float)g->n;
+  A.d_over_n_f = (float)(damping / (double)g->n);
+  A.nzero = (double)zero;
   A.err = (int*)g->err.p;
   return A;
 }
@@ -381,30 +577,33 @@ PrArgs make_args(graph* g, int cur, double damping) {
 template <class PR>
 graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* stats) {
   cudaStream_t st = g->stream;
-  Plan pl = make_plan(g);
-  GG_TRY(ensure_ws(g, at.precision, at.max_iter, pl.nblocks));
+  const PrPlan pl = make_plan(g);
+  GG_TRY(prepare_kernel<PR>());
+  GG_TRY(ensure_ws(g, at.precision, at.max_iter, std::max<uint32_t>(pl.nitems, 1)));
   PrWs* w = g->pr;
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
   const uint32_t nv0 = g->part[0].nv;
   int cur = 0;
+  for (int p = 0; p < 2; ++p)
+    GG_CUDA(cudaMemsetAsync(w->ticket[p].p, 0, 4ull * g->part[p].nhub, st));
+  GG_CUDA(cudaMemsetAsync(w->done.p, 0, sizeof(uint32_t), st));
   {
     PrArgs A = make_args(g, cur, at.damping);
     k_pr_init<PR><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n);
     GG_CUDA(cudaGetLastError());
-    // D_0 = (number of degree-zero vertices) / n
-    uint64_t zero = 0;
-    for (int p = 0; p < 2; ++p) zero += g->part[p].nv - g->part[p].cls_end[1];
-    double h[3];
-    const double D0 = at.dangling ? (double)zero / (double)g->n : 0.0;
-    h[0] = (1.0 - at.damping) / (double)g->n + at.damping * D0 / (double)g->n;
-    h[1] = D0;
-    h[2] = 0;
+    // D_0 = (number of degree-zero vertices) / n; degree-zero vertices start at 1/n.
+    const double D0 = at.dangling ? A.nzero / (double)g->n : 0.0;
+    const double base = (1.0 - at.damping) / (double)g->n + at.damping * D0 / (double)g->n;
+    double h[5] = {base, D0, 0.0, 1.0 / (double)g->n, 0.0};
+    const float bf = (float)base;
+    memcpy(&h[4], &bf, sizeof(float));
     GG_CUDA(cudaMemcpyAsync(w->scal.p, h, sizeof(h), cudaMemcpyHostToDevice, st));
     GG_CUDA(cudaStreamSynchronize(st));
   }
   const uint32_t nout = g->part[0].nout + g->part[1].nout;
+  const size_t smem = smem_bytes<PR>();
   int it = 0;
   int64_t launches = 1;
   double last_res = 0;
@@ -413,12 +612,9 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     timer.mark(2);
     if (nout) k_pr_publish<typename PR::XT><<<grid_for(nout, 256), 256, 0, st>>>(A);
     timer.mark(1);
-    if (pl.nblocks) k_pr_compute<PR><<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+    if (pl.nitems) k_pr_compute<PR><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling);
     timer.mark(0);
-    k_pr_finalize<<<1, 1024, 0, st>>>(A.partials, pl.nblocks, A.scal, (double*)w->resid.p, it,
-                                      at.damping, (double)g->n, at.dangling);
-    timer.mark(2);
-    launches += 1 + (nout ? 1 : 0) + (pl.nblocks ? 1 : 0);
+    launches += (nout ? 1 : 0) + (pl.nitems ? 1 : 0);
     GG_CUDA(cudaGetLastError());
     cur = 1 - cur;
     ++it;
@@ -436,8 +632,8 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   {
     PrArgs A = make_args(g, cur, at.damping);
     k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, out);
-    launches++;
     GG_CUDA(cudaGetLastError());
+    launches++;
   }
   if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(&last_res, (double*)w->scal.p + 2, 8, cudaMemcpyDeviceToHost, st));
