@@ -233,6 +233,36 @@ typedef struct {
 graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* ranks,
                       graph_stats* stats);
 
+/* ---------------------------------------------------------------------------------------
+ * bfs_csr_noalloc -- breadth-first search for callers that cannot allocate device memory.
+ * The paper has no counterpart: this entry point exists for code that must not call
+ * cudaMalloc at search time (host callbacks and driver hooks where allocation is forbidden
+ * or could deadlock, allocators frozen after start-up, services with a fixed device-memory
+ * budget). It allocates nothing: no cudaMalloc, cudaFree or allocating library call. Its
+ * scratch (visited bitmap, two frontier queues, counters) lives in one fixed device array
+ * of about 16.3 MB that every GPU loading this library holds until the process exits.
+ *   n        number of vertices, 1 <= n <= GRAPH_NOALLOC_MAX_VERTICES (larger n: EINVAL)
+ *   m        number of edge entries
+ *   offsets  DEVICE int64[n+1], cols DEVICE uint32[m]: the caller's CSR, read in place
+ *            and checked first (monotone offsets, offsets[n] = m, ids < n; else EINVAL)
+ *   source   start vertex (< n)
+ *   levels   DEVICE uint32[n]: hop distance, GRAPH_INF if unreached (required)
+ *   parents  DEVICE uint32[n]: a BFS tree (parents[source] = source), or NULL
+ *   stream   cudaStream_t for all work (NULL = legacy default stream); the call returns
+ *            after the results are complete
+ * Search is level-synchronous and top-down on the unpartitioned graph; levels equal those
+ * of bfs(). The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current, so make the first call before any
+ * stream capture. Every call shares the scratch array and clears what must start at zero;
+ * calls that overlap on the GPU race on it and must not be issued concurrently.
+ * Errors: EINVAL, ETIMEOUT (more than n levels), ECUDA.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_NOALLOC_MAX_VERTICES (1u << 21)
+
+graph_status bfs_csr_noalloc(uint32_t n, int64_t m, const int64_t* offsets,
+                             const uint32_t* cols, uint32_t source, uint32_t* levels,
+                             uint32_t* parents, void* stream);
+
 /* Releases every device and host resource of the handle (NULL is a no-op). Waits for the
  * handle's stream first. */
 void graph_free(graph_t* g);

@@ -19,7 +19,8 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "sssp", "pagerank", "graph_free", "Graph",
+           "graph_export_partition", "bfs", "sssp", "pagerank", "bfs_csr_noalloc",
+           "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
 INF = GRAPH_INF
@@ -232,6 +233,30 @@ def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float 
     st = _lib.load().pagerank(g.handle, C.byref(attr), pr_, C.byref(stats))
     _lib.check(st, "pagerank")
     return ranks, stats.as_dict()
+
+
+def bfs_csr_noalloc(offsets, cols, source: int, levels=None, parents=None, *, stream=None,
+                    want_parents: bool = True):
+    """Allocation-free BFS on a CSR already in device memory (torch CUDA tensors: int64
+    offsets[n+1], 32-bit cols[m]). For callers that cannot allocate device memory when they
+    search: the library keeps its scratch in one fixed device array of about 16.3 MB and
+    allocates nothing; pass preallocated `levels`/`parents` (int32 CUDA tensors of length n)
+    to keep this wrapper allocation-free as well. n is limited to 2^21 vertices. Calls share
+    the scratch array and must not overlap on the GPU; the first call on a device should come
+    before any stream capture."""
+    torch = _torch()
+    n = offsets.numel() - 1
+    m = cols.numel()
+    if levels is None:
+        levels = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    if want_parents and parents is None:
+        parents = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    st = _lib.load().bfs_csr_noalloc(n, m, offsets.data_ptr(), cols.data_ptr(), int(source),
+                                     levels.data_ptr(),
+                                     parents.data_ptr() if want_parents else None, s)
+    _lib.check(st, "bfs_csr_noalloc")
+    return levels, (parents if want_parents else None)
 
 
 def graph_free(g: Graph) -> None:
