@@ -11,12 +11,13 @@
 //    them in block order in FP64 and forms the next iteration's constant term (no extra
 //    launch).
 //
-// Work items (one CTA each): hub chunks (degree >= 2048; kHubChunk edges; the last chunk
-// of a hub adds the chunk sums in chunk order), class tiles (kLeafEdges >> (c-1) vertices
-// of degree class c, so at most kTileE edges; one lane, a lane group or a warp per
-// vertex), and tiles of degree-zero vertices. A CTA stages its item's edge ids and offsets
-// into shared memory with bulk copies (TMA engine) completing on an mbarrier, issues all of
-// its gathers before consuming any, then reduces per vertex from shared memory.
+// Work items (one CTA each): hub vertices (degree >= 2048; the CTA walks the adjacency in
+// chunks of kHubChunk edges, two chunks in flight: the bulk copy of chunk c+2 is issued as
+// soon as chunk c has been gathered), class tiles (kLeafEdges >> (c-1) vertices of degree
+// class c, so at most kTileE edges; one lane, a lane group or a warp per vertex), and
+// tiles of degree-zero vertices. A CTA stages its item's edge ids, offsets and previous
+// ranks into shared memory with bulk copies (TMA engine) completing on an mbarrier, issues
+// all of its gathers before consuming any, then reduces per vertex from shared memory.
 //
 // Degree-zero vertices: their neighbour sum is empty, so each of them holds exactly the
 // iteration's constant term. Their share of the dangling mass D and of the residual is
@@ -38,7 +39,7 @@ struct PrWs {
   int prec = -1;
   size_t esize = 0;  // bytes per stored contribution
   size_t rsize = 0;  // bytes per stored rank
-  DevBuf r[2], x[2][2], ghost[2], hubsum[2], ticket[2];
+  DevBuf r[2], x[2][2], ghost[2];
   DevBuf partials, scal, resid, done;
   uint32_t nblocks = 0;
   int max_iter = 0;
@@ -48,8 +49,7 @@ void free_pr(graph* g) {
   if (!g->pr) return;
   PrWs* w = g->pr;
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->r[p], &w->x[p][0], &w->x[p][1], &w->ghost[p], &w->hubsum[p],
-                     &w->ticket[p]};
+    DevBuf* all[] = {&w->r[p], &w->x[p][0], &w->x[p][1], &w->ghost[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
   dfree(g, w->partials);
@@ -70,11 +70,6 @@ struct PrSide {
   const void* x;      // contributions of this iteration
   void* xn;           // contributions of the next iteration
   void* ghost;        // contributions of the outbox targets
-  void* hubsum;       // per hub chunk partial sum (accumulator type)
-  uint32_t* ticket;   // per hub vertex chunk counter
-  const uint32_t* chunk_vertex;
-  const int64_t* chunk_first;
-  const uint32_t* hub_chunk0;
 };
 
 // Device scalars (doubles): [0] constant term of this iteration, (1-d)/n + d D/n;
@@ -159,8 +154,8 @@ enum { kItemHub = 0, kItemLeaf = 1, kItemZero = 2 };
 
 struct PrRange {
   uint32_t item0;  // first item index of the range
-  uint32_t first;  // first chunk (hub) or first vertex (leaf, zero)
-  uint32_t end;    // end chunk or end vertex
+  uint32_t first;  // first vertex
+  uint32_t end;    // end vertex
   uint32_t per;    // vertices per tile (leaf, zero)
   uint8_t kind, part, gshift, pad;
 };
@@ -173,8 +168,7 @@ struct PrPlan {
 
 struct Desc {
   int64_t e0, e1;     // edge range (hub, leaf)
-  uint32_t v0, v1;    // vertex range (leaf, zero) or hub vertex in v0
-  uint32_t chunk;     // hub chunk index
+  uint32_t v0, v1;    // vertex range (one vertex for a hub)
   uint32_t eshift;    // e0 - start of the staged granule
   uint32_t oshift;    // v0 - start of the staged offsets
   uint32_t rshift;    // v0 - start of the staged ranks
@@ -201,14 +195,12 @@ __device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc
   d.gshift = R.gshift;
   d.pad = 0;
   d.eshift = d.oshift = d.rshift = 0;
-  d.chunk = 0;
   const uint32_t j = item - R.item0;
   if (R.kind == kItemHub) {
-    d.chunk = R.first + j;
-    d.v0 = S.chunk_vertex[d.chunk];
+    d.v0 = R.first + j;
     d.v1 = d.v0 + 1;
-    d.e0 = S.chunk_first[d.chunk];
-    d.e1 = min(d.e0 + (int64_t)kHubChunk, S.P.off[d.v0 + 1]);
+    d.e0 = S.P.off[d.v0];
+    d.e1 = S.P.off[d.v0 + 1];
   } else {
     d.v0 = R.first + j * R.per;
     d.v1 = min(d.v0 + R.per, R.end);
@@ -221,8 +213,10 @@ __device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc
   uint32_t ebytes = 0, obytes = 0, rbytes = 0, o0 = 0, q0 = 0;
   int64_t a0 = 0;
   if (R.kind != kItemZero) {
+    // hubs: the first chunk only; the kernel streams the rest
+    const int64_t e1 = R.kind == kItemHub ? min(d.e1, d.e0 + (int64_t)kHubChunk) : d.e1;
     a0 = d.e0 & ~(int64_t)3;
-    const int64_t a1 = (d.e1 + 3) & ~(int64_t)3;
+    const int64_t a1 = (e1 + 3) & ~(int64_t)3;
     d.eshift = (uint32_t)(d.e0 - a0);
     ebytes = (uint32_t)((a1 - a0) * 4);
   }
@@ -242,6 +236,16 @@ __device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc
   if (ebytes) bulk_g2s(sE, S.P.E + a0, ebytes, bar);
   if (obytes) bulk_g2s(sOff, S.P.off + o0, obytes, bar);
   if (rbytes) bulk_g2s(sR, (const RT*)S.r + q0, rbytes, bar);
+}
+
+// Bulk copy of hub chunk c of the adjacency [e0, e1) into buf (16-byte granules).
+__device__ __forceinline__ void issue_chunk(const uint32_t* E, int64_t e0, int64_t e1, int c,
+                                            uint32_t* buf, uint64_t* bar) {
+  const int64_t cs = e0 + (int64_t)c * kHubChunk, ce = min(cs + (int64_t)kHubChunk, e1);
+  const int64_t a0 = cs & ~(int64_t)3, a1 = (ce + 3) & ~(int64_t)3;
+  const uint32_t bytes = (uint32_t)((a1 - a0) * 4);
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s(buf, E + a0, bytes, bar);
 }
 
 template <class PR>
@@ -290,14 +294,17 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
                               : reinterpret_cast<AT*>(smem);
   using RT = typename PR::RT;
   RT* sR = reinterpret_cast<RT*>(smem + ranks_offset<PR>());
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar, bar2;
   __shared__ Desc dsh;
   __shared__ AT red[kThreads / 32];
   __shared__ int flag;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
+    mbar_init(&bar2, 1);
     fence_mbar_init();
     issue_item<RT>(plan, A, blockIdx.x, dsh, sE, sOff, sR, &bar);
+    if (dsh.kind == kItemHub && dsh.e1 - dsh.e0 > kHubChunk)
+      issue_chunk(A.side[dsh.part].P.E, dsh.e0, dsh.e1, 1, reinterpret_cast<uint32_t*>(sOff), &bar2);
   }
   __syncthreads();
   const bool ok = mbar_wait_bounded(&bar, 0, A.err);
@@ -306,41 +313,36 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
     const Desc d = dsh;
     const PrSide& S = A.side[d.part];
     if (d.kind == kItemHub) {
-      const int cnt = (int)(d.e1 - d.e0);
-      const uint32_t* src = sE + d.eshift;
-      uint32_t e[kPerThread];
-      #pragma unroll
-      for (int u = 0; u < kPerThread; ++u) {
-        const int i = threadIdx.x + u * kThreads;
-        e[u] = i < cnt ? src[i] : 0u;
-      }
+      // Stream the hub's adjacency: chunk c sits in buffer c & 1 (edge-id stage or the
+      // offset stage reused), completing on bar / bar2 in alternating phases.
+      const int nch = (int)((d.e1 - d.e0 + kHubChunk - 1) / kHubChunk);
+      uint32_t* buf[2] = {sE, reinterpret_cast<uint32_t*>(sOff)};
       AT s = 0;
-      #pragma unroll
-      for (int u = 0; u < kPerThread; ++u)
-        if (threadIdx.x + u * kThreads < cnt) s += gather<PR>(S, e[u]);
-      const AT t = block_sum<AT>(s, red);
-      if (threadIdx.x == 0) {
-        ((AT*)S.hubsum)[d.chunk] = t;
-        __threadfence();
-        const int64_t deg = S.P.off[d.v0 + 1] - S.P.off[d.v0];
-        const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
-        flag = (atomicAdd(&S.ticket[d.v0], 1u) == nch - 1) ? (int)nch : 0;
-      }
-      __syncthreads();
-      const int nch = flag;
-      if (nch) {
-        // Last chunk of this hub: add the chunk sums in chunk order.
-        __threadfence();
-        const uint32_t c0 = S.hub_chunk0[d.v0];
-        AT p = 0;
-        for (int c = threadIdx.x; c < nch; c += kThreads) p += __ldcg((const AT*)S.hubsum + c0 + c);
-        const AT sum = block_sum<AT>(p, red);
-        if (threadIdx.x == 0) {
-          res += update_vertex<PR>(S, A, d.v0, sum, (int)(S.P.off[d.v0 + 1] - S.P.off[d.v0]),
-                                   (AT)((const RT*)S.r)[d.v0]);
-          S.ticket[d.v0] = 0;
+      bool ok2 = true;
+      for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        if (c > 0) {
+          ok2 = mbar_wait_bounded(b ? &bar2 : &bar, (c >> 1) & 1, A.err);
+          if (!__syncthreads_and(ok2)) break;
         }
+        const int64_t cs = d.e0 + (int64_t)c * kHubChunk;
+        const int cnt = (int)(min(cs + (int64_t)kHubChunk, d.e1) - cs);
+        const uint32_t* src = buf[b] + (cs & 3);
+        uint32_t e[kPerThread];
+        #pragma unroll
+        for (int u = 0; u < kPerThread; ++u) {
+          const int i = threadIdx.x + u * kThreads;
+          e[u] = i < cnt ? src[i] : 0u;
+        }
+        #pragma unroll
+        for (int u = 0; u < kPerThread; ++u)
+          if (threadIdx.x + u * kThreads < cnt) s += gather<PR>(S, e[u]);
+        __syncthreads();  // buffer b fully read
+        if (threadIdx.x == 0 && c + 2 < nch) issue_chunk(S.P.E, d.e0, d.e1, c + 2, buf[b], b ? &bar2 : &bar);
       }
+      const AT sum = block_sum<AT>(s, red);
+      if (threadIdx.x == 0 && ok2)
+        res += update_vertex<PR>(S, A, d.v0, sum, (int)(d.e1 - d.e0), (AT)((const RT*)S.r)[d.v0]);
     } else if (d.kind == kItemLeaf) {
       const int cnt = (int)(d.e1 - d.e0);
       const uint32_t* src = sE + d.eshift;
@@ -486,7 +488,7 @@ PrPlan make_plan(graph* g) {
   };
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
-    add(P.nchunk, 0, P.nchunk, 1, kItemHub, p, 8);
+    add(P.nhub, 0, P.nhub, 1, kItemHub, p, 8);
     for (int c = kClassHub - 1; c >= 1; --c) {
       const uint32_t v0 = P.cls_end[c + 1], v1 = P.cls_end[c];
       const uint32_t per = std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1));
@@ -529,8 +531,6 @@ graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
     GG_TRY(dalloc(g, w->x[p][0], es * P.nv));
     GG_TRY(dalloc(g, w->x[p][1], es * P.nv));
     GG_TRY(dalloc(g, w->ghost[p], es * P.nout));
-    GG_TRY(dalloc(g, w->hubsum[p], as * P.nchunk));
-    GG_TRY(dalloc(g, w->ticket[p], 4ull * P.nhub));
   }
   GG_TRY(dalloc(g, w->partials, as * (size_t)(nblocks + 1)));
   GG_TRY(dalloc(g, w->scal, 8 * sizeof(double)));
@@ -552,11 +552,6 @@ PrArgs make_args(graph* g, int cur, double damping) {
     S.x = w->x[p][cur].p;
     S.xn = w->x[p][1 - cur].p;
     S.ghost = w->ghost[p].p;
-    S.hubsum = w->hubsum[p].p;
-    S.ticket = (uint32_t*)w->ticket[p].p;
-    S.chunk_vertex = (const uint32_t*)P.chunk_vertex.p;
-    S.chunk_first = (const int64_t*)P.chunk_first.p;
-    S.hub_chunk0 = (const uint32_t*)P.hub_chunk0.p;
     zero += P.nv - P.cls_end[1];
   }
   A.scal = (double*)w->scal.p;
@@ -586,8 +581,6 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   timer.mark(2);
   const uint32_t nv0 = g->part[0].nv;
   int cur = 0;
-  for (int p = 0; p < 2; ++p)
-    GG_CUDA(cudaMemsetAsync(w->ticket[p].p, 0, 4ull * g->part[p].nhub, st));
   GG_CUDA(cudaMemsetAsync(w->done.p, 0, sizeof(uint32_t), st));
   {
     PrArgs A = make_args(g, cur, at.damping);
