@@ -233,9 +233,10 @@ __device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc
     rbytes = (q1 - q0) * (uint32_t)sizeof(RT);
   }
   mbar_expect_tx(bar, ebytes + obytes + rbytes);
-  if (ebytes) bulk_g2s(sE, S.P.E + a0, ebytes, bar);
-  if (obytes) bulk_g2s(sOff, S.P.off + o0, obytes, bar);
-  if (rbytes) bulk_g2s(sR, (const RT*)S.r + q0, rbytes, bar);
+  const uint64_t pol = l2_evict_first_policy();
+  if (ebytes) bulk_g2s_stream(sE, S.P.E + a0, ebytes, bar, pol);
+  if (obytes) bulk_g2s_stream(sOff, S.P.off + o0, obytes, bar, pol);
+  if (rbytes) bulk_g2s_stream(sR, (const RT*)S.r + q0, rbytes, bar, pol);
 }
 
 // Bulk copy of hub chunk c of the adjacency [e0, e1) into buf (16-byte granules).
@@ -245,7 +246,7 @@ __device__ __forceinline__ void issue_chunk(const uint32_t* E, int64_t e0, int64
   const int64_t a0 = cs & ~(int64_t)3, a1 = (ce + 3) & ~(int64_t)3;
   const uint32_t bytes = (uint32_t)((a1 - a0) * 4);
   mbar_expect_tx(bar, bytes);
-  bulk_g2s(buf, E + a0, bytes, bar);
+  bulk_g2s_stream(buf, E + a0, bytes, bar, l2_evict_first_policy());
 }
 
 template <class PR>
