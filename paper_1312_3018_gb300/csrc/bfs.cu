@@ -33,7 +33,7 @@ struct BfsCounters {
 };
 
 struct BfsWs {
-  DevBuf level[2], parent[2], visited[2], front[2][2], queue[2][2];
+  DevBuf level[2], parent[2], visited[2], front[2][2], queue[2][2], hubq[2][2];
   DevBuf oseen[2], olevel[2], oparent[2], dirty[2], ghost[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
 };
@@ -43,7 +43,8 @@ void free_bfs(graph* g) {
   BfsWs* w = g->bfs;
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->level[p], &w->parent[p], &w->visited[p], &w->front[p][0],
-                     &w->front[p][1], &w->queue[p][0], &w->queue[p][1], &w->oseen[p],
+                     &w->front[p][1], &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],
+                     &w->hubq[p][1], &w->oseen[p],
                      &w->olevel[p], &w->oparent[p], &w->dirty[p], &w->ghost[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
@@ -62,6 +63,7 @@ struct BfsSide {
   uint32_t* next;         // next frontier bitmap
   const uint32_t* queue;  // current queue (bucketed)
   uint32_t* nqueue;       // next queue (bucketed)
+  uint32_t* nhubq;        // next hub chunk list
   uint32_t* oseen;        // outbox claims
   uint32_t* olevel;
   uint32_t* oparent;
@@ -101,16 +103,19 @@ __device__ void flush_counts(LocalCounts c, BfsCounters* ctr) {
   }
 }
 
-// Top-down edge loop of one vertex (warp-uniform trip count). Edges e, e+stride, ... < t.
+// Top-down edge loop of one vertex whose adjacency starts at Ep: edges i = first,
+// first + stride, ... < deg (warp-uniform trip count). The append machinery runs only when
+// some lane of the warp discovered a vertex or claimed an outbox slot.
 __device__ __forceinline__ void td_edges(const BfsSide& S, int p, uint32_t L, uint32_t vgid,
-                                         int64_t e, int64_t t, int stride, BfsCounters* ctr,
-                                         LocalCounts& c) {
-  while (__any_sync(kFull, e < t)) {
+                                         const uint32_t* Ep, int first, int deg, int stride,
+                                         BfsCounters* ctr, LocalCounts& c) {
+  const uint64_t pol = l2_evict_first_policy();
+  for (int i = first; __any_sync(kFull, i < deg); i += stride) {
     bool dis = false, msg = false;
     uint32_t u = 0, idx = 0;
-    if (e < t) {
+    if (i < deg) {
       c.insp++;
-      const uint32_t x = S.P.E[e];
+      const uint32_t x = ld_stream(Ep + i, pol);
       if (!(x & kRemote)) {
         if (bitmap_claim(S.visited, x)) {
           dis = true;
@@ -130,9 +135,11 @@ __device__ __forceinline__ void td_edges(const BfsSide& S, int p, uint32_t L, ui
         }
       }
     }
-    warp_append_bucketed(dis, u, dis ? bucket_of(S.P, u) : 0, ctr->tail[p], S.nqueue, S.P);
-    warp_append(msg, idx, &ctr->dirty_tail[p], S.dirty);
-    e += stride;
+    if (__any_sync(kFull, dis || msg)) {
+      warp_append_bucketed(dis, u, dis ? bucket_of(S.P, u) : 0, ctr->tail[p], S.nqueue, S.P,
+                           S.nhubq);
+      warp_append(msg, idx, &ctr->dirty_tail[p], S.dirty);
+    }
   }
 }
 
@@ -144,9 +151,12 @@ k_bfs_topdown(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs
   const uint32_t rel = blockIdx.x - G.blk0;
   LocalCounts c;
   if (G.gshift >= 8) {
-    const uint32_t v = G.items[rel];
-    td_edges(S, p, A.L, S.P.l2g[v], S.P.off[v] + threadIdx.x, S.P.off[v + 1], kThreads, A.ctr,
-             c);
+    // one hub chunk per CTA
+    const uint32_t ch = G.items[rel];
+    const uint32_t v = S.P.chunk_vertex[ch];
+    const int64_t e0 = S.P.chunk_first[ch];
+    const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+    td_edges(S, p, A.L, S.P.l2g[v], S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, A.ctr, c);
   } else {
     const int gs = G.gshift;
     const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
@@ -159,7 +169,7 @@ k_bfs_topdown(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs
       vg = S.P.l2g[v];
     }
     const int gl = threadIdx.x & ((1 << gs) - 1);
-    td_edges(S, p, A.L, vg, s + gl, t, 1 << gs, A.ctr, c);
+    td_edges(S, p, A.L, vg, S.P.E + s, gl, (int)(t - s), 1 << gs, A.ctr, c);
   }
   flush_counts(c, A.ctr);
 }
@@ -192,7 +202,8 @@ __global__ void __launch_bounds__(kThreads) k_bfs_exchange(const __grid_constant
           c.mf += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
         }
       }
-      warp_append_bucketed(dis, u, dis ? bucket_of(Q.P, u) : 0, A.ctr->tail[q], Q.nqueue, Q.P);
+      warp_append_bucketed(dis, u, dis ? bucket_of(Q.P, u) : 0, A.ctr->tail[q], Q.nqueue, Q.P,
+                           Q.nhubq);
     }
   }
   flush_counts(c, A.ctr);
@@ -274,12 +285,13 @@ k_bfs_bottomup(const __grid_constant__ Plan plan, const __grid_constant__ BfsArg
     c.nf++;
     c.mf += (unsigned long long)(t - s);
   }
-  warp_append_bucketed(found, v, found ? G.bucket : 0, A.ctr->tail[p], S.nqueue, S.P);
+  warp_append_bucketed(found, v, found ? G.bucket : 0, A.ctr->tail[p], S.nqueue, S.P, S.nhubq);
   flush_counts(c, A.ctr);
 }
 
 __global__ void k_bfs_init(const __grid_constant__ BfsArgs A, const uint32_t* g2l,
-                           uint32_t source, uint32_t* queue0, uint32_t* queue1) {
+                           uint32_t source, uint32_t* queue0, uint32_t* queue1, uint32_t* hubq0,
+                           uint32_t* hubq1) {
   const uint32_t gl = g2l[source];
   const int p = gl >> 31;
   const uint32_t lid = gl & kIdMask;
@@ -291,7 +303,9 @@ __global__ void k_bfs_init(const __grid_constant__ BfsArgs A, const uint32_t* g2
   const int b = bucket_of(S.P, lid);
   A.ctr->nf = 1;
   A.ctr->mf = (unsigned long long)(S.P.off[lid + 1] - S.P.off[lid]);
-  if (b < kNBucket) {
+  if (b == 0) {
+    append_hub_chunks(S.P, lid, &A.ctr->tail[p][0], p == 0 ? hubq0 : hubq1);
+  } else if (b < kNBucket) {
     (p == 0 ? queue0 : queue1)[S.P.bstart[b]] = lid;
     A.ctr->tail[p][b] = 1;
   }
@@ -325,6 +339,8 @@ graph_status ensure_ws(graph* g) {
     GG_TRY(dalloc(g, w->front[p][1], 4 * words));
     GG_TRY(dalloc(g, w->queue[p][0], 4 * nv));
     GG_TRY(dalloc(g, w->queue[p][1], 4 * nv));
+    GG_TRY(dalloc(g, w->hubq[p][0], 4ull * P.nchunk));
+    GG_TRY(dalloc(g, w->hubq[p][1], 4ull * P.nchunk));
     GG_TRY(dalloc(g, w->oseen[p], 4 * owords));
     GG_TRY(dalloc(g, w->olevel[p], 4 * (size_t)P.nout));
     GG_TRY(dalloc(g, w->oparent[p], 4 * (size_t)P.nout));
@@ -352,6 +368,7 @@ BfsArgs make_args(graph* g, int cur, uint32_t L) {
     S.next = (uint32_t*)w->front[p][1 - cur].p;
     S.queue = (const uint32_t*)w->queue[p][cur].p;
     S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
+    S.nhubq = (uint32_t*)w->hubq[p][1 - cur].p;
     S.oseen = (uint32_t*)w->oseen[p].p;
     S.olevel = (uint32_t*)w->olevel[p].p;
     S.oparent = (uint32_t*)w->oparent[p].p;
@@ -412,7 +429,8 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
   {
     BfsArgs A = make_args(g, cur, 0);
     k_bfs_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
-                                (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p);
+                                (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p,
+                                (uint32_t*)w->hubq[0][cur].p, (uint32_t*)w->hubq[1][cur].p);
     GG_CUDA(cudaGetLastError());
   }
   BfsCounters* hc = (BfsCounters*)g->host_counters;
@@ -457,7 +475,8 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
       const int gsh[kNBucket] = {8, 5, kSubShift, 0};
       for (int p = 0; p < 2; ++p) {
         const PartView V = g->part[p].view();
-        for (int b = 0; b < kNBucket; ++b)
+        plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);  // chunks
+        for (int b = 1; b < kNBucket; ++b)
           plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
                    gsh[b], b);
       }

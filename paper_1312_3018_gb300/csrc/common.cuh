@@ -49,6 +49,12 @@ struct PartView {
   const uint32_t* W;      // [ne] or null
   const uint32_t* l2g;    // [nv]
   const uint32_t* outbox; // [nout] local ids in the other partition
+  // hub chunks: chunk c covers edges [chunk_first[c], min(+kHubChunk, end of its vertex))
+  // of vertex chunk_vertex[c]; hub vertex v owns chunks hub_chunk0[v] ...
+  const uint32_t* chunk_vertex;
+  const int64_t* chunk_first;
+  const uint32_t* hub_chunk0;
+  uint32_t nchunk;
   uint32_t bstart[kNBucket + 1];  // bucket b = [bstart[b], bstart[b+1]); bstart[4] = end of
                                   // vertices with edges (degree-zero vertices follow)
 };
@@ -118,14 +124,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Appends `item` (when `has`) to queue[bstart[bucket] + tail[bucket]++] with one atomic
-// per (warp, bucket); bucket 4 (degree zero) is not queued. All 32 lanes must call it.
+// Appends the chunks of hub vertex u (bucket 0) to a chunk list: push work on a hub is
+// split into kHubChunk-edge pieces, one CTA each.
+__device__ __forceinline__ void append_hub_chunks(const PartView& P, uint32_t u, uint32_t* tail,
+                                                  uint32_t* list) {
+  const int64_t deg = P.off[u + 1] - P.off[u];
+  const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
+  const uint32_t c0 = P.hub_chunk0[u];
+  const uint32_t at = atomicAdd(tail, nch);
+  for (uint32_t j = 0; j < nch; ++j) list[at + j] = c0 + j;
+}
+
+// Appends `item` (when `has`) to the next-round work of its bucket: buckets 1..3 to
+// queue[bstart[bucket] + tail[bucket]++] with one atomic per (warp, bucket); bucket 0 (hub)
+// as its chunks to hubq (tail[0] counts chunks); bucket 4 (degree zero) is not queued. All
+// 32 lanes must call it.
 __device__ __forceinline__ void warp_append_bucketed(bool has, uint32_t item, int bucket,
                                                      uint32_t* tails, uint32_t* queue,
-                                                     const PartView& P) {
+                                                     const PartView& P, uint32_t* hubq) {
   const uint32_t* bstart = P.bstart;
+  if (has && bucket == 0) append_hub_chunks(P, item, &tails[0], hubq);
   #pragma unroll
-  for (int b = 0; b < kNBucket; ++b) {
+  for (int b = 1; b < kNBucket; ++b) {
     const bool mine = has && bucket == b;
     const unsigned m = __ballot_sync(kFull, mine);
     if (m) {
@@ -217,6 +237,15 @@ __device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, uint
       " [%0], [%1], %2, [%3], %4;"
       ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
       : "memory");
+}
+// Read-only load of a streamed word (edge id or weight) that is not reused: L2 evicts it
+// first.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t policy) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+               : "=r"(v)
+               : "l"(p), "l"(policy));
+  return v;
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

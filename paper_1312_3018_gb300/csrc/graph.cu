@@ -115,6 +115,10 @@ PartView Part::view() const {
   v.W = (const uint32_t*)W.p;
   v.l2g = (const uint32_t*)l2g.p;
   v.outbox = (const uint32_t*)outbox.p;
+  v.chunk_vertex = (const uint32_t*)chunk_vertex.p;
+  v.chunk_first = (const int64_t*)chunk_first.p;
+  v.hub_chunk0 = (const uint32_t*)hub_chunk0.p;
+  v.nchunk = nchunk;
   v.bstart[0] = 0;
   v.bstart[1] = cls_end[kClassHub];
   v.bstart[2] = cls_end[kClassWarp];

@@ -2,15 +2,21 @@
 // on the partitioned graph.
 //
 // One BSP superstep per round:
-//  - compute: every active vertex reads its current distance and relaxes its edges with
-//    an atomic minimum on the target. A boundary target's minimum goes to its outbox
-//    slot, so the messages to one remote vertex reduce at the source (Section 3.4). A
-//    vertex whose distance drops joins the next round's active set (a bitmap guards
-//    against duplicates; queues are bucketed by degree class for work dispatch).
-//  - communication: the outbox slots lowered this round are applied to the owner with an
-//    atomic minimum (the inbox scatter with min of the Appendix); an owner vertex that
-//    improves becomes active.
-//  - termination: the round ends the search when no vertex became active.
+//  - compute: every active vertex relaxes its edges with a distance dv and records dv as the
+//    value it was relaxed with (a vertex handled by one lane group reads its newest
+//    distance; the chunks of a hub all use the distance it was queued with, so that every
+//    chunk relaxes with the same value): for a target whose distance exceeds dv + w,
+//    an atomic minimum (a reduction: no thread waits for it) lowers the distance and marks
+//    the target in a "touched" bitmap. A boundary target's minimum goes to its outbox slot
+//    (messages to one remote vertex reduce at the source, Section 3.4) and marks the slot
+//    in a dirty bitmap.
+//  - communication: the dirty outbox slots are applied to their owners with the same
+//    minimum-and-mark (the inbox scatter with min of the Appendix).
+//  - filter and termination: a touched vertex whose distance is now below the value it was
+//    last relaxed with joins the next round's active set (queues bucketed by degree class,
+//    hubs as edge chunks); the search ends when that set is empty. A non-hub vertex lowered
+//    while it waits in the current round is relaxed with its newest distance and not
+//    re-queued, the paper's same-round activation.
 // Distances are uint32; a relaxation saturates at 0xFFFFFFFE and flags an overflow.
 #include <string.h>
 
@@ -19,8 +25,7 @@
 namespace gg {
 
 struct SsspCounters {
-  uint32_t tail[2][kNBucket];
-  uint32_t dirty_tail[2];
+  uint32_t tail[2][kNBucket];  // next-round work: [0] hub chunks, [1..3] vertices
   uint32_t overflow;
   uint32_t pad;
   unsigned long long inspected;
@@ -30,7 +35,7 @@ struct SsspCounters {
 };
 
 struct SsspWs {
-  DevBuf dist[2], inq[2], queue[2][2], omsg[2], odirty[2], dirty[2];
+  DevBuf dist[2], snap[2], touched[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
 };
 
@@ -38,8 +43,9 @@ void free_sssp(graph* g) {
   if (!g->sssp) return;
   SsspWs* w = g->sssp;
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->dist[p], &w->inq[p], &w->queue[p][0], &w->queue[p][1],
-                     &w->omsg[p], &w->odirty[p], &w->dirty[p]};
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->touched[p], &w->queue[p][0],
+                     &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1], &w->omsg[p],
+                     &w->odirty[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
   delete w;
@@ -51,11 +57,12 @@ namespace {
 struct SsspSide {
   PartView P;
   uint32_t* dist;
-  uint32_t* inq;      // membership of the next active queue
+  uint32_t* snap;     // distance each vertex was last relaxed with (INF: never)
+  uint32_t* touched;  // vertices lowered this round
   uint32_t* nqueue;   // next active queue (bucketed)
+  uint32_t* nhubq;    // next hub chunk list
   uint32_t* omsg;     // outbox minima
   uint32_t* odirty;   // outbox slots lowered this round
-  uint32_t* dirty;    // list of those slots
 };
 
 struct SsspArgs {
@@ -70,6 +77,13 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b, bool& ovf) {
     return kInf - 1;
   }
   return (uint32_t)s;
+}
+
+__device__ __forceinline__ void red_min(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ void flush_ssp(unsigned long long insp, unsigned long long msg, bool ovf,
@@ -97,114 +111,140 @@ __device__ void flush_ssp(unsigned long long insp, unsigned long long msg, bool 
   }
 }
 
-__device__ __forceinline__ void relax_edges(const SsspSide& S, int p, uint32_t dv, int64_t e,
-                                            int64_t t, int stride, SsspCounters* ctr,
+// Relaxes edges i = first, first + stride, ... < deg of one vertex whose adjacency starts at
+// Ep / Wp. Lowering a distance is a fire-and-forget reduction plus a touched mark.
+__device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, const uint32_t* Ep,
+                                            const uint32_t* Wp, int first, int deg, int stride,
                                             unsigned long long& insp, bool& ovf) {
-  while (__any_sync(kFull, e < t)) {
-    bool act = false, msg = false;
-    uint32_t u = 0, idx = 0;
-    if (e < t) {
-      insp++;
-      const uint32_t x = S.P.E[e];
-      bool o = false;
-      const uint32_t nd = sat_add(dv, S.P.W[e], o);
-      if (!(x & kRemote)) {
-        if (nd < S.dist[x]) {
-          const uint32_t old = atomicMin(&S.dist[x], nd);
-          if (nd < old) {
-            ovf |= o;
-            if (bitmap_claim(S.inq, x)) {
-              act = true;
-              u = x;
-            }
-          }
-        }
-      } else {
-        idx = x & kIdMask;
-        if (nd < S.omsg[idx]) {
-          const uint32_t old = atomicMin(&S.omsg[idx], nd);
-          if (nd < old) {
-            ovf |= o;
-            msg = bitmap_claim(S.odirty, idx);
-          }
-        }
+  const uint64_t pol = l2_evict_first_policy();
+  #pragma unroll 2
+  for (int i = first; i < deg; i += stride) {
+    insp++;
+    const uint32_t x = ld_stream(Ep + i, pol);
+    bool o = false;
+    const uint32_t nd = sat_add(dv, ld_stream(Wp + i, pol), o);
+    if (!(x & kRemote)) {
+      if (nd < S.dist[x]) {
+        ovf |= o;
+        red_min(&S.dist[x], nd);
+        red_or(&S.touched[x >> 5], 1u << (x & 31u));
+      }
+    } else {
+      const uint32_t idx = x & kIdMask;
+      if (nd < S.omsg[idx]) {
+        ovf |= o;
+        red_min(&S.omsg[idx], nd);
+        red_or(&S.odirty[idx >> 5], 1u << (idx & 31u));
       }
     }
-    warp_append_bucketed(act, u, act ? bucket_of(S.P, u) : 0, ctr->tail[p], S.nqueue, S.P);
-    warp_append(msg, idx, &ctr->dirty_tail[p], S.dirty);
-    e += stride;
   }
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs A) {
   const Seg& G = plan.seg[find_seg(plan)];
-  const int p = G.part;
-  const SsspSide& S = A.side[p];
+  const SsspSide& S = A.side[G.part];
   const uint32_t rel = blockIdx.x - G.blk0;
   unsigned long long insp = 0;
   bool ovf = false;
   if (G.gshift >= 8) {
-    const uint32_t v = G.items[rel];
-    const uint32_t dv = __ldcg(&S.dist[v]);
-    relax_edges(S, p, dv, S.P.off[v] + threadIdx.x, S.P.off[v + 1], kThreads, A.ctr, insp, ovf);
+    // one hub chunk per CTA
+    const uint32_t ch = G.items[rel];
+    const uint32_t v = S.P.chunk_vertex[ch];
+    const int64_t e0 = S.P.chunk_first[ch];
+    const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+    const uint32_t dv = __ldcg(&S.snap[v]);  // the distance the hub was queued with
+    relax_edges(S, dv, S.P.E + e0, S.P.W + e0, threadIdx.x, (int)(e1 - e0), kThreads, insp, ovf);
   } else {
     const int gs = G.gshift;
     const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-    int64_t s = 0, t = 0;
-    uint32_t dv = 0;
+    const int gl = threadIdx.x & ((1 << gs) - 1);
     if (gi < G.count) {
       const uint32_t v = G.items[gi];
-      s = S.P.off[v];
-      t = S.P.off[v + 1];
-      dv = __ldcg(&S.dist[v]);
+      const int64_t s = S.P.off[v], t = S.P.off[v + 1];
+      const uint32_t dv = __ldcg(&S.dist[v]);
+      if (gl == 0) S.snap[v] = dv;
+      relax_edges(S, dv, S.P.E + s, S.P.W + s, gl, (int)(t - s), 1 << gs, insp, ovf);
     }
-    const int gl = threadIdx.x & ((1 << gs) - 1);
-    relax_edges(S, p, dv, s + gl, t, 1 << gs, A.ctr, insp, ovf);
   }
   flush_ssp(insp, 0, ovf, A.ctr);
 }
 
-// Communication phase: apply lowered outbox slots of p to the owner q (inbox scatter-min).
-__global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constant__ SsspArgs A) {
-  const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+// Communication phase: apply the dirty outbox slots of p to their owners in q.
+__global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constant__ SsspArgs A,
+                                                            uint32_t words0) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i < words0 ? 0 : 1;
+  const uint32_t word = p == 0 ? i : i - words0;
+  const SsspSide& S = A.side[p];
+  const SsspSide& Q = A.side[1 - p];
   unsigned long long msgs = 0;
-  for (int p = 0; p < 2; ++p) {
-    const SsspSide& S = A.side[p];
-    const SsspSide& Q = A.side[1 - p];
-    const int q = 1 - p;
-    const uint32_t cnt = *(volatile uint32_t*)&A.ctr->dirty_tail[p];
-    for (uint32_t i0 = warp_global * 32; i0 < cnt; i0 += nwarps * 32) {
-      const uint32_t i = i0 + lane_id();
-      bool act = false;
-      uint32_t u = 0;
-      if (i < cnt) {
-        const uint32_t idx = S.dirty[i];
-        atomicAnd(&S.odirty[idx >> 5], ~(1u << (idx & 31u)));
-        u = S.P.outbox[idx];
+  if (word * 32 < S.P.nout) {
+    uint32_t bits = S.odirty[word];
+    if (bits) {
+      S.odirty[word] = 0;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t idx = word * 32 + b;
+        const uint32_t u = S.P.outbox[idx];
         const uint32_t val = S.omsg[idx];
         msgs++;
         if (val < Q.dist[u]) {
-          const uint32_t old = atomicMin(&Q.dist[u], val);
-          if (val < old) act = bitmap_claim(Q.inq, u);
+          red_min(&Q.dist[u], val);
+          red_or(&Q.touched[u >> 5], 1u << (u & 31u));
         }
       }
-      warp_append_bucketed(act, u, act ? bucket_of(Q.P, u) : 0, A.ctr->tail[q], Q.nqueue, Q.P);
     }
   }
   flush_ssp(0, msgs, false, A.ctr);
 }
 
+// Filter: touched vertices whose distance dropped below the value they were last relaxed
+// with form the next active set. One lane per bitmap word; lanes walk their set bits in
+// step so that appends stay warp-aggregated.
+__global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant__ SsspArgs A,
+                                                          uint32_t words0, uint32_t words) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
+  const uint32_t word = p == 0 ? i : i - words0;
+  const SsspSide& S = A.side[p];
+  uint32_t bits = 0;
+  if (i < words) {
+    bits = S.touched[word];
+    if (bits) S.touched[word] = 0;
+  }
+  while (__any_sync(kFull, bits != 0)) {
+    bool act = false;
+    uint32_t x = 0;
+    if (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      x = word * 32 + b;
+      const uint32_t d = S.dist[x];
+      if (d < S.snap[x]) {
+        S.snap[x] = d;  // queued with d
+        act = true;
+      }
+    }
+    warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                         S.nhubq);
+  }
+}
+
 __global__ void k_sssp_init(const __grid_constant__ SsspArgs A, const uint32_t* g2l,
-                            uint32_t source, uint32_t* queue0, uint32_t* queue1) {
+                            uint32_t source, uint32_t* queue0, uint32_t* queue1,
+                            uint32_t* hubq0, uint32_t* hubq1) {
   const uint32_t gl = g2l[source];
   const int p = gl >> 31;
   const uint32_t lid = gl & kIdMask;
   const SsspSide& S = A.side[p];
   S.dist[lid] = 0;
+  S.snap[lid] = 0;
   const int b = bucket_of(S.P, lid);
-  if (b < kNBucket) {
+  if (b == 0) {
+    append_hub_chunks(S.P, lid, &A.ctr->tail[p][0], p == 0 ? hubq0 : hubq1);
+  } else if (b < kNBucket) {
     (p == 0 ? queue0 : queue1)[S.P.bstart[b]] = lid;
     A.ctr->tail[p][b] = 1;
   }
@@ -234,15 +274,18 @@ graph_status ensure_ws(graph* g) {
   g->sssp = w;
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
-    w->words[p] = (P.nv + 31) / 32;
-    w->owords[p] = (P.nout + 31) / 32;
+    // bitmap words rounded to whole warps (the filter assigns one lane per word)
+    w->words[p] = ((P.nv + 31) / 32 + 31) & ~(size_t)31;
+    w->owords[p] = ((P.nout + 31) / 32 + 31) & ~(size_t)31;
     GG_TRY(dalloc(g, w->dist[p], 4ull * P.nv));
-    GG_TRY(dalloc(g, w->inq[p], 4 * w->words[p]));
+    GG_TRY(dalloc(g, w->snap[p], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->touched[p], 4 * w->words[p]));
     GG_TRY(dalloc(g, w->queue[p][0], 4ull * P.nv));
     GG_TRY(dalloc(g, w->queue[p][1], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->hubq[p][0], 4ull * P.nchunk));
+    GG_TRY(dalloc(g, w->hubq[p][1], 4ull * P.nchunk));
     GG_TRY(dalloc(g, w->omsg[p], 4ull * P.nout));
     GG_TRY(dalloc(g, w->odirty[p], 4 * w->owords[p]));
-    GG_TRY(dalloc(g, w->dirty[p], 4ull * P.nout));
   }
   if (g->counters.bytes < sizeof(SsspCounters) || !g->counters.p) {
     dfree(g, g->counters);
@@ -259,11 +302,12 @@ SsspArgs make_args(graph* g, int cur) {
     SsspSide& S = A.side[p];
     S.P = g->part[p].view();
     S.dist = (uint32_t*)w->dist[p].p;
-    S.inq = (uint32_t*)w->inq[p].p;
+    S.snap = (uint32_t*)w->snap[p].p;
+    S.touched = (uint32_t*)w->touched[p].p;
     S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
+    S.nhubq = (uint32_t*)w->hubq[p][1 - cur].p;
     S.omsg = (uint32_t*)w->omsg[p].p;
     S.odirty = (uint32_t*)w->odirty[p].p;
-    S.dirty = (uint32_t*)w->dirty[p].p;
   }
   A.ctr = (SsspCounters*)g->counters.p;
   return A;
@@ -309,6 +353,8 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
     GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->touched[p].p, 0, 4 * w->words[p], st));
     GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * P.nout, st));
     GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
   }
@@ -317,7 +363,8 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
   {
     SsspArgs A = make_args(g, cur);
     k_sssp_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
-                                 (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p);
+                                 (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p,
+                                 (uint32_t*)w->hubq[0][cur].p, (uint32_t*)w->hubq[1][cur].p);
     GG_CUDA(cudaGetLastError());
   }
   SsspCounters* hc = (SsspCounters*)g->host_counters;
@@ -327,6 +374,8 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
   int64_t inspected = 0, messages = 0, launches = 1;
   bool overflow = false;
   int64_t rounds = 0;
+  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
   for (;; ++rounds) {
     SsspCounters c = *hc;
     uint64_t active = 0;
@@ -339,14 +388,14 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
       return GRAPH_ETIMEOUT;
     }
     GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(SsspCounters), st));
-    for (int p = 0; p < 2; ++p) GG_CUDA(cudaMemsetAsync(w->inq[p].p, 0, 4 * w->words[p], st));
     SsspArgs A = make_args(g, cur);
     Plan pl;
     memset(&pl, 0, sizeof(pl));
     const int gsh[kNBucket] = {8, 5, kSubShift, 0};
     for (int p = 0; p < 2; ++p) {
       const PartView V = g->part[p].view();
-      for (int b = 0; b < kNBucket; ++b)
+      plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);  // chunks
+      for (int b = 1; b < kNBucket; ++b)
         plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
                  gsh[b], b);
     }
@@ -354,10 +403,13 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
     if (pl.nblocks) k_sssp_relax<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
     GG_CUDA(cudaGetLastError());
     timer.mark(0);
-    k_sssp_exchange<<<152 * 4, kThreads, 0, st>>>(A);
-    launches += 1 + (pl.nblocks ? 1 : 0);
+    if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
     GG_CUDA(cudaGetLastError());
     timer.mark(1);
+    k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+    GG_CUDA(cudaGetLastError());
+    timer.mark(0);
+    launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
     GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;
@@ -376,8 +428,8 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
     SsspArgs A = make_args(g, cur);
     k_sssp_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, dd,
                                                          &dc->reached_degree, &dc->clamped);
-    launches++;
     GG_CUDA(cudaGetLastError());
+    launches++;
   }
   if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
