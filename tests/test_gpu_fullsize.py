@@ -1,0 +1,117 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times
+(degree split at T = 2048, RMAT with the Table 2 parameters, weights uniform in [1, 255]).
+
+RMAT scale 22 (4.19M vertices, ~128M edge entries): BFS levels and SSSP distances compared
+with the oracle element by element for sampled sources, PageRank to an L1 residual below
+1e-9 (the oracle's iteration count K*) in FP32 / FP16 against FP64.
+
+RMAT scale 25 (33.5M vertices, ~1.05B edge entries): BFS levels against the oracle for one
+source and its parents validated; SSSP distances checked with the optimality certificate
+(every edge satisfies dist[v] <= dist[u] + w and every reached vertex has a tight
+predecessor, which fixes the distances exactly); PageRank after 3 iterations against the
+FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+INF = oracle.INF
+T = 2048
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    g = synth.rmat(22, 16, seed=1)
+    synth.weights(g, 255, seed=3)
+    return g
+
+
+@pytest.fixture(scope="module")
+def rmat25():
+    g = synth.rmat(25, 16, seed=1)
+    synth.weights(g, 255, seed=3)
+    return g
+
+
+@pytest.fixture(scope="module")
+def loaded22(gpu, rmat22):
+    H = gpu.graph_load_csr(rmat22.offsets, rmat22.cols, rmat22.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=T)
+    yield H
+    H.free()
+
+
+@pytest.fixture(scope="module")
+def loaded25(gpu, rmat25):
+    H = gpu.graph_load_csr(rmat25.offsets, rmat25.cols, rmat25.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=T)
+    yield H
+    H.free()
+
+
+def test_rmat22_bfs_sixty_four_sources(gpu, rmat22, loaded22):
+    g = rmat22
+    srcs = synth.sources(g, 64, seed=2)
+    checked = 0
+    for k, s in enumerate(srcs):
+        lv, pa, st = gpu.bfs(loaded22, int(s), out="host")
+        assert lv[s] == 0 and pa[s] == s
+        if k < 4:  # element-by-element against the oracle for a sample of the searches
+            ref, _ = oracle.bfs(g.n, g.offsets, g.cols, int(s), want_parents=False)
+            assert np.array_equal(lv, ref)
+            assert oracle.check_bfs(g.n, g.offsets, g.cols, int(s), lv, pa) == 0
+            assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+            checked += 1
+    assert checked == 4
+
+
+def test_rmat22_sssp(gpu, rmat22, loaded22):
+    g = rmat22
+    for s in synth.sources(g, 2, seed=4):
+        d, st = gpu.sssp(loaded22, int(s), out="host")
+        ref = oracle.sssp(g.n, g.offsets, g.cols, g.weights, int(s))
+        assert np.array_equal(d, ref)
+        assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+
+
+def test_rmat22_pagerank_to_residual_1e9(gpu, rmat22, loaded22):
+    g = rmat22
+    ref, res, kstar = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=1000, tol=1e-9)
+    r64, st = gpu.pagerank(loaded22, max_iter=1000, tol=1e-9, precision="fp64", out="host")
+    assert st["supersteps"] == kstar
+    assert np.abs(r64 - ref).sum() <= 1e-12
+    r32, _ = gpu.pagerank(loaded22, max_iter=kstar, precision="fp32", out="host")
+    l1 = np.abs(r32 - ref).sum()
+    assert l1 <= 1e-6, f"FP32 L1 {l1:.3e} at K*={kstar}"
+    r16, _ = gpu.pagerank(loaded22, max_iter=kstar, precision="fp16", out="host")
+    assert np.abs(r16 - ref).sum() <= 1e-3
+
+
+def test_rmat25_bfs(gpu, rmat25, loaded25):
+    g = rmat25
+    s = int(synth.sources(g, 1, seed=2)[0])
+    lv, pa, st = gpu.bfs(loaded25, s, out="host")
+    ref, _ = oracle.bfs(g.n, g.offsets, g.cols, s, want_parents=False)
+    assert np.array_equal(lv, ref)
+    assert oracle.check_bfs(g.n, g.offsets, g.cols, s, lv, pa) == 0
+    assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+
+
+def test_rmat25_sssp_certificate(gpu, rmat25, loaded25):
+    g = rmat25
+    s = int(synth.sources(g, 1, seed=2)[0])
+    d, st = gpu.sssp(loaded25, s, out="host")
+    assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d) == 0
+    assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, d)
+
+
+def test_rmat25_pagerank_three_iterations(gpu, rmat25, loaded25):
+    g = rmat25
+    ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=3)
+    r32, _ = gpu.pagerank(loaded25, max_iter=3, precision="fp32", out="host")
+    assert np.abs(r32 - ref).sum() <= 1e-6
+    r16, _ = gpu.pagerank(loaded25, max_iter=3, precision="fp16", out="host")
+    assert np.abs(r16 - ref).sum() <= 1e-3
