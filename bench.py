@@ -63,6 +63,24 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def recorded_traffic(profile, source):
+    """DRAM bytes per launch from an ncu summary in profiles/, or None once the kernel's
+    source no longer matches the one the counters were taken on."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        src = open(os.path.join(ROOT, "paper_1312_3018_gb300", "csrc", source), "rb").read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    if f"sha256 prefix at capture: {sha}" not in text:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            return int(line.split(":")[1])
+    return None
+
+
 def workload_name(a):
     return (f"rmat{a.scale}-ef{a.edge_factor} bfs+sssp(w1..{a.wmax})+pagerank-fp32x{a.pr_iters}"
             f" degree-split T={a.threshold}")
@@ -318,6 +336,8 @@ def main():
         "k_bfs_topdown/bottomup": (bfs_bytes, bfs_compute_ms, bfs_levels),
     }
     dom = max(kern, key=lambda k: kern[k][1])
+    pr_traffic = recorded_traffic("k_pr_compute_fp32_rmat25_dram.md", "pagerank.cu") \
+        if a.scale == 25 else None
     rl = {}
     for name, (b, ms, launches_k) in kern.items():
         ach = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
@@ -325,6 +345,8 @@ def main():
                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
                     "launches": launches_k, "avg_launch_ms": round(ms / max(launches_k, 1), 4),
                     "peak_kind": peak_kind}
+    if pr_traffic:
+        rl["k_pr_compute<fp32>"]["traffic"] = pr_traffic
 
     # FP64 and FP16-stored PageRank rates (same graph, same iteration count).
     variants = {}
