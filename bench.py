@@ -147,16 +147,10 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def dist_setup(a):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
 def run_reference(a):
     """CPU oracle on the same workload: bounded per-step samples, rank 0 only."""
-    world, rank, _ = dist_setup(a)
+    from paper_1312_3018_gb300 import replicas
+    world, rank, _ = replicas.env()
     if rank != 0:
         return
     import oracle
@@ -230,18 +224,19 @@ def main():
     if a.impl == "reference":
         run_reference(a)
         return
-    world, rank, local = dist_setup(a)
     import torch
+    from paper_1312_3018_gb300 import replicas
+    world, rank, local = replicas.env()
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    replicas.init("nccl")
     import paper_1312_3018_gb300 as G
     import synth
 
     hbm_peak, peak_kind = peaks()
     g, gen_s = make_graph(a)
-    srcs = synth.sources(g, 64, seed=2 + 1000 * rank)  # replicas draw their own sources
+    # every replica answers its own, disjoint share of one seeded source list
+    srcs = replicas.rank_slice(synth.sources(g, 64 * world, seed=2), rank, world)
     stream = torch.cuda.current_stream()
 
     t = time.perf_counter()
@@ -282,8 +277,7 @@ def main():
 
     def barrier():
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     for k in range(a.warmup):
@@ -298,11 +292,7 @@ def main():
     t1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = replicas.max_over_ranks(t0.elapsed_time(t1), device="cuda")
 
     bfs_ms = sum(e[0].elapsed_time(e[1]) for e, *_ in recs)
     sssp_ms = sum(e[1].elapsed_time(e[2]) for e, *_ in recs)
@@ -311,8 +301,8 @@ def main():
     sssp_e = sum(ss["edges_traversed"] for _, _, ss, _ in recs)
     pr_e = sum(sp["edges_traversed"] for _, _, _, sp in recs)
     launches = sum(sb["launches"] + ss["launches"] + sp["launches"] for _, sb, ss, sp in recs)
-    step_edges = (bfs_e + sssp_e + pr_e) / a.steps
-    value = world * step_edges * a.steps / (total_ms / 1e3) / 1e9
+    all_edges = replicas.sum_over_ranks(bfs_e + sssp_e + pr_e, device="cuda")
+    value = replicas.aggregate_rate(all_edges, total_ms) / 1e9
 
     # Kernel-level times from the library's CUDA events on the same stream.
     pr_compute_ms = sum(sp["ms_compute"] for *_, sp in recs)
@@ -380,10 +370,11 @@ def main():
         erecs = [step(a.warmup + k, "host", bufs) for k in range(a.steps)]
         s1.record(stream)
         barrier()
-        ems = s0.elapsed_time(s1)
-        ee = sum(sb["edges_traversed"] + ss["edges_traversed"] + sp["edges_traversed"]
-                 for _, sb, ss, sp in erecs)
-        e2e = {"value": world * ee / (ems / 1e3) / 1e9, "unit": UNIT,
+        ems = replicas.max_over_ranks(s0.elapsed_time(s1), device="cuda")
+        ee = replicas.sum_over_ranks(
+            sum(sb["edges_traversed"] + ss["edges_traversed"] + sp["edges_traversed"]
+                for _, sb, ss, sp in erecs), device="cuda")
+        e2e = {"value": replicas.aggregate_rate(ee, ems) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 20 * n,
                "note": "resident graph; per step the two source ids go in as call arguments "
                        "and levels, parents, distances (uint32) and ranks (FP64) come back "
