@@ -145,31 +145,34 @@ __device__ __forceinline__ void td_edges(const BfsSide& S, int p, uint32_t L, ui
 
 __global__ void __launch_bounds__(kThreads)
 k_bfs_topdown(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs A) {
-  const Seg& G = plan.seg[find_seg(plan)];
-  const int p = G.part;
-  const BfsSide& S = A.side[p];
-  const uint32_t rel = blockIdx.x - G.blk0;
   LocalCounts c;
-  if (G.gshift >= 8) {
-    // one hub chunk per CTA
-    const uint32_t ch = G.items[rel];
-    const uint32_t v = S.P.chunk_vertex[ch];
-    const int64_t e0 = S.P.chunk_first[ch];
-    const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
-    td_edges(S, p, A.L, S.P.l2g[v], S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, A.ctr, c);
-  } else {
-    const int gs = G.gshift;
-    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-    int64_t s = 0, t = 0;
-    uint32_t vg = 0;
-    if (gi < G.count) {
-      const uint32_t v = G.items[gi];
-      s = S.P.off[v];
-      t = S.P.off[v + 1];
-      vg = S.P.l2g[v];
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const int p = G.part;
+    const BfsSide& S = A.side[p];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      // one hub chunk per plan block
+      const uint32_t ch = G.items[rel];
+      const uint32_t v = S.P.chunk_vertex[ch];
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      td_edges(S, p, A.L, S.P.l2g[v], S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, A.ctr,
+               c);
+    } else {
+      const int gs = G.gshift;
+      const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+      int64_t s = 0, t = 0;
+      uint32_t vg = 0;
+      if (gi < G.count) {
+        const uint32_t v = G.items[gi];
+        s = S.P.off[v];
+        t = S.P.off[v + 1];
+        vg = S.P.l2g[v];
+      }
+      const int gl = threadIdx.x & ((1 << gs) - 1);
+      td_edges(S, p, A.L, vg, S.P.E + s, gl, (int)(t - s), 1 << gs, A.ctr, c);
     }
-    const int gl = threadIdx.x & ((1 << gs) - 1);
-    td_edges(S, p, A.L, vg, S.P.E + s, gl, (int)(t - s), 1 << gs, A.ctr, c);
   }
   flush_counts(c, A.ctr);
 }
@@ -225,67 +228,73 @@ __global__ void k_bfs_publish_frontier(const __grid_constant__ BfsArgs A, uint32
   if (lane_id() == 0) S.ghost[word] = m;
 }
 
-// Bottom-up level over every unvisited vertex with edges (dense bucket segments).
+// Bottom-up level over every unvisited vertex with edges (dense bucket segments). Leaf-
+// partition vertices scan their adjacency from the end: their boundary neighbours (the
+// hubs, listed after the local ones) are the likeliest frontier members.
 __global__ void __launch_bounds__(kThreads)
 k_bfs_bottomup(const __grid_constant__ Plan plan, const __grid_constant__ BfsArgs A) {
-  const Seg& G = plan.seg[find_seg(plan)];
-  const int p = G.part;
-  const BfsSide& S = A.side[p];
-  const BfsSide& Q = A.side[1 - p];
-  const uint32_t rel = blockIdx.x - G.blk0;
-  const int gs = G.gshift;  // <= 5 here
-  const int gsz = 1 << gs;
-  const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-  const int gl = threadIdx.x & (gsz - 1);
-  const unsigned gmask = (gsz == 32) ? kFull : (((1u << gsz) - 1) << (lane_id() & ~(gsz - 1)));
   LocalCounts c;
-  uint32_t v = 0;
-  int64_t s = 0, t = 0;
-  bool active = false;
-  if (gi < G.count) {
-    v = G.v0 + gi;
-    if (!bitmap_test(S.visited, v)) {
-      active = true;
-      s = S.P.off[v];
-      t = S.P.off[v + 1];
-    }
-  }
-  bool found = false;
-  uint32_t pg = 0;
-  int64_t e = s + gl;
-  while (__any_sync(kFull, active)) {
-    bool hit = false;
-    uint32_t x = 0;
-    if (active && e < t) {
-      c.insp++;
-      x = S.P.E[e];
-      hit = (x & kRemote) ? bitmap_test(S.ghost, x & kIdMask) : bitmap_test(S.front, x);
-    }
-    const unsigned hits = __ballot_sync(kFull, hit) & gmask;
-    if (active) {
-      if (hits) {
-        const int src = __ffs(hits) - 1;
-        const uint32_t xs = __shfl_sync(gmask, x, src);
-        if (gl == 0) {
-          found = true;
-          pg = (xs & kRemote) ? Q.P.l2g[S.P.outbox[xs & kIdMask]] : S.P.l2g[xs];
-        }
-        active = false;
-      } else {
-        e += gsz;
-        if (e - gl >= t) active = false;
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const int p = G.part;
+    const BfsSide& S = A.side[p];
+    const BfsSide& Q = A.side[1 - p];
+    const uint32_t rel = vb - G.blk0;
+    const int gs = G.gshift;  // <= 5 here
+    const int gsz = 1 << gs;
+    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+    const int gl = threadIdx.x & (gsz - 1);
+    const unsigned gmask = (gsz == 32) ? kFull : (((1u << gsz) - 1) << (lane_id() & ~(gsz - 1)));
+    uint32_t v = 0;
+    int64_t s = 0, t = 0;
+    bool active = false;
+    if (gi < G.count) {
+      v = G.v0 + gi;
+      if (!bitmap_test(S.visited, v)) {
+        active = true;
+        s = S.P.off[v];
+        t = S.P.off[v + 1];
       }
     }
+    const int deg = (int)(t - s);
+    const bool rev = p == 1;
+    bool found = false;
+    uint32_t pg = 0;
+    int i = gl;
+    while (__any_sync(kFull, active)) {
+      bool hit = false;
+      uint32_t x = 0;
+      if (active && i < deg) {
+        c.insp++;
+        x = S.P.E[rev ? t - 1 - i : s + i];
+        hit = (x & kRemote) ? bitmap_test(S.ghost, x & kIdMask) : bitmap_test(S.front, x);
+      }
+      const unsigned hits = __ballot_sync(kFull, hit) & gmask;
+      if (active) {
+        if (hits) {
+          const int src = __ffs(hits) - 1;
+          const uint32_t xs = __shfl_sync(gmask, x, src);
+          if (gl == 0) {
+            found = true;
+            pg = (xs & kRemote) ? Q.P.l2g[S.P.outbox[xs & kIdMask]] : S.P.l2g[xs];
+          }
+          active = false;
+        } else {
+          i += gsz;
+          if (i - gl >= deg) active = false;
+        }
+      }
+    }
+    if (found) {
+      S.level[v] = A.L + 1;
+      S.parent[v] = pg;
+      atomicOr(&S.visited[v >> 5], 1u << (v & 31u));
+      atomicOr(&S.next[v >> 5], 1u << (v & 31u));
+      c.nf++;
+      c.mf += (unsigned long long)deg;
+    }
+    warp_append_bucketed(found, v, found ? G.bucket : 0, A.ctr->tail[p], S.nqueue, S.P, S.nhubq);
   }
-  if (found) {
-    S.level[v] = A.L + 1;
-    S.parent[v] = pg;
-    atomicOr(&S.visited[v >> 5], 1u << (v & 31u));
-    atomicOr(&S.next[v >> 5], 1u << (v & 31u));
-    c.nf++;
-    c.mf += (unsigned long long)(t - s);
-  }
-  warp_append_bucketed(found, v, found ? G.bucket : 0, A.ctr->tail[p], S.nqueue, S.P, S.nhubq);
   flush_counts(c, A.ctr);
 }
 
@@ -480,7 +489,7 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
           plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
                    gsh[b], b);
       }
-      if (pl.nblocks) k_bfs_topdown<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+      if (pl.nblocks) k_bfs_topdown<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
       GG_CUDA(cudaGetLastError());
       timer.mark(0);
       k_bfs_exchange<<<152 * 4, kThreads, 0, st>>>(A);
@@ -504,7 +513,7 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
         for (int b = 0; b < kNBucket; ++b)
           plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
       }
-      if (pl.nblocks) k_bfs_bottomup<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+      if (pl.nblocks) k_bfs_bottomup<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
       launches += pl.nblocks ? 1 : 0;
       GG_CUDA(cudaGetLastError());
       timer.mark(0);

@@ -105,14 +105,19 @@ inline void plan_add(Plan& pl, const uint32_t* items, uint32_t v0, uint32_t coun
   pl.nblocks += seg_blocks(count, gshift);
 }
 
-__device__ __forceinline__ int find_seg(const Plan& pl) {
-  // pl must be a __grid_constant__ kernel parameter (its address is taken)
+// Segment of plan block b (pl must be a __grid_constant__ kernel parameter: its address is
+// taken).
+__device__ __forceinline__ int find_seg(const Plan& pl, uint32_t b = blockIdx.x) {
   int s = 0;
   #pragma unroll 1
   for (int i = 1; i < pl.nseg; ++i)
-    if (blockIdx.x >= pl.seg[i].blk0) s = i;
+    if (b >= pl.seg[i].blk0) s = i;
   return s;
 }
+
+// Grid for kernels that walk a plan's blocks with a grid stride: enough CTAs to fill the
+// GPU (8 per SM), never more than the plan has.
+unsigned plan_grid(uint32_t plan_blocks);
 
 // ------------------------------------------------------------------------------------
 // Warp helpers

@@ -105,6 +105,18 @@ graph_status deliver(graph* g, void* dst, const void* dev_src, size_t bytes, int
   return GRAPH_OK;
 }
 
+unsigned plan_grid(uint32_t plan_blocks) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+  }
+  const uint32_t cap = (uint32_t)sms * 8u;
+  return plan_blocks < cap ? plan_blocks : cap;
+}
+
 PartView Part::view() const {
   PartView v;
   v.nv = nv;

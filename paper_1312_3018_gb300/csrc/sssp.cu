@@ -142,29 +142,32 @@ __device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, cons
 
 __global__ void __launch_bounds__(kThreads)
 k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs A) {
-  const Seg& G = plan.seg[find_seg(plan)];
-  const SsspSide& S = A.side[G.part];
-  const uint32_t rel = blockIdx.x - G.blk0;
   unsigned long long insp = 0;
   bool ovf = false;
-  if (G.gshift >= 8) {
-    // one hub chunk per CTA
-    const uint32_t ch = G.items[rel];
-    const uint32_t v = S.P.chunk_vertex[ch];
-    const int64_t e0 = S.P.chunk_first[ch];
-    const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
-    const uint32_t dv = __ldcg(&S.snap[v]);  // the distance the hub was queued with
-    relax_edges(S, dv, S.P.E + e0, S.P.W + e0, threadIdx.x, (int)(e1 - e0), kThreads, insp, ovf);
-  } else {
-    const int gs = G.gshift;
-    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-    const int gl = threadIdx.x & ((1 << gs) - 1);
-    if (gi < G.count) {
-      const uint32_t v = G.items[gi];
-      const int64_t s = S.P.off[v], t = S.P.off[v + 1];
-      const uint32_t dv = __ldcg(&S.dist[v]);
-      if (gl == 0) S.snap[v] = dv;
-      relax_edges(S, dv, S.P.E + s, S.P.W + s, gl, (int)(t - s), 1 << gs, insp, ovf);
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const SsspSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      // one hub chunk per plan block
+      const uint32_t ch = G.items[rel];
+      const uint32_t v = S.P.chunk_vertex[ch];
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      const uint32_t dv = __ldcg(&S.snap[v]);  // the distance the hub was queued with
+      relax_edges(S, dv, S.P.E + e0, S.P.W + e0, threadIdx.x, (int)(e1 - e0), kThreads, insp,
+                  ovf);
+    } else {
+      const int gs = G.gshift;
+      const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+      const int gl = threadIdx.x & ((1 << gs) - 1);
+      if (gi < G.count) {
+        const uint32_t v = G.items[gi];
+        const int64_t s = S.P.off[v], t = S.P.off[v + 1];
+        const uint32_t dv = __ldcg(&S.dist[v]);
+        if (gl == 0) S.snap[v] = dv;
+        relax_edges(S, dv, S.P.E + s, S.P.W + s, gl, (int)(t - s), 1 << gs, insp, ovf);
+      }
     }
   }
   flush_ssp(insp, 0, ovf, A.ctr);
@@ -400,7 +403,7 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
                  gsh[b], b);
     }
     timer.mark(2);
-    if (pl.nblocks) k_sssp_relax<<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+    if (pl.nblocks) k_sssp_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
     GG_CUDA(cudaGetLastError());
     timer.mark(0);
     if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
