@@ -39,28 +39,32 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    vp, u32, i32, dbl, i64 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
+                              ctypes.c_double, ctypes.c_int64)
+    lib.orc_bfs.restype = i32
+    lib.orc_bfs.argtypes = [u32, vp, vp, u32, vp, vp]
+    lib.orc_sssp.restype = i32
+    lib.orc_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
+    lib.orc_pagerank.restype = i32
+    lib.orc_pagerank.argtypes = [u32, vp, vp, dbl, i32, dbl, i32, vp, vp, vp]
+    lib.orc_partition.restype = i32
+    lib.orc_partition.argtypes = [u32, vp, vp, vp, vp] + [vp] * 6 + [vp, vp, vp, vp]
+    lib.orc_check_bfs.restype = i32
+    lib.orc_check_bfs.argtypes = [u32, vp, vp, u32, vp, vp]
+    lib.orc_check_sssp.restype = i32
+    lib.orc_check_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
+    lib.orc_traversed.restype = i64
+    lib.orc_traversed.argtypes = [u32, vp, vp]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            vp, u32, i32, dbl, i64 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
-                                      ctypes.c_double, ctypes.c_int64)
-            lib.orc_bfs.restype = i32
-            lib.orc_bfs.argtypes = [u32, vp, vp, u32, vp, vp]
-            lib.orc_sssp.restype = i32
-            lib.orc_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
-            lib.orc_pagerank.restype = i32
-            lib.orc_pagerank.argtypes = [u32, vp, vp, dbl, i32, dbl, i32, vp, vp, vp]
-            lib.orc_partition.restype = i32
-            lib.orc_partition.argtypes = [u32, vp, vp, vp, vp] + [vp] * 6 + [vp, vp, vp, vp]
-            lib.orc_check_bfs.restype = i32
-            lib.orc_check_bfs.argtypes = [u32, vp, vp, u32, vp, vp]
-            lib.orc_check_sssp.restype = i32
-            lib.orc_check_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
-            lib.orc_traversed.restype = i64
-            lib.orc_traversed.argtypes = [u32, vp, vp]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
 
 

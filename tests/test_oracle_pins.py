@@ -156,6 +156,23 @@ def test_bfs_validator_rejects_planted_mistakes():
     assert oracle.check_bfs(g.n, g.offsets, g.cols, 0, bad, None) == 2
     bad = lv.copy(); bad[0] = 1
     assert oracle.check_bfs(g.n, g.offsets, g.cols, 0, bad, pa) == 1
+    # a parent one level up that is not a neighbour: only the edge rule rejects it
+    # (vertex 8 = (2,1) at level 3; vertex 12 = (0,2) at level 2 is not adjacent to it)
+    bad = pa.copy(); bad[8] = 12
+    assert lv[12] + 1 == lv[8]
+    assert oracle.check_bfs(g.n, g.offsets, g.cols, 0, lv, bad) == 4
+
+
+def test_bfs_validator_rejects_level_jump_on_a_non_tree_edge():
+    """Path 0-1-2-3 closed by edge 0-3: true levels from 0 are [0,1,2,1]. Levels [0,1,2,3]
+    with parents [0,0,1,2] form a consistent tree, and only the non-tree edge 0-3, which
+    spans three levels, shows them wrong."""
+    g = synth.from_edges(4, [(0, 1), (1, 2), (2, 3), (0, 3)])
+    lv = np.array([0, 1, 2, 3], np.uint32)
+    pa = np.array([0, 0, 1, 2], np.uint32)
+    assert oracle.check_bfs(g.n, g.offsets, g.cols, 0, lv, pa) == 3
+    ref, rpa = oracle.bfs(g.n, g.offsets, g.cols, 0)
+    assert list(ref) == [0, 1, 2, 1]
 
 
 def test_traversed_edges_is_degree_sum_of_reached():
