@@ -164,15 +164,15 @@ def test_bfs_validator_rejects_planted_mistakes():
 
 
 def test_bfs_validator_rejects_level_jump_on_a_non_tree_edge():
-    """Path 0-1-2-3 closed by edge 0-3: true levels from 0 are [0,1,2,1]. Levels [0,1,2,3]
-    with parents [0,0,1,2] form a consistent tree, and only the non-tree edge 0-3, which
-    spans three levels, shows them wrong."""
-    g = synth.from_edges(4, [(0, 1), (1, 2), (2, 3), (0, 3)])
-    lv = np.array([0, 1, 2, 3], np.uint32)
-    pa = np.array([0, 0, 1, 2], np.uint32)
+    """Triangle 0-1-2: true levels from 0 are [0,1,1]. Levels [0,1,2] with parents [0,0,1]
+    form a consistent tree, and only the non-tree edge 0-2, which spans two levels, shows
+    them wrong."""
+    g = synth.from_edges(3, [(0, 1), (1, 2), (0, 2)])
+    lv = np.array([0, 1, 2], np.uint32)
+    pa = np.array([0, 0, 1], np.uint32)
     assert oracle.check_bfs(g.n, g.offsets, g.cols, 0, lv, pa) == 3
-    ref, rpa = oracle.bfs(g.n, g.offsets, g.cols, 0)
-    assert list(ref) == [0, 1, 2, 1]
+    ref, _ = oracle.bfs(g.n, g.offsets, g.cols, 0)
+    assert list(ref) == [0, 1, 1]
 
 
 def test_traversed_edges_is_degree_sum_of_reached():
