@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--wmax", type=int, default=255)
     ap.add_argument("--pr-iters", type=int, default=20)
-    ap.add_argument("--threshold", type=int, default=2048)
+    ap.add_argument("--threshold", default="auto",
+                    help="hub degree threshold T, or 'auto': the autotuner's choice among "
+                         "thresholds that keep a hub and a leaf partition")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
@@ -83,7 +85,7 @@ def recorded_traffic(profile, source):
 
 def workload_name(a):
     return (f"rmat{a.scale}-ef{a.edge_factor} bfs+sssp(w1..{a.wmax})+pagerank-fp32x{a.pr_iters}"
-            f" degree-split T={a.threshold}")
+            f" degree-split T={a.threshold}")  # T may be 'auto' (chosen value in config)
 
 
 def make_graph(a):
@@ -244,9 +246,16 @@ def main():
     torch.cuda.synchronize()
     load_s = time.perf_counter() - t
     t = time.perf_counter()
-    info = G.graph_partition(H, "degree", degree_threshold=a.threshold)
+    tuned = None
+    if a.threshold == "auto":
+        from paper_1312_3018_gb300 import autotune
+        tuned = autotune.autotune_threshold(G, H, int(srcs[0]), weighted=True)
+        info = G.graph_get_partition_info(H)
+    else:
+        info = G.graph_partition(H, "degree", degree_threshold=int(a.threshold))
     torch.cuda.synchronize()
     part_s = time.perf_counter() - t
+    threshold = info["threshold"]
 
     n, m = g.n, g.m
     lv = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -392,7 +401,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
         "data": "synthetic (seeded RMAT, Table 2 parameters; weights seeded)",
         "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
-                   "n": n, "m": m, "partition": {"strategy": "degree", "T": a.threshold,
+                   "n": n, "m": m, "partition": {"strategy": "degree", "T": threshold,
+                                                  "autotuned": tuned,
                                                   "nv": info["nv"], "ne": info["ne"],
                                                   "nout": info["nout"]},
                    "l2": "inputs larger than L2 (edge array 4m bytes >> 129 MB); no flush",
