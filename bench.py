@@ -2,7 +2,8 @@
 
 Workload (default): RMAT scale 25, edge factor 16, (A,B,C) = (0.57, 0.19, 0.19), seeded,
 symmetrised, deduplicated, vertex ids permuted; uint32 weights uniform in [1, 255];
-degree split at T = 2048 (hub / leaf partitions with outbox/inbox). One step is the whole
+degree split at a threshold T chosen by timing the step's algorithms at T = 256 ... 32768
+(hub / leaf partitions with outbox/inbox; `--threshold T` fixes it). One step is the whole
 hot path on the resident graph: BFS from one seeded source (levels and parents), SSSP
 from the same source, and 20 iterations of FP32 PageRank (damping 0.85). The graph load
 and partition are preprocessing (Section 5: only algorithm time is measured) and are
@@ -12,9 +13,10 @@ value = traversed edges of the step / step time, in GTEPS, with traversed edges 
 as in Section 5: BFS and SSSP the degree sum of the reached vertices, PageRank m per
 iteration. Per-algorithm rates, the FP64 / FP16 PageRank variants, the roofline of the
 dominant kernel, the CPU oracle baseline and the end-to-end number (host result buffers,
-device-to-host copies inside the timed region) are added to the same JSON line.
+device-to-host copies inside the timed region) are added to the same JSON line, and so is
+a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one.
 
-`--impl reference` times the CPU oracle (the reference arm of this build) on the same
+`--impl reference` times the CPU oracle (the reference arm) on the same
 workload and prints the same kind of line.
 """
 from __future__ import annotations
@@ -50,8 +52,15 @@ def parse():
     ap.add_argument("--threshold", default="auto",
                     help="hub degree threshold T, or 'auto': the autotuner's choice among "
                          "thresholds that keep a hub and a leaf partition")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_1312_3018_gb300",
+                                                         "tuned_thresholds.json"),
+                    help="autotuner results keyed by graph signature ('' disables)")
+    ap.add_argument("--retune", action="store_true",
+                    help="time the threshold candidates even if the cache has this graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-search batched BFS measurement")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     return ap.parse_args()
 
@@ -65,9 +74,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(profile, source):
+def recorded_traffic(profile, source, threshold):
     """DRAM bytes per launch from an ncu summary in profiles/, or None once the kernel's
-    source no longer matches the one the counters were taken on."""
+    source no longer matches the one the counters were taken on, or the summary was taken
+    at another degree threshold."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", profile)).read()
@@ -76,6 +86,8 @@ def recorded_traffic(profile, source):
         return None
     sha = hashlib.sha256(src).hexdigest()[:16]
     if f"sha256 prefix at capture: {sha}" not in text:
+        return None
+    if f"threshold at capture: {threshold}\n" not in text:
         return None
     for line in text.splitlines():
         if line.startswith("traffic_bytes_per_launch:"):
@@ -249,7 +261,8 @@ def main():
     tuned = None
     if a.threshold == "auto":
         from paper_1312_3018_gb300 import autotune
-        tuned = autotune.autotune_threshold(G, H, int(srcs[0]), weighted=True)
+        tuned = autotune.autotune_threshold(G, H, int(srcs[0]), weighted=True,
+                                            cache=a.tune_cache or None, retune=a.retune)
         info = G.graph_get_partition_info(H)
     else:
         info = G.graph_partition(H, "degree", degree_threshold=int(a.threshold))
@@ -335,8 +348,8 @@ def main():
         "k_bfs_topdown/bottomup": (bfs_bytes, bfs_compute_ms, bfs_levels),
     }
     dom = max(kern, key=lambda k: kern[k][1])
-    pr_traffic = recorded_traffic("k_pr_compute_fp32_rmat25_dram.md", "pagerank.cu") \
-        if a.scale == 25 else None
+    pr_traffic = recorded_traffic("k_pr_compute_fp32_rmat25_dram.md", "pagerank.cu",
+                                  threshold) if a.scale == 25 else None
     rl = {}
     for name, (b, ms, launches_k) in kern.items():
         ach = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
@@ -364,6 +377,48 @@ def main():
         variants[prec] = {"gedges_per_s_iter": m * a.pr_iters / (ms / 1e3) / 1e9,
                           "compute_ms_per_iter": per_it,
                           "hbm_frac_compute": byt / (per_it / 1e3) / 1e9 / hbm_peak}
+
+    # Batched BFS: the rank's 64 searches as bit lanes of one superstep sequence, against
+    # the same 64 searches one call each (levels only, device output, after the timed
+    # region).
+    batch = None
+    if not a.no_batch:
+        bsrc = np.asarray(srcs[:64])
+        blv = torch.empty((len(bsrc), n), dtype=torch.int32, device="cuda")
+        G.bfs_batch(H, bsrc, blv)
+        bms, bst = [], None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, bst = G.bfs_batch(H, bsrc, blv, timing=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bms.append(e0.elapsed_time(e1))
+        del blv
+        single_ms, single_e = 0.0, 0
+        G.bfs(H, int(bsrc[0]), lv, want_parents=False)
+        for s in bsrc:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, ss1 = G.bfs(H, int(s), lv, want_parents=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            single_ms += e0.elapsed_time(e1)
+            single_e += ss1["edges_traversed"]
+        best = min(bms)
+        batch = {"k": len(bsrc), "ms": round(best, 3),
+                 "gteps": bst["edges_traversed"] / (best / 1e3) / 1e9,
+                 "single_ms_total": round(single_ms, 3),
+                 "single_gteps": single_e / (single_ms / 1e3) / 1e9,
+                 "speedup": single_ms / best, "supersteps": bst["supersteps"],
+                 "push_steps": bst["topdown_steps"], "pull_steps": bst["bottomup_steps"],
+                 "ms_compute": round(bst["ms_compute"], 3),
+                 "ms_exchange": round(bst["ms_exchange"], 3),
+                 "edges_inspected": bst["edges_inspected"],
+                 "note": "bfs_batch, levels only, k x n uint32 device output; best of 3; "
+                         "singles are bfs() calls without parents on the same sources"}
 
     # End to end through the public API with pinned host result buffers.
     e2e = None
@@ -427,6 +482,7 @@ def main():
         "rooflines": rl,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batch_bfs": batch,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),

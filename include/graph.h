@@ -181,6 +181,36 @@ graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint32_t* parent
                  const bfs_attr* attr, graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * bfs_batch -- k <= 64 breadth-first searches in one sequence of supersteps. The paper
+ * runs one search per call (Section 6.3.2, Figure 11); here every vertex carries a 64-bit
+ * frontier mask and a 64-bit seen mask, bit s belonging to search s (multi-source BFS as
+ * bit lanes, Then et al., VLDB 2014), so the edges of a level are read once for all k
+ * searches. Each superstep has the same three phases as bfs: compute (push: a frontier
+ * vertex ORs its mask, less what the neighbour has seen, into the neighbour's next mask,
+ * boundary neighbours into their outbox slot; or pull: a vertex ORs the frontier masks of
+ * its neighbours until every search it has not seen is covered, boundary neighbours read
+ * from the ghost masks the owner published), communication (push: outbox masks are ORed
+ * into the owner's next masks; pull: publication of the frontier masks) and termination
+ * (no search found a new vertex).
+ *   sources  k uint32 source ids in host memory (duplicates allowed), each < n
+ *   k        1 <= k <= GRAPH_BATCH_MAX (other values: EINVAL)
+ *   levels   k * n uint32, row s (levels + s * n) = hop distances from sources[s] in global
+ *            vertex order, INF if unreached: exactly what bfs returns for sources[s].
+ *            Host or device memory per attr->out_mem; caller-owned.
+ * attr: out_mem, direction (GRAPH_BFS_AUTO picks push or pull per superstep by comparing
+ * the frontier's edges with the edges of vertices some search has not reached, weighted
+ * by alpha), alpha, max_supersteps and timing as for bfs; beta is unused. No parents.
+ * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator.
+ * Device workspace: 24 bytes per vertex, 16 per outbox slot and 4 * roundup(k, 4) per
+ * vertex of level lanes, kept with the graph until it is re-partitioned or freed.
+ * Errors: EINVAL, ESTATE (not partitioned), ETIMEOUT (max_supersteps), ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_BATCH_MAX 64u
+
+graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t k, uint32_t* levels,
+                       const bfs_attr* attr, graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
  * sssp -- single-source shortest paths by Bellman-Ford with an active set (Section 7.3,
  * Figure 20): each round relaxes the edges of the vertices whose distance improved,
  * atomic minimum on the target (boundary targets reduce into their outbox slot), and the

@@ -19,7 +19,7 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "sssp", "pagerank", "bfs_csr_noalloc",
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "bfs_csr_noalloc",
            "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
@@ -203,6 +203,27 @@ def bfs(g: Graph, source: int, levels=None, parents=None, *, want_parents: bool 
     st = _lib.load().bfs(g.handle, int(source), pl, pp, C.byref(attr), C.byref(stats))
     _lib.check(st, "bfs")
     return levels, (parents if want_parents else None), stats.as_dict()
+
+
+def bfs_batch(g: Graph, sources, levels=None, *, direction: str = "auto", alpha: float = 0.0,
+              out: str = "device", max_supersteps: int = 0, timing: bool = False):
+    """k = len(sources) <= BATCH_MAX searches in one pass of supersteps; levels [k, n]
+    uint32 (row s for sources[s], INF unreached) and stats."""
+    torch = _torch()
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64))
+    if src.ndim != 1 or np.any(src < 0) or np.any(src >= 2**32):
+        raise ValueError("sources must be a 1-D list of vertex ids")
+    src = src.astype(np.uint32)
+    k = len(src)
+    if levels is None:
+        levels = (torch.empty((k, g.n), dtype=torch.int32, device="cuda") if out == "device"
+                  else np.empty((k, g.n), dtype=np.uint32))
+    pl, mem = _ptr(levels)
+    attr = _lib.bfs_attr(mem, _DIR[direction], alpha, 0.0, max_supersteps, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().bfs_batch(g.handle, src.ctypes.data, k, pl, C.byref(attr), C.byref(stats))
+    _lib.check(st, "bfs_batch")
+    return levels, stats.as_dict()
 
 
 def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_supersteps: int = 0,

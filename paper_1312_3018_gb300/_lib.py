@@ -30,6 +30,7 @@ GRAPH_PR_FP32 = 0
 GRAPH_PR_FP64 = 1
 GRAPH_PR_FP16 = 2
 GRAPH_NOALLOC_MAX_VERTICES = 1 << 21
+GRAPH_BATCH_MAX = 64
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -87,6 +88,7 @@ SIGNATURES = {
     "graph_get_partition_info": (_int, [_vp, C.POINTER(graph_partition_info)]),
     "graph_export_partition": (_int, [_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bfs": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
+    "bfs_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
     "bfs_csr_noalloc": (_int, [_u32, _i64, _vp, _vp, _u32, _vp, _vp, _vp]),

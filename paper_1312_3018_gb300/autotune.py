@@ -30,12 +30,14 @@ def _signature(G, H, candidates):
 
 
 def autotune_threshold(G, H, source: int, *, weighted: bool, candidates=DEFAULT_CANDIDATES,
-                       pr_iters: int = 3, iters_per_step: int = 20, cache: str | None = None):
+                       pr_iters: int = 3, iters_per_step: int = 20, cache: str | None = None,
+                       retune: bool = False):
     """Returns {"T": best, "ms": {T: step estimate}, "cached": bool}; H ends partitioned at
-    the best T. G is the paper_1312_3018_gb300 module (passed in to avoid an import cycle)."""
+    the best T. G is the paper_1312_3018_gb300 module (passed in to avoid an import cycle).
+    retune: time the candidates even when the cache holds this graph (and update it)."""
     sig = _signature(G, H, candidates)
     key = json.dumps(sig, sort_keys=True)
-    if cache and os.path.exists(cache):
+    if cache and os.path.exists(cache) and not retune:
         try:
             with open(cache) as f:
                 table = json.load(f)

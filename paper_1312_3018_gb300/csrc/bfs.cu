@@ -332,7 +332,7 @@ __global__ void k_bfs_collect(const __grid_constant__ BfsArgs A, uint32_t nv0, u
   if (parents) parents[gid] = S.parent[lid];
 }
 
-graph_status ensure_ws(graph* g) {
+graph_status alloc_ws(graph* g) {
   if (g->bfs) return GRAPH_OK;
   BfsWs* w = new BfsWs();
   g->bfs = w;
@@ -361,6 +361,13 @@ graph_status ensure_ws(graph* g) {
     GG_TRY(dalloc(g, g->counters, 1024));
   }
   return ensure_host_counters(g, 1024);
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g) {
+  const graph_status s = alloc_ws(g);
+  if (s != GRAPH_OK) free_bfs(g);
+  return s;
 }
 
 BfsArgs make_args(graph* g, int cur, uint32_t L) {

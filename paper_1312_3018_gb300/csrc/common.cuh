@@ -296,6 +296,7 @@ struct Part {
 struct BfsWs;
 struct SsspWs;
 struct PrWs;
+struct MsWs;
 
 }  // namespace gg
 
@@ -319,6 +320,7 @@ struct graph {
   gg::BfsWs* bfs = nullptr;
   gg::SsspWs* sssp = nullptr;
   gg::PrWs* pr = nullptr;
+  gg::MsWs* ms = nullptr;     // batched BFS workspace
 };
 
 namespace gg {
@@ -359,6 +361,7 @@ graph_status deliver(graph* g, void* dst, const void* dev_src, size_t bytes, int
 void free_bfs(graph* g);
 void free_sssp(graph* g);
 void free_pr(graph* g);
+void free_msbfs(graph* g);
 
 inline unsigned grid_for(uint64_t work, unsigned per_block) {
   uint64_t b = (work + per_block - 1) / per_block;

@@ -1,0 +1,559 @@
+// Batched BFS: up to 64 level-synchronous searches share one sequence of BSP supersteps
+// (Section 4.1's compute / communication / termination phases, the BFS of Section 6.3.2
+// and Figure 11 run for k sources at once). Every vertex carries 64-bit masks, bit s
+// belonging to search s (multi-source BFS as bit lanes, Then et al., VLDB 2014):
+//   seen[v]   searches that have reached v
+//   front[v]  searches for which v is in the current frontier
+//   next[v]   searches that reach v in this level
+// One superstep:
+//  - compute, push: each frontier vertex ORs front[v] & ~seen[u] into next[u] of every
+//    local neighbour u and front[v] into the outbox slot of every boundary neighbour; or
+//    pull: each vertex that some search has not reached ORs the frontier masks of its
+//    neighbours (boundary neighbours through the ghost masks) until every missing search
+//    is covered, and keeps the covered bits in next[v].
+//  - communication: push ORs each outbox slot, less what the owner has seen, into the
+//    owner's next mask (the inbox side); pull publishes the owner's frontier masks into the
+//    ghost masks before the compute phase (Section 4.3.2's pull direction).
+//  - advance and termination: seen |= next, next becomes the frontier, the level of each
+//    new (vertex, search) pair is written to the vertex's level lanes, and the host reads
+//    how many vertices gained a bit; zero ends all k searches.
+// Level lanes are vertex-major (K = roundup(k, 4) uint32 per vertex) so that the advance
+// writes and the final transpose to the caller's search-major layout are coalesced.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace gg {
+
+typedef unsigned long long u64;
+
+struct MsCounters {
+  u64 nf;         // vertices that gained a bit this level
+  u64 mf;         // their degree sum (edges out of the next frontier)
+  u64 mu;         // degree sum of vertices with edges that some search has not reached
+  u64 traversed;  // sum over new (vertex, search) pairs of the vertex degree
+  u64 inspected;  // edge entries read by the compute phase
+  u64 messages;   // outbox slots delivered by the exchange
+};
+
+struct MsWs {
+  DevBuf seen[2], mask[2][2], lvl[2], ghost[2], omsg[2];
+  uint32_t K = 0;  // level lanes per vertex the lvl buffers hold
+};
+
+void free_msbfs(graph* g) {
+  if (!g->ms) return;
+  MsWs* w = g->ms;
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->seen[p], &w->mask[p][0], &w->mask[p][1], &w->lvl[p], &w->ghost[p],
+                     &w->omsg[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  delete w;
+  g->ms = nullptr;
+}
+
+namespace {
+
+struct MsSide {
+  PartView P;
+  u64* seen;
+  u64* front;   // current frontier masks
+  u64* next;    // masks gained this level
+  u64* ghost;   // [nout] frontier masks of the outbox targets (pull)
+  u64* omsg;    // [nout] masks pushed to the outbox targets (push)
+  uint32_t* lvl;  // [nv * K] level lanes
+};
+
+struct MsArgs {
+  MsSide side[2];
+  MsCounters* ctr;
+  u64 full;     // bits of the k searches
+  uint32_t K;
+  uint32_t L;   // level being expanded
+};
+
+struct MsSources {
+  uint32_t id[GRAPH_BATCH_MAX];
+};
+
+struct Cnt {
+  u64 nf = 0, mf = 0, mu = 0, trav = 0, insp = 0, msg = 0;
+};
+
+__device__ void flush(const Cnt& c, MsCounters* ctr) {
+  __shared__ u64 s[6];
+  if (threadIdx.x < 6) s[threadIdx.x] = 0;
+  __syncthreads();
+  const u64 v[6] = {warp_sum(c.nf), warp_sum(c.mf), warp_sum(c.mu), warp_sum(c.trav),
+                    warp_sum(c.insp), warp_sum(c.msg)};
+  if (lane_id() == 0)
+    for (int j = 0; j < 6; ++j)
+      if (v[j]) atomicAdd(&s[j], v[j]);
+  __syncthreads();
+  if (threadIdx.x < 6 && s[threadIdx.x]) atomicAdd(&((u64*)ctr)[threadIdx.x], s[threadIdx.x]);
+}
+
+// OR within aligned groups of 2^gshift lanes (gshift <= 5); all 32 lanes must call.
+__device__ __forceinline__ u64 group_or(u64 v, int gshift) {
+  for (int o = 1; o < (1 << gshift); o <<= 1) v |= __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Push of one frontier vertex's mask fm over edges first, first + stride, ... < deg.
+__device__ __forceinline__ void push_edges(const MsSide& S, u64 fm, const uint32_t* Ep,
+                                           int first, int deg, int stride, Cnt& c) {
+  const uint64_t pol = l2_evict_first_policy();
+  for (int i = first; i < deg; i += stride) {
+    c.insp++;
+    const uint32_t x = ld_stream(Ep + i, pol);
+    if (!(x & kRemote)) {
+      const u64 nb = fm & ~S.seen[x];
+      // next only gains bits during the compute phase, so an old copy never hides a bit
+      // that still has to be set
+      if (nb & ~__ldcg(&S.next[x])) atomicOr(&S.next[x], nb);
+    } else {
+      const uint32_t idx = x & kIdMask;
+      if (fm & ~__ldcg(&S.omsg[idx])) atomicOr(&S.omsg[idx], fm);
+    }
+  }
+}
+
+// Compute phase, push direction, over every vertex with edges (hub vertices as one CTA
+// per kHubChunk-edge chunk); vertices outside every frontier are skipped.
+__global__ void __launch_bounds__(kThreads)
+k_ms_push(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
+  Cnt c;
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const MsSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      const uint32_t ch = G.v0 + rel;
+      const uint32_t v = S.P.chunk_vertex[ch];
+      const u64 fm = S.front[v];
+      if (!fm) continue;  // CTA-uniform
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      push_edges(S, fm, S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, c);
+    } else {
+      const int gs = G.gshift;
+      const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+      if (gi >= G.count) continue;
+      const uint32_t v = G.v0 + gi;
+      const u64 fm = S.front[v];
+      if (!fm) continue;
+      const int64_t s = S.P.off[v], t = S.P.off[v + 1];
+      push_edges(S, fm, S.P.E + s, threadIdx.x & ((1 << gs) - 1), (int)(t - s), 1 << gs, c);
+    }
+  }
+  flush(c, A.ctr);
+}
+
+// Communication phase after a push level: outbox slot i of partition p carries the
+// searches that reached outbox[i] of the other partition q; ORed into q's next mask less
+// what q has seen, then cleared for the next level.
+__global__ void __launch_bounds__(kThreads) k_ms_exchange(const __grid_constant__ MsArgs A) {
+  Cnt c;
+  const uint64_t nout0 = A.side[0].P.nout;
+  const uint64_t total = nout0 + A.side[1].P.nout;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int p = i < nout0 ? 0 : 1;
+    const uint32_t idx = (uint32_t)(p == 0 ? i : i - nout0);
+    const MsSide& S = A.side[p];
+    const MsSide& Q = A.side[1 - p];
+    const u64 msg = S.omsg[idx];
+    if (!msg) continue;
+    S.omsg[idx] = 0;
+    c.msg++;
+    const uint32_t u = S.P.outbox[idx];
+    const u64 nb = msg & ~Q.seen[u];
+    if (nb) atomicOr(&Q.next[u], nb);
+  }
+  flush(c, A.ctr);
+}
+
+// Communication phase before a pull level: ghost mask i of p = frontier mask of outbox
+// target i in the other partition.
+__global__ void k_ms_publish(const __grid_constant__ MsArgs A) {
+  const uint64_t nout0 = A.side[0].P.nout;
+  const uint64_t total = nout0 + A.side[1].P.nout;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int p = i < nout0 ? 0 : 1;
+    const uint32_t idx = (uint32_t)(p == 0 ? i : i - nout0);
+    const MsSide& S = A.side[p];
+    S.ghost[idx] = A.side[1 - p].front[S.P.outbox[idx]];
+  }
+}
+
+__device__ __forceinline__ u64 frontier_of(const MsSide& S, uint32_t x) {
+  return (x & kRemote) ? S.ghost[x & kIdMask] : S.front[x];
+}
+
+// Compute phase, pull direction. A group of lanes scans vertex v's adjacency and stops
+// once the frontier masks it has ORed cover every search v has not seen. Leaf-partition
+// vertices scan from the end, where their boundary neighbours (the hubs) are listed. A hub
+// vertex is scanned chunk by chunk, one CTA per chunk, each warp a contiguous slice.
+__global__ void __launch_bounds__(kThreads)
+k_ms_pull(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
+  Cnt c;
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const int p = G.part;
+    const MsSide& S = A.side[p];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      const uint32_t ch = G.v0 + rel;
+      const uint32_t v = S.P.chunk_vertex[ch];
+      const u64 need = A.full & ~S.seen[v];
+      if (!need) continue;  // CTA-uniform
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t len = min((int64_t)kHubChunk, S.P.off[v + 1] - e0);
+      const int64_t slice = (len + (kThreads / 32) - 1) / (kThreads / 32);
+      const int64_t w0 = e0 + (threadIdx.x >> 5) * slice;
+      const int64_t w1 = min(w0 + slice, e0 + len);
+      u64 acc = 0;
+      for (int64_t b = w0; b < w1; b += 32) {  // warp-uniform trip count
+        const int64_t e = b + lane_id();
+        if (e < w1) {
+          c.insp++;
+          acc |= frontier_of(S, S.P.E[e]);
+        }
+        acc = group_or(acc, 5);
+        if ((acc & need) == need) break;
+      }
+      if (lane_id() == 0 && (acc & need)) atomicOr(&S.next[v], acc & need);
+      continue;
+    }
+    const int gs = G.gshift;
+    const int gsz = 1 << gs;
+    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+    const int gl = threadIdx.x & (gsz - 1);
+    uint32_t v = 0;
+    int64_t s = 0, t = 0;
+    u64 need = 0;
+    if (gi < G.count) {
+      v = G.v0 + gi;
+      need = A.full & ~S.seen[v];
+      if (need) {
+        s = S.P.off[v];
+        t = S.P.off[v + 1];
+      }
+    }
+    const int deg = (int)(t - s);
+    const bool rev = p == 1;
+    bool active = need != 0 && deg > 0;
+    u64 acc = 0;
+    int i = gl;
+    while (__any_sync(kFull, active)) {
+      if (active && i < deg) {
+        c.insp++;
+        acc |= frontier_of(S, S.P.E[rev ? t - 1 - i : s + i]);
+      }
+      acc = group_or(acc, gs);
+      if (active) {
+        i += gsz;
+        if ((acc & need) == need || i - gl >= deg) active = false;
+      }
+    }
+    if (gl == 0 && (acc & need)) S.next[v] = acc & need;
+  }
+  flush(c, A.ctr);
+}
+
+// Advance: seen |= next; the next masks become the frontier (the old frontier buffer is
+// cleared to serve as the next level's next buffer); new (vertex, search) pairs get level
+// L + 1 in the vertex's level lanes, written by the whole warp one vertex at a time.
+__global__ void __launch_bounds__(256) k_ms_advance(const __grid_constant__ MsArgs A) {
+  Cnt c;
+  const uint32_t nv0 = A.side[0].P.nv;
+  const uint64_t total = (uint64_t)nv0 + A.side[1].P.nv;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const uint64_t i = base + threadIdx.x;
+    int p = 0;
+    uint32_t v = 0;
+    u64 nx = 0;
+    if (i < total) {
+      p = i < nv0 ? 0 : 1;
+      v = (uint32_t)(p == 0 ? i : i - nv0);
+      const MsSide& S = A.side[p];
+      nx = S.next[v];
+      if (S.front[v]) S.front[v] = 0;
+      const int64_t deg = S.P.off[v + 1] - S.P.off[v];
+      u64 sm = S.seen[v];
+      if (nx) {
+        sm |= nx;
+        S.seen[v] = sm;
+        c.nf++;
+        c.mf += (u64)deg;
+        c.trav += (u64)deg * (u64)__popcll(nx);
+      }
+      if (deg > 0 && sm != A.full) c.mu += (u64)deg;
+    }
+    unsigned todo = __ballot_sync(kFull, nx != 0);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int pj = __shfl_sync(kFull, p, j);
+      const uint32_t vj = __shfl_sync(kFull, v, j);
+      const u64 mj = __shfl_sync(kFull, nx, j);
+      uint32_t* row = A.side[pj].lvl + (size_t)vj * A.K;
+      const uint32_t l = lane_id();
+      if ((mj >> l) & 1ull) row[l] = A.L + 1;
+      if ((mj >> (l + 32)) & 1ull) row[l + 32] = A.L + 1;
+    }
+  }
+  flush(c, A.ctr);
+}
+
+__global__ void k_ms_init(const __grid_constant__ MsArgs A, const __grid_constant__ MsSources src,
+                          uint32_t k, const uint32_t* g2l) {
+  const uint32_t s = threadIdx.x;
+  if (s >= k) return;
+  const uint32_t gl = g2l[src.id[s]];
+  const int p = gl >> 31;
+  const uint32_t lid = gl & kIdMask;
+  const MsSide& S = A.side[p];
+  const u64 bit = 1ull << s;
+  const u64 old = atomicOr(&S.seen[lid], bit);
+  atomicOr(&S.front[lid], bit);
+  S.lvl[(size_t)lid * A.K + s] = 0;
+  const u64 deg = (u64)(S.P.off[lid + 1] - S.P.off[lid]);
+  atomicAdd(&A.ctr->traversed, deg);
+  if (old == 0) {
+    atomicAdd(&A.ctr->nf, 1ull);
+    atomicAdd(&A.ctr->mf, deg);
+  }
+}
+
+// Local -> global, vertex-major level lanes -> search-major rows of the caller's array.
+__global__ void k_ms_collect(const __grid_constant__ MsArgs A, uint32_t n, uint32_t k,
+                             const uint32_t* g2l, uint32_t* levels) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const uint32_t gl = g2l[g];
+  const MsSide& S = A.side[gl >> 31];
+  const uint32_t lid = gl & kIdMask;
+  const u64 sm = S.seen[lid];
+  const uint4* row = (const uint4*)(S.lvl + (size_t)lid * A.K);
+  for (uint32_t s4 = 0; s4 * 4 < k; ++s4) {
+    const uint4 q = row[s4];
+    const uint32_t val[4] = {q.x, q.y, q.z, q.w};
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t s = s4 * 4 + j;
+      if (s < k) levels[(size_t)s * n + g] = ((sm >> s) & 1ull) ? val[j] : kInf;
+    }
+  }
+}
+
+graph_status alloc_ws(graph* g, uint32_t K) {
+  if (!g->ms) {
+    MsWs* w = new MsWs();
+    g->ms = w;
+    for (int p = 0; p < 2; ++p) {
+      const Part& P = g->part[p];
+      GG_TRY(dalloc(g, w->seen[p], 8ull * P.nv));
+      GG_TRY(dalloc(g, w->mask[p][0], 8ull * P.nv));
+      GG_TRY(dalloc(g, w->mask[p][1], 8ull * P.nv));
+      GG_TRY(dalloc(g, w->ghost[p], 8ull * P.nout));
+      GG_TRY(dalloc(g, w->omsg[p], 8ull * P.nout));
+    }
+  }
+  MsWs* w = g->ms;
+  if (w->K < K) {
+    w->K = 0;
+    for (int p = 0; p < 2; ++p) {
+      dfree(g, w->lvl[p]);
+      GG_TRY(dalloc(g, w->lvl[p], 4ull * K * g->part[p].nv));
+    }
+    w->K = K;
+  }
+  if (g->counters.bytes < sizeof(MsCounters) || !g->counters.p) {
+    dfree(g, g->counters);
+    GG_TRY(dalloc(g, g->counters, 1024));
+  }
+  return ensure_host_counters(g, 1024);
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g, uint32_t K) {
+  const graph_status s = alloc_ws(g, K);
+  if (s != GRAPH_OK) free_msbfs(g);
+  return s;
+}
+
+MsArgs make_args(graph* g, int cur, uint32_t k, uint32_t L) {
+  MsWs* w = g->ms;
+  MsArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int p = 0; p < 2; ++p) {
+    MsSide& S = A.side[p];
+    S.P = g->part[p].view();
+    S.seen = (u64*)w->seen[p].p;
+    S.front = (u64*)w->mask[p][cur].p;
+    S.next = (u64*)w->mask[p][1 - cur].p;
+    S.ghost = (u64*)w->ghost[p].p;
+    S.omsg = (u64*)w->omsg[p].p;
+    S.lvl = (uint32_t*)w->lvl[p].p;
+  }
+  A.ctr = (MsCounters*)g->counters.p;
+  A.full = k == 64 ? ~0ull : ((1ull << k) - 1);
+  A.K = w->K;
+  A.L = L;
+  return A;
+}
+
+}  // namespace
+}  // namespace gg
+
+using namespace gg;
+
+extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t k,
+                                  uint32_t* levels, const bfs_attr* attr, graph_stats* stats) {
+  if (!g || !sources || !levels) {
+    set_error("graph, sources or levels is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (k < 1 || k > GRAPH_BATCH_MAX) {
+    set_error("k = %u outside 1..%u", k, GRAPH_BATCH_MAX);
+    return GRAPH_EINVAL;
+  }
+  MsSources src;
+  memset(&src, 0, sizeof(src));
+  for (uint32_t s = 0; s < k; ++s) {
+    if (sources[s] >= g->n) {
+      set_error("sources[%u] = %u >= n %u", s, sources[s], g->n);
+      return GRAPH_EINVAL;
+    }
+    src.id[s] = sources[s];
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before bfs_batch");
+    return GRAPH_ESTATE;
+  }
+  bfs_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) {
+    set_error("bad out_mem");
+    return GRAPH_EINVAL;
+  }
+  const double alpha = at.alpha > 0 ? at.alpha : 15.0;
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  const uint32_t K = (k + 3) & ~3u;
+  GG_TRY(ensure_ws(g, K));
+  MsWs* w = g->ms;
+  cudaStream_t st = g->stream;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->seen[p].p, 0, 8ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->mask[p][0].p, 0, 8ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->mask[p][1].p, 0, 8ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0, 8ull * P.nout, st));
+  }
+  GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(MsCounters), st));
+  int cur = 0;
+  k_ms_init<<<1, 64, 0, st>>>(make_args(g, cur, k, 0), src, k, (const uint32_t*)g->g2l.p);
+  GG_CUDA(cudaGetLastError());
+  MsCounters* hc = (MsCounters*)g->host_counters;
+  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
+  // Both directions walk the same dense plan: hub chunks, then buckets 1..3 of each part.
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+  }
+  const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
+  const uint64_t nvt = (uint64_t)g->part[0].nv + g->part[1].nv;
+  const unsigned sweep_grid = 152 * 8;
+  int64_t traversed = (int64_t)hc->traversed, inspected = 0, messages = 0, launches = 1;
+  int push_steps = 0, pull_steps = 0;
+  uint64_t mu = (uint64_t)g->m;
+  int64_t L = 0;
+  for (;; ++L) {
+    const MsCounters c = *hc;
+    if (c.nf == 0) break;
+    if (L >= cap) {
+      set_error("bfs_batch reached the superstep cap (%lld)", (long long)cap);
+      timer.finish(nullptr);
+      return GRAPH_ETIMEOUT;
+    }
+    if (L > 0) mu = c.mu;
+    bool pull;
+    if (at.direction == GRAPH_BFS_TOPDOWN) pull = false;
+    else if (at.direction == GRAPH_BFS_BOTTOMUP) pull = L > 0;
+    else pull = L > 0 && (double)c.mf * alpha > (double)mu;
+    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(MsCounters), st));
+    const MsArgs A = make_args(g, cur, k, (uint32_t)L);
+    timer.mark(2);
+    if (!pull) {
+      if (pl.nblocks) k_ms_push<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      if (nout) k_ms_exchange<<<sweep_grid, kThreads, 0, st>>>(A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      launches += (pl.nblocks ? 1 : 0) + (nout ? 1 : 0);
+      push_steps++;
+    } else {
+      if (nout) k_ms_publish<<<sweep_grid, 256, 0, st>>>(A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      if (pl.nblocks) k_ms_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      launches += (pl.nblocks ? 1 : 0) + (nout ? 1 : 0);
+      pull_steps++;
+    }
+    k_ms_advance<<<grid_for(nvt, 256) < sweep_grid ? grid_for(nvt, 256) : sweep_grid, 256, 0,
+                   st>>>(A);
+    GG_CUDA(cudaGetLastError());
+    launches++;
+    timer.mark(2);
+    GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
+    messages += (int64_t)hc->messages;
+    traversed += (int64_t)hc->traversed;
+    cur = 1 - cur;
+  }
+  uint32_t* dl = levels;
+  const size_t bytes = 4ull * k * g->n;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, bytes));
+    dl = (uint32_t*)g->stage.p;
+  }
+  k_ms_collect<<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, cur, k, 0), g->n, k,
+                                                   (const uint32_t*)g->g2l.p, dl);
+  GG_CUDA(cudaGetLastError());
+  launches++;
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, levels, dl, bytes, GRAPH_MEM_HOST));
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)L;
+    stats->topdown_steps = push_steps;
+    stats->bottomup_steps = pull_steps;
+    stats->edges_traversed = traversed;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+  }
+  timer.finish(stats);
+  return s;
+}

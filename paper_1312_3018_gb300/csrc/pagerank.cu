@@ -512,7 +512,7 @@ graph_status prepare_kernel() {
   return GRAPH_OK;
 }
 
-graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
+graph_status alloc_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
   const size_t es = prec == GRAPH_PR_FP64 ? 8 : (prec == GRAPH_PR_FP16 ? 2 : 4);
   const size_t rs = prec == GRAPH_PR_FP64 ? 8 : 4;
   const size_t as = prec == GRAPH_PR_FP64 ? 8 : 4;
@@ -538,6 +538,13 @@ graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
   GG_TRY(dalloc(g, w->resid, sizeof(double) * (size_t)(max_iter + 1)));
   GG_TRY(dalloc(g, w->done, sizeof(uint32_t)));
   return GRAPH_OK;
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
+  const graph_status s = alloc_ws(g, prec, max_iter, nblocks);
+  if (s != GRAPH_OK) free_pr(g);
+  return s;
 }
 
 PrArgs make_args(graph* g, int cur, double damping) {

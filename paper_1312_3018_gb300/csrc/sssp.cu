@@ -271,7 +271,7 @@ __global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t nv0,
   if (lane_id() == 0 && d) atomicAdd(reached_degree, d);
 }
 
-graph_status ensure_ws(graph* g) {
+graph_status alloc_ws(graph* g) {
   if (g->sssp) return GRAPH_OK;
   SsspWs* w = new SsspWs();
   g->sssp = w;
@@ -295,6 +295,13 @@ graph_status ensure_ws(graph* g) {
     GG_TRY(dalloc(g, g->counters, 1024));
   }
   return ensure_host_counters(g, 1024);
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g) {
+  const graph_status s = alloc_ws(g);
+  if (s != GRAPH_OK) free_sssp(g);
+  return s;
 }
 
 SsspArgs make_args(graph* g, int cur) {

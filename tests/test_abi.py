@@ -88,10 +88,24 @@ def test_algorithms_reject_null_handles(lib):
     lv = (ctypes.c_uint32 * 4)()
     assert lib.bfs(None, 0, ctypes.addressof(lv), None, None, None) == _lib.GRAPH_EINVAL
     assert lib.sssp(None, 0, ctypes.addressof(lv), None, None) == _lib.GRAPH_EINVAL
+    src = (ctypes.c_uint32 * 1)()
+    assert lib.bfs_batch(None, ctypes.addressof(src), 1, ctypes.addressof(lv), None,
+                         None) == _lib.GRAPH_EINVAL
     attr = _lib.pagerank_attr(0.85, 10, 0.0, 0, 1, 0, 0)
     assert lib.pagerank(None, ctypes.byref(attr), None, None) == _lib.GRAPH_EINVAL
     assert lib.graph_partition(None, None) == _lib.GRAPH_EINVAL
     lib.graph_free(None)
+
+
+def test_binding_constants_match_the_header():
+    from paper_1312_3018_gb300 import _lib
+    src = open(HEADER).read()
+    for name in ("GRAPH_BATCH_MAX", "GRAPH_NOALLOC_MAX_VERTICES", "GRAPH_INF", "GRAPH_MEM_HOST",
+                 "GRAPH_MEM_DEVICE"):
+        m = re.search(r"#define\s+%s\s+\(?([0-9xXa-fA-F]+)u?(?:\s*<<\s*(\d+))?" % name, src)
+        assert m, name
+        val = int(m.group(1), 0) << (int(m.group(2)) if m.group(2) else 0)
+        assert getattr(_lib, name) == val, name
 
 
 def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):

@@ -24,4 +24,7 @@ def test_autotune_picks_a_candidate_and_caches(gpu, tmp_path):
     assert np.array_equal(lv, oracle.bfs(g.n, g.offsets, g.cols, s)[0])
     r2 = autotune.autotune_threshold(gpu, H, s, weighted=True, candidates=cands, cache=cache)
     assert r2["cached"] and r2["T"] == r1["T"]
+    r3 = autotune.autotune_threshold(gpu, H, s, weighted=True, candidates=cands, cache=cache,
+                                     retune=True)
+    assert not r3["cached"] and r3["T"] in cands
     H.free()

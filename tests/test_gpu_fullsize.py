@@ -115,3 +115,38 @@ def test_rmat25_pagerank_three_iterations(gpu, rmat25, loaded25):
     assert np.abs(r32 - ref).sum() <= 1e-6
     r16, _ = gpu.pagerank(loaded25, max_iter=3, precision="fp16", out="host")
     assert np.abs(r16 - ref).sum() <= 1e-3
+
+
+def test_rmat22_bfs_batch_sixty_four_sources(gpu, rmat22, loaded22):
+    """One 64-search batch at full size: every row has level 0 at its source and obeys the
+    BFS edge rule; four rows are compared with the oracle element by element, and the
+    traversed-edge count is the sum of the rows' TEPS numerators."""
+    g = rmat22
+    srcs = synth.sources(g, 64, seed=2)
+    lv, st = gpu.bfs_batch(loaded22, srcs, out="host")
+    total = 0
+    for row, s in enumerate(srcs):
+        assert lv[row, s] == 0
+        total += oracle.traversed(g.n, g.offsets, lv[row])
+        if row < 4:
+            ref, _ = oracle.bfs(g.n, g.offsets, g.cols, int(s), want_parents=False)
+            assert np.array_equal(lv[row], ref), f"row {row}"
+    assert st["edges_traversed"] == total
+    # |level[u] - level[v]| <= 1 along every edge, for a sample of rows
+    src_of_edge = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
+    for row in (10, 37, 63):
+        a = lv[row][src_of_edge].astype(np.int64)
+        b = lv[row][g.cols].astype(np.int64)
+        both = (a != INF) & (b != INF)
+        assert np.all(np.abs(a[both] - b[both]) <= 1)
+        assert np.all((a == INF) == (b == INF))
+
+
+def test_rmat25_bfs_batch(gpu, rmat25, loaded25):
+    g = rmat25
+    srcs = synth.sources(g, 64, seed=2)
+    lv, st = gpu.bfs_batch(loaded25, srcs, out="device")
+    for row in (0, 41):
+        ref, _ = oracle.bfs(g.n, g.offsets, g.cols, int(srcs[row]), want_parents=False)
+        assert np.array_equal(gpu.as_numpy_u32(lv[row]), ref), f"row {row}"
+    del lv

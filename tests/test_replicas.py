@@ -52,3 +52,4 @@ def test_single_rank_is_identity(monkeypatch):
     assert replicas.max_over_ranks(3.5) == 3.5
     assert replicas.sum_over_ranks(2.0) == 2.0
     assert replicas.rank_slice([1, 2, 3], 0, 1) == [1, 2, 3]
+
