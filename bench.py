@@ -14,7 +14,9 @@ as in Section 5: BFS and SSSP the degree sum of the reached vertices, PageRank m
 iteration. Per-algorithm rates, the FP64 / FP16 PageRank variants, the roofline of the
 dominant kernel, the CPU oracle baseline and the end-to-end number (host result buffers,
 device-to-host copies inside the timed region) are added to the same JSON line, and so is
-a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one.
+a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one, and
+PageRank of 256 uneven RMAT graphs in one union (pagerank_multi, iterations replayed as a
+CUDA graph) timed against one pagerank() call per graph.
 
 `--impl reference` times the CPU oracle (the reference arm) on the same
 workload and prints the same kind of line.
@@ -60,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the 64-search batched BFS measurement")
+                    help="skip the batched BFS and many-graph PageRank measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     return ap.parse_args()
 
@@ -420,6 +422,66 @@ def main():
                  "note": "bfs_batch, levels only, k x n uint32 device output; best of 3; "
                          "singles are bfs() calls without parents on the same sources"}
 
+    # Many-graph PageRank: 256 uneven RMAT graphs (scales 10-17, edge factors 8-32) as one
+    # union, 30 FP32 iterations in one replayed CUDA graph, against the same 256 graphs
+    # ranked one pagerank() call each (each graph its own handle, same threshold).
+    batch_pr = None
+    if not a.no_batch:
+        import synth as _synth
+        from paper_1312_3018_gb300 import autotune as _at
+        t = time.perf_counter()
+        fam = _synth.rmat_family(256, scales=(10, 17), edge_factors=(8, 32), seed=7)
+        U, vb = _synth.disjoint_union(fam)
+        fam_s = time.perf_counter() - t
+        HU = G.graph_load_csr(U.offsets, U.cols)
+        tunedm = _at.autotune_multi_threshold(G, HU, vb, iters=30)
+        Tm = tunedm["T"]
+        ru = torch.empty(U.n, dtype=torch.float64, device="cuda")
+        G.pagerank_multi(HU, vb, max_iter=30, ranks=ru)
+        mms, mst = [], None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, mres, mst = G.pagerank_multi(HU, vb, max_iter=30, ranks=ru)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms.append(e0.elapsed_time(e1))
+        HU.free()
+        del ru
+        handles = []
+        for fg in fam:
+            hg = G.graph_load_csr(fg.offsets, fg.cols)
+            G.graph_partition(hg, "degree", degree_threshold=Tm)
+            handles.append(hg)
+        rs = [torch.empty(fg.n, dtype=torch.float64, device="cuda") for fg in fam]
+        for hg, rg in zip(handles, rs):
+            G.pagerank(hg, max_iter=30, ranks=rg)
+        sms = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for hg, rg in zip(handles, rs):
+                G.pagerank(hg, max_iter=30, ranks=rg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sms.append(e0.elapsed_time(e1))
+        for hg in handles:
+            hg.free()
+        del rs
+        best, sbest = min(mms), min(sms)
+        batch_pr = {"graphs": len(fam), "n": U.n, "m": U.m, "iters": 30, "T": Tm,
+                    "autotuned": tunedm, "ms": round(best, 3),
+                    "gedges_per_s_iter": U.m * 30 / (best / 1e3) / 1e9,
+                    "single_ms_total": round(sbest, 3),
+                    "single_gedges_per_s_iter": U.m * 30 / (sbest / 1e3) / 1e9,
+                    "speedup": sbest / best, "launches_per_call": mst["launches"],
+                    "max_component_residual": float(np.max(mres)),
+                    "generate_s": round(fam_s, 2),
+                    "note": "pagerank_multi (iterations replayed as one CUDA graph) vs one "
+                            "pagerank() call per graph; FP32, device ranks, best of 3 / 2"}
+
     # End to end through the public API with pinned host result buffers.
     e2e = None
     if not a.no_e2e:
@@ -483,6 +545,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batch_bfs": batch,
+        "batch_pagerank": batch_pr,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),

@@ -264,6 +264,33 @@ graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* ranks,
                       graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * pagerank_multi -- PageRank of many independent graphs in one pass of supersteps. The
+ * paper ranks one graph per run (Section 7.1, Figure 14); here the loaded graph is the
+ * disjoint union of ngraphs components, component c owning global vertex ids
+ * [vbase[c], vbase[c+1]), and each component gets exactly the iteration pagerank gives
+ * that graph alone: r_0 = 1/n_c, r' = (1-d)/n_c + d (sum + D_c/n_c) with its own dangling
+ * mass D_c. Every iteration is one launch over the work items of all components; the
+ * max_iter iterations are captured once as a CUDA graph and replayed by later calls with
+ * the same layout, iteration count, damping and dangling mode.
+ *   ngraphs    >= 1 components
+ *   vbase      ngraphs + 1 uint32 in host memory: 0 = vbase[0] <= vbase[1] <= ... <=
+ *              vbase[ngraphs] = n (empty components allowed). Every edge must join two
+ *              vertices of one component (checked on the device; else EINVAL).
+ *   attr       as for pagerank, with tol = 0 (a fixed count of max_iter iterations)
+ *   ranks      n doubles in global order, each component's ranks summing to 1 (host or
+ *              device per attr->out_mem)
+ *   residuals  ngraphs doubles in host memory: each component's L1 change in the last
+ *              iteration, or NULL
+ * The first call for a layout validates it and counts each component's degree-zero
+ * vertices (one pass over the edges); the layout, the per-vertex component ids and the
+ * captured graph are kept with the PageRank workspace (freed on re-partition or
+ * graph_free). Errors: EINVAL, ESTATE (not partitioned), ENOMEM, ECUDA, ETIMEOUT.
+ * ------------------------------------------------------------------------------------- */
+graph_status pagerank_multi(graph_t* g, uint32_t ngraphs, const uint32_t* vbase,
+                            const pagerank_attr* attr, double* ranks, double* residuals,
+                            graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
  * bfs_csr_noalloc -- breadth-first search for callers that cannot allocate device memory.
  * The paper has no counterpart: this entry point exists for code that must not call
  * cudaMalloc at search time (host callbacks and driver hooks where allocation is forbidden

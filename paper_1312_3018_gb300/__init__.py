@@ -19,7 +19,7 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "bfs_csr_noalloc",
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "pagerank_multi", "bfs_csr_noalloc",
            "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
@@ -254,6 +254,32 @@ def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float 
     st = _lib.load().pagerank(g.handle, C.byref(attr), pr_, C.byref(stats))
     _lib.check(st, "pagerank")
     return ranks, stats.as_dict()
+
+
+def pagerank_multi(g: Graph, vbase, *, damping: float = 0.85, max_iter: int = 30,
+                   precision: str = "fp32", dangling: bool = True, ranks=None,
+                   out: str = "device", timing: bool = False):
+    """PageRank of each component [vbase[c], vbase[c+1]) of the loaded union, max_iter
+    iterations in one replayed CUDA graph. Returns (FP64 ranks in global order, per-component
+    residual of the last iteration, stats)."""
+    torch = _torch()
+    vb = np.ascontiguousarray(np.asarray(vbase, dtype=np.int64))
+    if vb.ndim != 1 or len(vb) < 2 or np.any(vb < 0) or np.any(vb >= 2**32):
+        raise ValueError("vbase must be a 1-D list of at least two vertex ids")
+    vb = vb.astype(np.uint32)
+    G = len(vb) - 1
+    if ranks is None:
+        ranks = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"
+                 else np.empty(g.n, dtype=np.float64))
+    pr_, mem = _ptr(ranks)
+    res = np.zeros(G, dtype=np.float64)
+    attr = _lib.pagerank_attr(float(damping), int(max_iter), 0.0, _PREC[precision],
+                              int(bool(dangling)), mem, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().pagerank_multi(g.handle, G, vb.ctypes.data, C.byref(attr), pr_,
+                                    res.ctypes.data, C.byref(stats))
+    _lib.check(st, "pagerank_multi")
+    return ranks, res, stats.as_dict()
 
 
 def bfs_csr_noalloc(offsets, cols, source: int, levels=None, parents=None, *, stream=None,

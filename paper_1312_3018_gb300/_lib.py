@@ -91,6 +91,8 @@ SIGNATURES = {
     "bfs_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
+    "pagerank_multi": (_int, [_vp, _u32, _vp, C.POINTER(pagerank_attr), _vp, _vp,
+                              C.POINTER(graph_stats)]),
     "bfs_csr_noalloc": (_int, [_u32, _i64, _vp, _vp, _u32, _vp, _vp, _vp]),
     "graph_free": (None, [_vp]),
     "graph_strerror": (C.c_char_p, [_int]),

@@ -78,3 +78,24 @@ def autotune_threshold(G, H, source: int, *, weighted: bool, candidates=DEFAULT_
             json.dump(table, f)
         os.replace(tmp, cache)
     return result
+
+
+# Candidates for a union of many small graphs: their hubs are far smaller, and a single
+# partition (1 << 31) is included because the components never need an exchange.
+MULTI_CANDIDATES = (64, 256, 2048, 1 << 31)
+
+
+def autotune_multi_threshold(G, H, vbase, *, candidates=MULTI_CANDIDATES, iters: int = 30,
+                             precision: str = "fp32"):
+    """Degree threshold for pagerank_multi on the union H: re-partition per candidate, run
+    once (validates the layout and captures the iteration graph), time one replay with the
+    library's CUDA events, keep the fastest; H ends partitioned at the winner."""
+    scores = {}
+    for T in candidates:
+        G.graph_partition(H, "degree", degree_threshold=T)
+        G.pagerank_multi(H, vbase, max_iter=iters, precision=precision)
+        _, _, st = G.pagerank_multi(H, vbase, max_iter=iters, precision=precision, timing=True)
+        scores[T] = st["ms_total"]
+    best = min(scores, key=scores.get)
+    G.graph_partition(H, "degree", degree_threshold=best)
+    return {"T": best, "ms": {str(k): v for k, v in scores.items()}}

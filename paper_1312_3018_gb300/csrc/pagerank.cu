@@ -30,10 +30,25 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
 namespace gg {
+
+// State of pagerank_multi: the component layout it last validated, per-vertex component
+// ids, the per-iteration constant table and the captured iteration graph.
+struct MultiWs {
+  std::vector<uint32_t> vbase;      // validated component boundaries (global ids)
+  std::vector<uint32_t> nzero;      // degree-zero vertices per component
+  DevBuf dvbase, dnzero, gix[2], base, dn, nf, res;
+  size_t base_bytes = 0;
+  cudaStream_t capture = nullptr;   // private stream used only to capture
+  cudaGraphExec_t exec = nullptr;   // iterations [0, iters) of the last capture
+  int iters = 0;
+  double damping = -1;              // kernel parameters baked into the capture
+  int dangling = -1;
+};
 
 struct PrWs {
   int prec = -1;
@@ -43,11 +58,25 @@ struct PrWs {
   DevBuf partials, scal, resid, done;
   uint32_t nblocks = 0;
   int max_iter = 0;
+  MultiWs* multi = nullptr;
 };
+
+void free_multi(graph* g, PrWs* w) {
+  MultiWs* m = w->multi;
+  if (!m) return;
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->capture) cudaStreamDestroy(m->capture);
+  DevBuf* all[] = {&m->dvbase, &m->dnzero, &m->gix[0], &m->gix[1], &m->base, &m->dn, &m->nf,
+                   &m->res};
+  for (DevBuf* b : all) dfree(g, *b);
+  delete m;
+  w->multi = nullptr;
+}
 
 void free_pr(graph* g) {
   if (!g->pr) return;
   PrWs* w = g->pr;
+  free_multi(g, w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->r[p], &w->x[p][0], &w->x[p][1], &w->ghost[p]};
     for (DevBuf* b : all) dfree(g, *b);
@@ -86,6 +115,20 @@ struct PrArgs {
   float damping_f, n_f, d_over_n_f;
   double nzero;       // number of degree-zero vertices
   int* err;
+};
+
+// Many independent graphs in one launch (pagerank_multi): vertex v of partition p belongs
+// to component gix[p][v]; component g uses the constant term base[iter * G + g] (its own
+// (1-d)/n_g + d D_g/n_g, a scalar recurrence computed on the host), dn[g] = d/n_g and
+// nf[g] = n_g (FP16 scaling). On the last iteration each vertex adds |r' - r| to res[g].
+struct MultiArgs {
+  const uint32_t* gix[2];
+  const void* base;   // [iters][G] in the accumulation type
+  const void* dn;     // [G]
+  const void* nf;     // [G]
+  double* res;        // [G]
+  uint32_t G;
+  int last;           // this launch is the last iteration
 };
 
 template <class XT> struct XConv;
@@ -130,14 +173,27 @@ template <> struct Consts<double> {
 };
 
 // Update of a vertex with degree deg > 0 from its neighbour sum and its previous rank ro;
-// returns |r' - r|.
-template <class PR>
+// returns |r' - r| (MULTI: adds it to its component's residual on the last iteration and
+// returns 0).
+template <class PR, bool MULTI>
 __device__ __forceinline__ typename PR::AT update_vertex(const PrSide& S, const PrArgs& A,
+                                                         const MultiArgs& M, int p, int iter,
                                                          uint32_t v, typename PR::AT sum,
                                                          int deg, typename PR::AT ro) {
   using AT = typename PR::AT;
   using RT = typename PR::RT;
   using C = Consts<AT>;
+  if (MULTI) {
+    const uint32_t g = M.gix[p][v];
+    const AT base = ((const AT*)M.base)[(size_t)iter * M.G + g];
+    const AT rn = PR::SCALED ? base + ((const AT*)M.dn)[g] * sum : base + C::d(A) * sum;
+    ((RT*)S.r)[v] = (RT)rn;
+    typename PR::XT* xn = (typename PR::XT*)S.xn;
+    if (PR::SCALED) XConv<typename PR::XT>::store(xn + v, (rn * ((const AT*)M.nf)[g]) / (AT)deg);
+    else XConv<typename PR::XT>::store(xn + v, rn / (AT)deg);
+    if (M.last) atomicAdd(M.res + g, (double)(rn > ro ? rn - ro : ro - rn));
+    return (AT)0;
+  }
   const AT rn = PR::SCALED ? C::base(A) + C::d_over_n(A) * sum : C::base(A) + C::d(A) * sum;
   ((RT*)S.r)[v] = (RT)rn;
   typename PR::XT* xn = (typename PR::XT*)S.xn;
@@ -283,10 +339,10 @@ __host__ __device__ constexpr size_t smem_bytes() {
   return ranks_offset<PR>() + sizeof(typename PR::RT) * (kTileV + 8);
 }
 
-template <class PR>
+template <class PR, bool MULTI>
 __global__ void __launch_bounds__(kThreads)
 k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs A, int iter,
-             int dangling) {
+             int dangling, const __grid_constant__ MultiArgs M) {
   using AT = typename PR::AT;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sE = reinterpret_cast<uint32_t*>(smem);
@@ -343,7 +399,8 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
       }
       const AT sum = block_sum<AT>(s, red);
       if (threadIdx.x == 0 && ok2)
-        res += update_vertex<PR>(S, A, d.v0, sum, (int)(d.e1 - d.e0), (AT)((const RT*)S.r)[d.v0]);
+        res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0, sum, (int)(d.e1 - d.e0),
+                                        (AT)((const RT*)S.r)[d.v0]);
     } else if (d.kind == kItemLeaf) {
       const int cnt = (int)(d.e1 - d.e0);
       const uint32_t* src = sE + d.eshift;
@@ -382,17 +439,22 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
         }
         s = group_sum(s, gs);
         if (j < nvt && gl == 0)
-          res += update_vertex<PR>(S, A, d.v0 + j, s, ee - es, (AT)sR[d.rshift + j]);
+          res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, s, ee - es,
+                                          (AT)sR[d.rshift + j]);
       }
     } else {
       // Degree-zero vertices: the rank is the constant term, the contribution zero.
       const typename PR::RT b = (typename PR::RT)Consts<AT>::base(A);
       for (uint32_t v = d.v0 + threadIdx.x; v < d.v1; v += kThreads) {
-        ((typename PR::RT*)S.r)[v] = b;
+        ((typename PR::RT*)S.r)[v] =
+            MULTI ? (typename PR::RT)((const AT*)M.base)[(size_t)iter * M.G + M.gix[d.part][v]]
+                  : b;
         XConv<typename PR::XT>::store((typename PR::XT*)S.xn + v, (AT)0);
       }
     }
   }
+  // Components keep no global scalars: their constants come from the host's table.
+  if (MULTI) return;
   // Residual partial of this block; the last block adds all of them in block order.
   res = block_sum<AT>(res, red);
   if (threadIdx.x == 0) {
@@ -440,15 +502,17 @@ __global__ void k_pr_publish(const __grid_constant__ PrArgs A) {
   ((XT*)S.ghost)[j] = ((const XT*)Q.x)[S.P.outbox[j]];
 }
 
-template <class PR>
-__global__ void k_pr_init(const __grid_constant__ PrArgs A, uint32_t nv0, uint32_t ntot) {
+template <class PR, bool MULTI>
+__global__ void k_pr_init(const __grid_constant__ PrArgs A, uint32_t nv0, uint32_t ntot,
+                          const __grid_constant__ MultiArgs M) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntot) return;
   const int p = i < nv0 ? 0 : 1;
   const uint32_t v = p == 0 ? i : i - nv0;
   const PrSide& S = A.side[p];
   using AT = typename PR::AT;
-  const AT r0 = (AT)(1.0 / A.n);
+  // r_0 = 1/n (MULTI: 1/n_g of the vertex's component)
+  const AT r0 = MULTI ? (AT)(1.0 / (double)((const AT*)M.nf)[M.gix[p][v]]) : (AT)(1.0 / A.n);
   ((typename PR::RT*)S.r)[v] = (typename PR::RT)r0;
   const int deg = (int)(S.P.off[v + 1] - S.P.off[v]);
   typename PR::XT* x = (typename PR::XT*)S.x;
@@ -501,11 +565,12 @@ PrPlan make_plan(graph* g) {
   return pl;
 }
 
-template <class PR>
+template <class PR, bool MULTI>
 graph_status prepare_kernel() {
   static bool done = false;
   if (!done) {
-    GG_CUDA(cudaFuncSetAttribute(k_pr_compute<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GG_CUDA(cudaFuncSetAttribute(k_pr_compute<PR, MULTI>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes<PR>()));
     done = true;
   }
@@ -581,7 +646,7 @@ template <class PR>
 graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* stats) {
   cudaStream_t st = g->stream;
   const PrPlan pl = make_plan(g);
-  GG_TRY(prepare_kernel<PR>());
+  GG_TRY((prepare_kernel<PR, false>()));
   GG_TRY(ensure_ws(g, at.precision, at.max_iter, std::max<uint32_t>(pl.nitems, 1)));
   PrWs* w = g->pr;
   PhaseTimer timer;
@@ -592,7 +657,7 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   GG_CUDA(cudaMemsetAsync(w->done.p, 0, sizeof(uint32_t), st));
   {
     PrArgs A = make_args(g, cur, at.damping);
-    k_pr_init<PR><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n);
+    k_pr_init<PR, false><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, MultiArgs{});
     GG_CUDA(cudaGetLastError());
     // D_0 = (number of degree-zero vertices) / n; degree-zero vertices start at 1/n.
     const double D0 = at.dangling ? A.nzero / (double)g->n : 0.0;
@@ -613,7 +678,9 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     timer.mark(2);
     if (nout) k_pr_publish<typename PR::XT><<<grid_for(nout, 256), 256, 0, st>>>(A);
     timer.mark(1);
-    if (pl.nitems) k_pr_compute<PR><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling);
+    if (pl.nitems)
+      k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
+                                                                 MultiArgs{});
     timer.mark(0);
     launches += (nout ? 1 : 0) + (pl.nitems ? 1 : 0);
     GG_CUDA(cudaGetLastError());
@@ -654,6 +721,237 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   return s;
 }
 
+// ---------------------------------------------------------------------------------------
+// pagerank_multi: components given as global-id ranges [vbase[c], vbase[c+1]).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t component_of(const uint32_t* vbase, uint32_t G, uint32_t v) {
+  uint32_t lo = 0, hi = G;  // vbase[lo] <= v < vbase[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (vbase[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One warp per vertex u (grid stride): every neighbour must lie in u's component; counts
+// the degree-zero vertices of each component. bad != 0 if an edge crosses components.
+__global__ void k_multi_validate(const int64_t* off, const uint32_t* col, uint32_t n,
+                                 const uint32_t* vbase, uint32_t G, uint32_t* nzero, int* bad) {
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t u = w0; u < n; u += nw) {
+    const uint32_t c = component_of(vbase, G, u);
+    const uint32_t lo = vbase[c], hi = vbase[c + 1];
+    const int64_t e0 = off[u], e1 = off[u + 1];
+    if (e0 == e1) {
+      if (lane_id() == 0) atomicAdd(nzero + c, 1u);
+      continue;
+    }
+    bool out = false;
+    for (int64_t e = e0 + lane_id(); e < e1; e += 32) {
+      const uint32_t x = col[e];
+      out |= x < lo || x >= hi;
+    }
+    if (__any_sync(kFull, out) && lane_id() == 0) atomicOr(bad, 1);
+  }
+}
+
+__global__ void k_multi_gix(const uint32_t* l2g, uint32_t nv, const uint32_t* vbase, uint32_t G,
+                            uint32_t* gix) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) gix[v] = component_of(vbase, G, l2g[v]);
+}
+
+// Validates the component layout (once per layout and workspace) and builds the
+// per-vertex component ids.
+graph_status prepare_multi(graph* g, PrWs* w, uint32_t G, const uint32_t* vbase) {
+  if (!w->multi) w->multi = new MultiWs();
+  MultiWs* m = w->multi;
+  if (m->vbase.size() == (size_t)G + 1 && memcmp(m->vbase.data(), vbase, 4ull * (G + 1)) == 0)
+    return GRAPH_OK;
+  cudaStream_t st = g->stream;
+  m->vbase.clear();
+  m->nzero.assign(G, 0);
+  if (m->exec) {
+    cudaGraphExecDestroy(m->exec);
+    m->exec = nullptr;
+    m->iters = 0;
+  }
+  DevBuf* old[] = {&m->dvbase, &m->dnzero, &m->gix[0], &m->gix[1], &m->dn, &m->nf, &m->res};
+  for (DevBuf* b : old) dfree(g, *b);
+  GG_TRY(dalloc(g, m->dvbase, 4ull * (G + 1)));
+  GG_TRY(dalloc(g, m->dnzero, 4ull * G));
+  GG_TRY(dalloc(g, m->dn, 8ull * G));
+  GG_TRY(dalloc(g, m->nf, 8ull * G));
+  GG_TRY(dalloc(g, m->res, 8ull * G));
+  for (int p = 0; p < 2; ++p) GG_TRY(dalloc(g, m->gix[p], 4ull * g->part[p].nv));
+  GG_CUDA(cudaMemcpyAsync(m->dvbase.p, vbase, 4ull * (G + 1), cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemsetAsync(m->dnzero.p, 0, 4ull * G, st));
+  GG_CUDA(cudaMemsetAsync(g->err.p, 0, sizeof(int), st));
+  int* bad = (int*)g->err.p;
+  k_multi_validate<<<152 * 8, 256, 0, st>>>((const int64_t*)g->off.p, (const uint32_t*)g->col.p,
+                                            g->n, (const uint32_t*)m->dvbase.p, G,
+                                            (uint32_t*)m->dnzero.p, bad);
+  GG_CUDA(cudaGetLastError());
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    if (P.nv == 0) continue;
+    k_multi_gix<<<grid_for(P.nv, 256), 256, 0, st>>>((const uint32_t*)P.l2g.p, P.nv,
+                                                     (const uint32_t*)m->dvbase.p, G,
+                                                     (uint32_t*)m->gix[p].p);
+    GG_CUDA(cudaGetLastError());
+  }
+  int hbad = 0;
+  GG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaMemcpyAsync(m->nzero.data(), m->dnzero.p, 4ull * G, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  if (hbad) {
+    GG_CUDA(cudaMemsetAsync(g->err.p, 0, sizeof(int), st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    set_error("an edge joins two components of vbase");
+    return GRAPH_EINVAL;
+  }
+  m->vbase.assign(vbase, vbase + G + 1);
+  return GRAPH_OK;
+}
+
+template <class PR>
+graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagerank_attr& at,
+                       double* ranks, double* residuals, graph_stats* stats) {
+  using AT = typename PR::AT;
+  cudaStream_t st = g->stream;
+  const PrPlan pl = make_plan(g);
+  GG_TRY((prepare_kernel<PR, true>()));
+  GG_TRY(ensure_ws(g, at.precision, at.max_iter, std::max<uint32_t>(pl.nitems, 1)));
+  PrWs* w = g->pr;
+  {
+    const graph_status s = prepare_multi(g, w, G, vbase);
+    if (s != GRAPH_OK) {
+      free_multi(g, w);
+      return s;
+    }
+  }
+  MultiWs* m = w->multi;
+  const int K = at.max_iter;
+  // Per-component constants, FP64 on the host. A degree-zero vertex has an empty neighbour
+  // sum, so it holds the constant term base_t itself; the dangling mass is therefore
+  // D_{t+1} = nzero_c base_t and base_{t+1} = (1-d)/n_c + d D_{t+1}/n_c, from D_0 =
+  // nzero_c / n_c (ranks start at 1/n_c).
+  const double d = at.damping;
+  std::vector<AT> hbase((size_t)K * G), hdn(G), hnf(G);
+  std::vector<double> zres(G, 0.0);
+  for (uint32_t c = 0; c < G; ++c) {
+    const double nc = (double)(vbase[c + 1] - vbase[c]);
+    hdn[c] = (AT)(nc > 0 ? d / nc : 0.0);
+    hnf[c] = (AT)nc;
+    if (nc == 0) continue;
+    double D = at.dangling ? m->nzero[c] / nc : 0.0, prev = 1.0 / nc, base = 0;
+    for (int t = 0; t < K; ++t) {
+      base = (1.0 - d) / nc + d * D / nc;
+      hbase[(size_t)t * G + c] = (AT)base;
+      if (t == K - 1) zres[c] = m->nzero[c] * fabs(base - prev);
+      prev = base;
+      D = at.dangling ? m->nzero[c] * base : 0.0;
+    }
+  }
+  const size_t bb = sizeof(AT) * (size_t)K * G;
+  if (m->base_bytes < bb) {
+    dfree(g, m->base);
+    GG_TRY(dalloc(g, m->base, bb));
+    m->base_bytes = bb;
+    if (m->exec) {
+      cudaGraphExecDestroy(m->exec);
+      m->exec = nullptr;
+      m->iters = 0;
+    }
+  }
+  GG_CUDA(cudaMemcpyAsync(m->base.p, hbase.data(), bb, cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemcpyAsync(m->dn.p, hdn.data(), sizeof(AT) * G, cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemcpyAsync(m->nf.p, hnf.data(), sizeof(AT) * G, cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemsetAsync(m->res.p, 0, 8ull * G, st));
+  MultiArgs M;
+  memset(&M, 0, sizeof(M));
+  for (int p = 0; p < 2; ++p) M.gix[p] = (const uint32_t*)m->gix[p].p;
+  M.base = m->base.p;
+  M.dn = m->dn.p;
+  M.nf = m->nf.p;
+  M.res = (double*)m->res.p;
+  M.G = G;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  const uint32_t nv0 = g->part[0].nv;
+  k_pr_init<PR, true><<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, 0, d), nv0, g->n, M);
+  GG_CUDA(cudaGetLastError());
+  timer.mark(2);
+  // The K supersteps (publish + compute) as one CUDA graph, captured on a private stream
+  // and replayed while the layout, the workspace, K and the damping stay the same.
+  const uint32_t nout = g->part[0].nout + g->part[1].nout;
+  const size_t smem = smem_bytes<PR>();
+  if (!m->exec || m->iters != K || m->damping != d || m->dangling != at.dangling) {
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    m->exec = nullptr;
+    if (!m->capture) GG_CUDA(cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking));
+    GG_CUDA(cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal));
+    int cur = 0;
+    for (int it = 0; it < K; ++it) {
+      const PrArgs A = make_args(g, cur, d);
+      M.last = it == K - 1;
+      if (nout) k_pr_publish<typename PR::XT><<<grid_for(nout, 256), 256, 0, m->capture>>>(A);
+      if (pl.nitems)
+        k_pr_compute<PR, true><<<pl.nitems, kThreads, smem, m->capture>>>(pl, A, it,
+                                                                          at.dangling, M);
+      cur = 1 - cur;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(m->capture, &graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "capture of the iterations", __FILE__, __LINE__);
+    const cudaError_t ie = cudaGraphInstantiate(&m->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      m->exec = nullptr;
+      return cuda_fail(ie, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    m->iters = K;
+    m->damping = d;
+    m->dangling = at.dangling;
+  }
+  GG_CUDA(cudaGraphLaunch(m->exec, st));
+  timer.mark(0);
+  double* out = ranks;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 8ull * g->n));
+    out = (double*)g->stage.p;
+  }
+  k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, K & 1, d),
+                                                                     nv0, g->n, out);
+  GG_CUDA(cudaGetLastError());
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
+  std::vector<double> hres(G);
+  GG_CUDA(cudaMemcpyAsync(hres.data(), m->res.p, 8ull * G, cudaMemcpyDeviceToHost, st));
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  double total = 0;
+  for (uint32_t c = 0; c < G; ++c) {
+    hres[c] += zres[c];
+    total += hres[c];
+  }
+  if (residuals) memcpy(residuals, hres.data(), 8ull * G);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = K;
+    stats->edges_traversed = g->m * (int64_t)K;
+    stats->edges_inspected = g->m * (int64_t)K;
+    stats->messages = (int64_t)nout * K;
+    stats->residual = total;
+    stats->launches = 2 + (int64_t)K * ((nout ? 1 : 0) + (pl.nitems ? 1 : 0));
+  }
+  timer.finish(stats);
+  return s;
+}
+
 }  // namespace
 }  // namespace gg
 
@@ -680,6 +978,43 @@ extern "C" graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* 
     case GRAPH_PR_FP32: return run<PrecF32>(g, at, ranks, stats);
     case GRAPH_PR_FP64: return run<PrecF64>(g, at, ranks, stats);
     case GRAPH_PR_FP16: return run<PrecF16>(g, at, ranks, stats);
+    default:
+      set_error("bad precision %d", at.precision);
+      return GRAPH_EINVAL;
+  }
+}
+
+extern "C" graph_status pagerank_multi(graph_t* g, uint32_t ngraphs, const uint32_t* vbase,
+                                       const pagerank_attr* attr, double* ranks,
+                                       double* residuals, graph_stats* stats) {
+  if (!g || !attr || !ranks || !vbase || ngraphs == 0) {
+    set_error("graph, vbase, attr or ranks is NULL, or ngraphs is 0");
+    return GRAPH_EINVAL;
+  }
+  if (vbase[0] != 0 || vbase[ngraphs] != g->n) {
+    set_error("vbase must start at 0 and end at n = %u", g->n);
+    return GRAPH_EINVAL;
+  }
+  for (uint32_t c = 0; c < ngraphs; ++c)
+    if (vbase[c + 1] < vbase[c]) {
+      set_error("vbase decreases at %u", c);
+      return GRAPH_EINVAL;
+    }
+  const pagerank_attr at = *attr;
+  if (!(at.damping >= 0.0 && at.damping <= 1.0) || at.max_iter < 1 || at.tol != 0.0 ||
+      (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) ||
+      (at.dangling != 0 && at.dangling != 1)) {
+    set_error("bad pagerank_multi attributes (tol must be 0: fixed iteration count)");
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before pagerank_multi");
+    return GRAPH_ESTATE;
+  }
+  switch (at.precision) {
+    case GRAPH_PR_FP32: return run_multi<PrecF32>(g, ngraphs, vbase, at, ranks, residuals, stats);
+    case GRAPH_PR_FP64: return run_multi<PrecF64>(g, ngraphs, vbase, at, ranks, residuals, stats);
+    case GRAPH_PR_FP16: return run_multi<PrecF16>(g, ngraphs, vbase, at, ranks, residuals, stats);
     default:
       set_error("bad precision %d", at.precision);
       return GRAPH_EINVAL;

@@ -168,6 +168,45 @@ def random_assignment(n: int, share0: float, seed: int) -> np.ndarray:
     return out[:n]
 
 
+def rmat_family(count: int, scales=(10, 17), edge_factors=(8, 32), seed: int = 7,
+                threads: int = 0) -> list:
+    """`count` independent RMAT graphs (Table 2 parameters) whose scale and edge factor are
+    drawn uniformly from the inclusive ranges by a seeded generator; graph i uses RMAT seed
+    seed * 1000 + i. The recipe of each graph records its draw."""
+    rng = np.random.default_rng(seed)
+    sc = rng.integers(scales[0], scales[1] + 1, size=count)
+    ef = rng.integers(edge_factors[0], edge_factors[1] + 1, size=count)
+    return [rmat(int(sc[i]), int(ef[i]), seed=seed * 1000 + i, threads=threads)
+            for i in range(count)]
+
+
+def disjoint_union(graphs) -> tuple:
+    """Block-diagonal union: vertex v of graph i becomes vbase[i] + v. Returns the union
+    (weights concatenated when every graph has them) and vbase (uint32, len + 1)."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    ms = np.array([g.m for g in graphs], dtype=np.int64)
+    vbase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    vbase[1:] = np.cumsum(ns)
+    ebase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    ebase[1:] = np.cumsum(ms)
+    if vbase[-1] >= 2**31:
+        raise ValueError("union too large for 31-bit vertex ids")
+    off = np.empty(int(vbase[-1]) + 1, dtype=np.int64)
+    cols = np.empty(int(ebase[-1]), dtype=np.uint32)
+    weighted = all(g.weights is not None for g in graphs) and len(graphs) > 0
+    w = np.empty(int(ebase[-1]), dtype=np.uint32) if weighted else None
+    for i, g in enumerate(graphs):
+        v0, e0 = int(vbase[i]), int(ebase[i])
+        off[v0:v0 + g.n] = np.asarray(g.offsets[:-1]) + e0
+        cols[e0:e0 + g.m] = np.asarray(g.cols[:g.m]) + np.uint32(v0)
+        if weighted:
+            w[e0:e0 + g.m] = g.weights[:g.m]
+    off[-1] = ebase[-1]
+    u = Csr(int(vbase[-1]), off, cols, w,
+            dict(generator="disjoint_union", parts=[g.recipe for g in graphs]))
+    return u, vbase.astype(np.uint32)
+
+
 # ---- small structured graphs used by closed-form tests (plain constructions) -------------
 
 def from_edges(n: int, edges, symmetric: bool = True, w=None) -> Csr:

@@ -150,3 +150,25 @@ def test_rmat25_bfs_batch(gpu, rmat25, loaded25):
         ref, _ = oracle.bfs(g.n, g.offsets, g.cols, int(srcs[row]), want_parents=False)
         assert np.array_equal(gpu.as_numpy_u32(lv[row]), ref), f"row {row}"
     del lv
+
+
+def test_many_graph_pagerank_256_uneven_rmat(gpu):
+    """The batching workload at full size: 256 RMAT graphs, scales 10-17, edge factors 8-32,
+    30 FP32 iterations in one pagerank_multi call; the smallest, the largest and four more
+    components against the oracle run on that graph alone, and every component's ranks
+    summing to one."""
+    fam = synth.rmat_family(256, scales=(10, 17), edge_factors=(8, 32), seed=7)
+    U, vb = synth.disjoint_union(fam)
+    H = gpu.graph_load_csr(U.offsets, U.cols)
+    gpu.graph_partition(H, "degree", degree_threshold=256)
+    r, res, st = gpu.pagerank_multi(H, vb, max_iter=30, precision="fp32", out="host")
+    sums = np.add.reduceat(r, vb[:-1].astype(np.int64))
+    assert np.all(np.abs(sums - 1.0) <= 1e-5)
+    ms = np.array([g.m for g in fam])
+    pick = {int(np.argmin(ms)), int(np.argmax(ms)), 3, 77, 150, 255}
+    for i in sorted(pick):
+        g = fam[i]
+        ref, rres, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=30)
+        assert np.abs(r[vb[i]:vb[i + 1]] - ref).sum() <= 1e-6, f"component {i}"
+        assert abs(res[i] - rres[-1]) <= 2e-6
+    H.free()
