@@ -16,7 +16,8 @@ dominant kernel, the CPU oracle baseline and the end-to-end number (host result 
 device-to-host copies inside the timed region) are added to the same JSON line, and so is
 a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one, and
 PageRank of 256 uneven RMAT graphs in one union (pagerank_multi, iterations replayed as a
-CUDA graph) timed against one pagerank() call per graph.
+CUDA graph) timed against one pagerank() call per graph, and the query server (continuous
+batching of BFS and SSSP queries on a resident RMAT-23 graph) under Poisson arrivals.
 
 `--impl reference` times the CPU oracle (the reference arm) on the same
 workload and prints the same kind of line.
@@ -61,6 +62,9 @@ def parse():
                     help="time the threshold candidates even if the cache has this graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the query-server (continuous batching) measurement")
+    ap.add_argument("--serve-scale", type=int, default=23)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched BFS and many-graph PageRank measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
@@ -95,6 +99,96 @@ def recorded_traffic(profile, source, threshold):
         if line.startswith("traffic_bytes_per_launch:"):
             return int(line.split(":")[1])
     return None
+
+
+def serving_bench(G, a, torch):
+    """Query server on a resident RMAT graph (scale 23, weights 1..64): Poisson arrivals of
+    70% BFS / 30% SSSP queries from seeded random non-isolated sources, at rates swept as
+    multiples of the plain form's capacity (one bfs() / sssp() call after another);
+    latency = completion - submission on the server's clock."""
+    import synth
+    t = time.perf_counter()
+    g = synth.rmat(a.serve_scale, 16, seed=1)
+    synth.weights(g, 64, seed=3)
+    gen_s = time.perf_counter() - t
+    H = G.graph_load_csr(g.offsets, g.cols, g.weights)
+    G.graph_partition(H, "degree", degree_threshold=2048)
+    srcs = synth.sources(g, 4096, seed=5)
+    rng = np.random.default_rng(11)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    # plain form: the same kind of queries one call at a time
+    plain = []
+    G.bfs(H, int(srcs[0]), out, want_parents=False)
+    G.sssp(H, int(srcs[0]), out)
+    for i in range(100):
+        s = int(srcs[rng.integers(len(srcs))])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if rng.random() < 0.7:
+            G.bfs(H, s, out, want_parents=False)
+        else:
+            G.sssp(H, s, out)
+        torch.cuda.synchronize()
+        plain.append((time.perf_counter() - t) * 1e3)
+    plain_qps = 1e3 * len(plain) / sum(plain)
+    nbuf = 400
+    bufs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)]
+    points = []
+    with G.Server(H, out="device") as srv:
+        info0 = srv.info()
+        for i in range(64):  # warm-up
+            srv.submit("bfs" if i % 3 else "sssp", int(srcs[i]), bufs[i])
+        got = 0
+        while got < 64:
+            got += len(srv.poll(cap=256, wait_ms=50))
+        for mult in (0.5, 1, 2, 4, 8, 16):
+            rate = plain_qps * mult
+            N = int(min(nbuf, max(100, rate * 1.5)))
+            gaps = rng.exponential(1.0 / rate, size=N)
+            kinds = np.where(rng.random(N) < 0.7, "bfs", "sssp")
+            picks = srcs[rng.integers(len(srcs), size=N)]
+            arrive = np.cumsum(gaps)
+
+            def submitter():
+                t0 = time.perf_counter()
+                for i in range(N):
+                    while time.perf_counter() - t0 < arrive[i]:
+                        pass
+                    srv.submit(str(kinds[i]), int(picks[i]), bufs[i])
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            done = []
+            while len(done) < N:
+                done += srv.poll(cap=512, wait_ms=20)
+            th.join()
+            lat = np.array([c["t_done_ms"] - c["t_submit_ms"] for c in done])
+            lb = np.array([c["t_done_ms"] - c["t_submit_ms"] for c in done if c["kind"] == "bfs"])
+            ls = np.array([c["t_done_ms"] - c["t_submit_ms"] for c in done if c["kind"] == "sssp"])
+            span = max(c["t_done_ms"] for c in done) - min(c["t_submit_ms"] for c in done)
+            bad = sum(1 for c in done if c["status"] != 0)
+            points.append({"offered_qps": round(rate, 1), "queries": N,
+                           "achieved_qps": round(1e3 * N / span, 1),
+                           "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                           "bfs_p50_ms": round(float(np.percentile(lb, 50)), 3) if len(lb) else None,
+                           "sssp_p50_ms": round(float(np.percentile(ls, 50)), 3) if len(ls) else None,
+                           "errors": bad})
+        info = srv.info()
+    H.free()
+    best = max(p["achieved_qps"] for p in points)
+    return {"graph": f"rmat{a.serve_scale}-ef16 w1..64", "n": g.n, "m": g.m,
+            "mix": "70% BFS / 30% SSSP, Poisson arrivals", "plain_qps": round(plain_qps, 1),
+            "plain_p50_ms": round(float(np.percentile(plain, 50)), 3),
+            "plain_p99_ms": round(float(np.percentile(plain, 99)), 3),
+            "best_achieved_qps": best, "vs_plain": round(best / plain_qps, 2),
+            "points": points, "bfs_lanes": info["bfs_lanes"],
+            "sssp_slots": info["sssp_slots"], "max_lanes_busy": info["max_lanes_busy"],
+            "max_slots_busy": info["max_slots_busy"],
+            "bytes_lanes": info0["bytes_lanes"], "bytes_per_sssp": info0["bytes_per_sssp"],
+            "generate_s": round(gen_s, 2),
+            "note": "graph_server (continuous batching: BFS lanes join and leave between "
+                    "supersteps; SSSP jobs on their own streams); device outputs"}
 
 
 def workload_name(a):
@@ -482,6 +576,8 @@ def main():
                     "note": "pagerank_multi (iterations replayed as one CUDA graph) vs one "
                             "pagerank() call per graph; FP32, device ranks, best of 3 / 2"}
 
+    serving = None if a.no_serve else serving_bench(G, a, torch)
+
     # End to end through the public API with pinned host result buffers.
     e2e = None
     if not a.no_e2e:
@@ -546,6 +642,7 @@ def main():
         "e2e": e2e,
         "batch_bfs": batch,
         "batch_pagerank": batch_pr,
+        "serving": serving,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),

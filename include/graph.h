@@ -291,6 +291,72 @@ graph_status pagerank_multi(graph_t* g, uint32_t ngraphs, const uint32_t* vbase,
                             graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * Query server -- continuous batching of BFS and SSSP queries on one resident graph. The
+ * paper runs one algorithm at a time (Section 4.1); a server keeps the partitioned graph
+ * resident and runs many queries at once, each advancing one BSP superstep at a time:
+ *  - BFS queries take bit lanes of one resident multi-source search (as in bfs_batch): a
+ *    query joins at the next superstep boundary on a free lane and leaves when a superstep
+ *    adds no vertex to its search, so queries enter and leave while others run.
+ *  - SSSP queries each run on an SSSP job with its own workspace and stream; up to
+ *    sssp_slots jobs run at once, their supersteps overlapping on the device.
+ *  - Admission is by device memory: at creation the server sizes the lanes and the job
+ *    slots to mem_budget (per-query state: bfs_lanes_bytes once, sssp_job_bytes per
+ *    slot) and allocates them; a query waits in FIFO order until a lane or a slot is free.
+ * A worker thread inside the library issues all device work (nothing is allocated after
+ * creation); results are exactly those of bfs() levels / sssp() distances for the source.
+ * While a server exists the graph handle must not be used by other calls, re-partitioned
+ * or freed.
+ * ------------------------------------------------------------------------------------- */
+typedef struct graph_server graph_server_t;
+
+#define GRAPH_QUERY_BFS 0
+#define GRAPH_QUERY_SSSP 1
+
+typedef struct {
+  uint64_t mem_budget; /* bytes for per-query state; 0: half of the free device memory */
+  uint32_t bfs_lanes;  /* BFS lanes, 1..64 (0: 64) */
+  uint32_t max_sssp;   /* upper bound on SSSP slots (0: 64); the budget may allow fewer */
+  int out_mem;         /* GRAPH_MEM_HOST (pinned recommended) or _DEVICE for outputs */
+} graph_server_attr;
+
+typedef struct {
+  uint64_t ticket;     /* as returned by graph_server_submit */
+  int kind;            /* GRAPH_QUERY_* */
+  int status;          /* GRAPH_OK or the query's error */
+  uint32_t source;
+  int supersteps;      /* supersteps the query took part in */
+  double t_submit_ms;  /* times since the server's creation (host steady clock) */
+  double t_admit_ms;   /* lane or slot assigned, device work issued */
+  double t_done_ms;    /* result complete in the output array */
+} graph_completion;
+
+typedef struct {
+  uint32_t bfs_lanes, sssp_slots;
+  uint64_t bytes_lanes, bytes_per_sssp, mem_budget;
+  uint64_t submitted, completed, pending;
+  uint32_t max_lanes_busy, max_slots_busy; /* peak concurrency seen */
+  uint64_t bfs_supersteps;                  /* supersteps of the lane search */
+} graph_server_info;
+
+/* Creates a server on g (loaded, partitioned; SSSP slots need weights, else 0 slots).
+ * Errors: EINVAL, ESTATE, ENOMEM (not even one lane set or slot fits), ECUDA. */
+graph_status graph_server_create(graph_t* g, const graph_server_attr* attr,
+                                 graph_server_t** out);
+/* Queues a query; out receives n uint32 (levels or distances, global order, INF
+ * unreached) in the memory kind of attr.out_mem and must stay valid until the query's
+ * completion is returned. Never blocks on the device. Errors: EINVAL (kind, source >= n,
+ * NULL out, SSSP without slots). */
+graph_status graph_server_submit(graph_server_t* s, int kind, uint32_t source, uint32_t* out,
+                                 uint64_t* ticket);
+/* Moves up to cap completions (oldest first) into done; *count receives how many. Waits up
+ * to wait_ms milliseconds for the first one when none is ready (0: no wait). */
+graph_status graph_server_poll(graph_server_t* s, graph_completion* done, uint32_t cap,
+                               uint32_t* count, int wait_ms);
+graph_status graph_server_info_get(graph_server_t* s, graph_server_info* info);
+/* Finishes every queued and running query, then frees the server's device memory. */
+graph_status graph_server_destroy(graph_server_t* s);
+
+/* ---------------------------------------------------------------------------------------
  * bfs_csr_noalloc -- breadth-first search for callers that cannot allocate device memory.
  * The paper has no counterpart: this entry point exists for code that must not call
  * cudaMalloc at search time (host callbacks and driver hooks where allocation is forbidden

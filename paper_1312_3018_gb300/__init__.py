@@ -19,7 +19,7 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "pagerank_multi", "bfs_csr_noalloc",
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
            "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
@@ -280,6 +280,68 @@ def pagerank_multi(g: Graph, vbase, *, damping: float = 0.85, max_iter: int = 30
                                     res.ctypes.data, C.byref(stats))
     _lib.check(st, "pagerank_multi")
     return ranks, res, stats.as_dict()
+
+
+class Server:
+    """Continuous-batching query server on a resident, partitioned graph (graph_server_*):
+    BFS queries share the lanes of one multi-source search, SSSP queries run on job slots
+    sized by a device-memory budget. Outputs are caller arrays of n uint32 (host: numpy,
+    pinned for speed; device: torch tensors) kept alive here until their query completes."""
+
+    KINDS = {"bfs": _lib.GRAPH_QUERY_BFS, "sssp": _lib.GRAPH_QUERY_SSSP}
+
+    def __init__(self, g: Graph, *, mem_budget: int = 0, bfs_lanes: int = 0, max_sssp: int = 0,
+                 out: str = "device"):
+        _torch()
+        self.g = g
+        self.out = out
+        mem = GRAPH_MEM_DEVICE if out == "device" else GRAPH_MEM_HOST
+        attr = _lib.graph_server_attr(int(mem_budget), int(bfs_lanes), int(max_sssp), mem)
+        h = C.c_void_p(0)
+        _lib.check(_lib.load().graph_server_create(g.handle, C.byref(attr), C.byref(h)),
+                   "graph_server_create")
+        self.handle = h.value
+        self._outs = {}
+
+    def submit(self, kind: str, source: int, out) -> int:
+        ptr, mem = _ptr(out)
+        if mem != (GRAPH_MEM_DEVICE if self.out == "device" else GRAPH_MEM_HOST):
+            raise ValueError("output array in the wrong memory for this server")
+        t = C.c_uint64(0)
+        _lib.check(_lib.load().graph_server_submit(self.handle, self.KINDS[kind], int(source),
+                                                   ptr, C.byref(t)), "graph_server_submit")
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, cap: int = 256, wait_ms: int = 0) -> list:
+        buf = (_lib.graph_completion * cap)()
+        k = C.c_uint32(0)
+        _lib.check(_lib.load().graph_server_poll(self.handle, buf, cap, C.byref(k), int(wait_ms)),
+                   "graph_server_poll")
+        res = []
+        for c in buf[:k.value]:
+            d = {f: getattr(c, f) for f, _ in c._fields_}
+            d["kind"] = "bfs" if c.kind == _lib.GRAPH_QUERY_BFS else "sssp"
+            d["out"] = self._outs.pop(c.ticket, None)
+            res.append(d)
+        return res
+
+    def info(self) -> dict:
+        i = _lib.graph_server_info()
+        _lib.check(_lib.load().graph_server_info_get(self.handle, C.byref(i)),
+                   "graph_server_info_get")
+        return i.as_dict()
+
+    def close(self):
+        if self.handle:
+            _lib.check(_lib.load().graph_server_destroy(self.handle), "graph_server_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def bfs_csr_noalloc(offsets, cols, source: int, levels=None, parents=None, *, stream=None,

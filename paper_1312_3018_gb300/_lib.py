@@ -31,6 +31,8 @@ GRAPH_PR_FP64 = 1
 GRAPH_PR_FP16 = 2
 GRAPH_NOALLOC_MAX_VERTICES = 1 << 21
 GRAPH_BATCH_MAX = 64
+GRAPH_QUERY_BFS = 0
+GRAPH_QUERY_SSSP = 1
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -50,6 +52,29 @@ class graph_partition_info(C.Structure):
     _fields_ = [("n", C.c_uint32), ("m", C.c_int64), ("threshold", C.c_uint32),
                 ("nv", C.c_uint32 * 2), ("ne", C.c_int64 * 2), ("nout", C.c_uint32 * 2),
                 ("cls_end", (C.c_uint32 * 34) * 2), ("bytes_graph", C.c_int64)]
+
+
+class graph_server_attr(C.Structure):
+    _fields_ = [("mem_budget", C.c_uint64), ("bfs_lanes", C.c_uint32), ("max_sssp", C.c_uint32),
+                ("out_mem", C.c_int)]
+
+
+class graph_completion(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("kind", C.c_int), ("status", C.c_int),
+                ("source", C.c_uint32), ("supersteps", C.c_int), ("t_submit_ms", C.c_double),
+                ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
+class graph_server_info(C.Structure):
+    _fields_ = [("bfs_lanes", C.c_uint32), ("sssp_slots", C.c_uint32),
+                ("bytes_lanes", C.c_uint64), ("bytes_per_sssp", C.c_uint64),
+                ("mem_budget", C.c_uint64), ("submitted", C.c_uint64),
+                ("completed", C.c_uint64), ("pending", C.c_uint64),
+                ("max_lanes_busy", C.c_uint32), ("max_slots_busy", C.c_uint32),
+                ("bfs_supersteps", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class graph_stats(C.Structure):
@@ -94,6 +119,12 @@ SIGNATURES = {
     "pagerank_multi": (_int, [_vp, _u32, _vp, C.POINTER(pagerank_attr), _vp, _vp,
                               C.POINTER(graph_stats)]),
     "bfs_csr_noalloc": (_int, [_u32, _i64, _vp, _vp, _u32, _vp, _vp, _vp]),
+    "graph_server_create": (_int, [_vp, C.POINTER(graph_server_attr), C.POINTER(_vp)]),
+    "graph_server_submit": (_int, [_vp, _int, _u32, _vp, C.POINTER(C.c_uint64)]),
+    "graph_server_poll": (_int, [_vp, C.POINTER(graph_completion), _u32, C.POINTER(_u32),
+                                 _int]),
+    "graph_server_info_get": (_int, [_vp, C.POINTER(graph_server_info)]),
+    "graph_server_destroy": (_int, [_vp]),
     "graph_free": (None, [_vp]),
     "graph_strerror": (C.c_char_p, [_int]),
     "graph_last_error": (C.c_char_p, []),

@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     if force or jobs or _stale(LIB, objs):
         libdir = cuda_lib_dir()
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB + ".tmp"] + objs + [
-            "-L" + libdir, "-Xlinker", "-rpath=" + libdir]
+            "-L" + libdir, "-Xlinker", "-rpath=" + libdir, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "jobs.cuh"
 
 namespace gg {
 
@@ -34,6 +35,7 @@ struct MsCounters {
   u64 traversed;  // sum over new (vertex, search) pairs of the vertex degree
   u64 inspected;  // edge entries read by the compute phase
   u64 messages;   // outbox slots delivered by the exchange
+  u64 gained;     // searches (bits) that reached a new vertex this level
 };
 
 struct MsWs {
@@ -78,20 +80,25 @@ struct MsSources {
 };
 
 struct Cnt {
-  u64 nf = 0, mf = 0, mu = 0, trav = 0, insp = 0, msg = 0;
+  u64 nf = 0, mf = 0, mu = 0, trav = 0, insp = 0, msg = 0, gained = 0;
 };
 
 __device__ void flush(const Cnt& c, MsCounters* ctr) {
-  __shared__ u64 s[6];
-  if (threadIdx.x < 6) s[threadIdx.x] = 0;
+  __shared__ u64 s[7];
+  if (threadIdx.x < 7) s[threadIdx.x] = 0;
   __syncthreads();
   const u64 v[6] = {warp_sum(c.nf), warp_sum(c.mf), warp_sum(c.mu), warp_sum(c.trav),
                     warp_sum(c.insp), warp_sum(c.msg)};
-  if (lane_id() == 0)
+  const u64 gor = ((u64)__reduce_or_sync(kFull, (unsigned)(c.gained >> 32)) << 32) |
+                  __reduce_or_sync(kFull, (unsigned)c.gained);
+  if (lane_id() == 0) {
     for (int j = 0; j < 6; ++j)
       if (v[j]) atomicAdd(&s[j], v[j]);
+    if (gor) atomicOr(&s[6], gor);
+  }
   __syncthreads();
   if (threadIdx.x < 6 && s[threadIdx.x]) atomicAdd(&((u64*)ctr)[threadIdx.x], s[threadIdx.x]);
+  if (threadIdx.x == 6 && s[6]) atomicOr(&ctr->gained, s[6]);
 }
 
 // OR within aligned groups of 2^gshift lanes (gshift <= 5); all 32 lanes must call.
@@ -290,6 +297,7 @@ __global__ void __launch_bounds__(256) k_ms_advance(const __grid_constant__ MsAr
         c.nf++;
         c.mf += (u64)deg;
         c.trav += (u64)deg * (u64)__popcll(nx);
+        c.gained |= nx;
       }
       if (deg > 0 && sm != A.full) c.mu += (u64)deg;
     }
@@ -350,10 +358,54 @@ __global__ void k_ms_collect(const __grid_constant__ MsArgs A, uint32_t n, uint3
   }
 }
 
-graph_status alloc_ws(graph* g, uint32_t K) {
-  if (!g->ms) {
-    MsWs* w = new MsWs();
-    g->ms = w;
+// Lanes joining at level L: search `lane[t]` starts from `src[t]` (its level counts from L).
+struct MsSeeds {
+  uint32_t lane[GRAPH_BATCH_MAX];
+  uint32_t src[GRAPH_BATCH_MAX];
+  uint32_t count;
+};
+
+__global__ void k_ms_seed(const __grid_constant__ MsArgs A, const __grid_constant__ MsSeeds S,
+                          const uint32_t* g2l) {
+  const uint32_t t = threadIdx.x;
+  if (t >= S.count) return;
+  const uint32_t gl = g2l[S.src[t]];
+  const MsSide& P = A.side[gl >> 31];
+  const uint32_t lid = gl & kIdMask;
+  const u64 bit = 1ull << S.lane[t];
+  atomicOr(&P.seen[lid], bit);
+  atomicOr(&P.front[lid], bit);
+  P.lvl[(size_t)lid * A.K + S.lane[t]] = A.L;
+}
+
+// Levels of the finished lanes F (relative to each lane's start level) into their output
+// arrays in global order; the lanes' seen bits are cleared so that the lanes can take new
+// searches.
+struct MsLaneOut {
+  uint32_t* out[GRAPH_BATCH_MAX];
+  uint32_t start[GRAPH_BATCH_MAX];
+  u64 F;
+};
+
+__global__ void k_ms_lane_collect(const __grid_constant__ MsArgs A,
+                                  const __grid_constant__ MsLaneOut O, uint32_t n,
+                                  const uint32_t* g2l) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const uint32_t gl = g2l[g];
+  const MsSide& S = A.side[gl >> 31];
+  const uint32_t lid = gl & kIdMask;
+  const u64 sm = S.seen[lid];
+  const uint32_t* row = S.lvl + (size_t)lid * A.K;
+  for (u64 f = O.F; f; f &= f - 1) {
+    const int l = __ffsll((long long)f) - 1;
+    O.out[l][g] = ((sm >> l) & 1ull) ? row[l] - O.start[l] : kInf;
+  }
+  if (sm & O.F) S.seen[lid] = sm & ~O.F;
+}
+
+graph_status alloc_ms_into(graph* g, MsWs* w, uint32_t K) {
+  if (!w->seen[0].p) {
     for (int p = 0; p < 2; ++p) {
       const Part& P = g->part[p];
       GG_TRY(dalloc(g, w->seen[p], 8ull * P.nv));
@@ -363,7 +415,6 @@ graph_status alloc_ws(graph* g, uint32_t K) {
       GG_TRY(dalloc(g, w->omsg[p], 8ull * P.nout));
     }
   }
-  MsWs* w = g->ms;
   if (w->K < K) {
     w->K = 0;
     for (int p = 0; p < 2; ++p) {
@@ -372,6 +423,21 @@ graph_status alloc_ws(graph* g, uint32_t K) {
     }
     w->K = K;
   }
+  return GRAPH_OK;
+}
+
+void free_ms_buffers(graph* g, MsWs* w) {
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->seen[p], &w->mask[p][0], &w->mask[p][1], &w->lvl[p], &w->ghost[p],
+                     &w->omsg[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  w->K = 0;
+}
+
+graph_status alloc_ws(graph* g, uint32_t K) {
+  if (!g->ms) g->ms = new MsWs();
+  GG_TRY(alloc_ms_into(g, g->ms, K));
   if (g->counters.bytes < sizeof(MsCounters) || !g->counters.p) {
     dfree(g, g->counters);
     GG_TRY(dalloc(g, g->counters, 1024));
@@ -386,8 +452,7 @@ graph_status ensure_ws(graph* g, uint32_t K) {
   return s;
 }
 
-MsArgs make_args(graph* g, int cur, uint32_t k, uint32_t L) {
-  MsWs* w = g->ms;
+MsArgs make_args_ws(graph* g, MsWs* w, MsCounters* ctr, int cur, u64 full, uint32_t L) {
   MsArgs A;
   memset(&A, 0, sizeof(A));
   for (int p = 0; p < 2; ++p) {
@@ -400,14 +465,239 @@ MsArgs make_args(graph* g, int cur, uint32_t k, uint32_t L) {
     S.omsg = (u64*)w->omsg[p].p;
     S.lvl = (uint32_t*)w->lvl[p].p;
   }
-  A.ctr = (MsCounters*)g->counters.p;
-  A.full = k == 64 ? ~0ull : ((1ull << k) - 1);
+  A.ctr = ctr;
+  A.full = full;
   A.K = w->K;
   A.L = L;
   return A;
 }
 
+u64 lanes_mask(uint32_t k) { return k >= 64 ? ~0ull : ((1ull << k) - 1); }
+
+MsArgs make_args(graph* g, int cur, uint32_t k, uint32_t L) {
+  return make_args_ws(g, g->ms, (MsCounters*)g->counters.p, cur, lanes_mask(k), L);
+}
+
+// Both directions walk the same dense plan: hub chunks, then buckets 1..3 of each part.
+Plan make_plan(graph* g) {
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+  }
+  return pl;
+}
+
+constexpr unsigned kSweepGrid = 152 * 8;
+
+// One superstep (compute, communication, advance) with A's counters cleared first.
+graph_status launch_superstep(graph* g, const MsArgs& A, const Plan& pl, bool pull,
+                              cudaStream_t st, PhaseTimer* timer, int64_t* launches) {
+  const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
+  const uint64_t nvt = (uint64_t)g->part[0].nv + g->part[1].nv;
+  GG_CUDA(cudaMemsetAsync(A.ctr, 0, sizeof(MsCounters), st));
+  if (timer) timer->mark(2);
+  if (!pull) {
+    if (pl.nblocks) k_ms_push<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+    GG_CUDA(cudaGetLastError());
+    if (timer) timer->mark(0);
+    if (nout) k_ms_exchange<<<kSweepGrid, kThreads, 0, st>>>(A);
+    GG_CUDA(cudaGetLastError());
+    if (timer) timer->mark(1);
+  } else {
+    if (nout) k_ms_publish<<<kSweepGrid, 256, 0, st>>>(A);
+    GG_CUDA(cudaGetLastError());
+    if (timer) timer->mark(1);
+    if (pl.nblocks) k_ms_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+    GG_CUDA(cudaGetLastError());
+    if (timer) timer->mark(0);
+  }
+  k_ms_advance<<<grid_for(nvt, 256) < kSweepGrid ? grid_for(nvt, 256) : kSweepGrid, 256, 0,
+                 st>>>(A);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(2);
+  *launches += (pl.nblocks ? 1 : 0) + (nout ? 1 : 0) + 1;
+  return GRAPH_OK;
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// BFS lanes for the query server: the 64-lane search above kept resident, lanes joining at
+// any superstep boundary (continuous batching) and leaving when their search ends.
+// ---------------------------------------------------------------------------------------
+struct BfsLanes {
+  MsWs ws;
+  DevBuf ctr;                 // MsCounters (device)
+  MsCounters* hc = nullptr;   // pinned mirror
+  DevBuf stage;               // nlanes x n uint32: results for host destinations
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  Plan plan;
+  uint32_t nlanes = 0;
+  int cur = 0;
+  uint32_t L = 0;             // supersteps issued so far (the level clock)
+  bool in_flight = false;
+  bool have_counts = false;
+  u64 active = 0;             // lanes holding a search
+  u64 pending = 0;            // admitted, not yet seeded
+  u64 stepped = 0;            // lanes that took part in the superstep in flight
+  u64 mf = 0, mu = 0;         // last superstep: next frontier's edges, unreached edges
+  uint32_t src[GRAPH_BATCH_MAX] = {};
+  uint32_t start[GRAPH_BATCH_MAX] = {};
+  uint32_t* dst[GRAPH_BATCH_MAX] = {};
+  int dst_mem[GRAPH_BATCH_MAX] = {};
+};
+
+size_t bfs_lanes_bytes(const graph* g, uint32_t nlanes) {
+  const size_t K = (nlanes + 3) & ~3u;
+  size_t b = 1024 + 4ull * g->n * nlanes;
+  for (int p = 0; p < 2; ++p) b += (24 + 4 * K) * (size_t)g->part[p].nv + 16ull * g->part[p].nout;
+  return b;
+}
+
+void bfs_lanes_destroy(graph* g, BfsLanes* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  free_ms_buffers(g, &b->ws);
+  dfree(g, b->ctr);
+  dfree(g, b->stage);
+  if (b->hc) cudaFreeHost(b->hc);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+static graph_status lanes_alloc(graph* g, BfsLanes* b) {
+  GG_TRY(alloc_ms_into(g, &b->ws, (b->nlanes + 3) & ~3u));
+  GG_TRY(dalloc(g, b->ctr, 1024));
+  GG_TRY(dalloc(g, b->stage, 4ull * g->n * b->nlanes));
+  GG_CUDA(cudaMallocHost(&b->hc, sizeof(MsCounters)));
+  GG_CUDA(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+  GG_CUDA(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+  for (int p = 0; p < 2; ++p) {
+    GG_CUDA(cudaMemsetAsync(b->ws.seen[p].p, 0, 8ull * g->part[p].nv, b->st));
+    GG_CUDA(cudaMemsetAsync(b->ws.mask[p][0].p, 0, 8ull * g->part[p].nv, b->st));
+    GG_CUDA(cudaMemsetAsync(b->ws.mask[p][1].p, 0, 8ull * g->part[p].nv, b->st));
+    GG_CUDA(cudaMemsetAsync(b->ws.omsg[p].p, 0, 8ull * g->part[p].nout, b->st));
+  }
+  GG_CUDA(cudaStreamSynchronize(b->st));
+  b->plan = make_plan(g);
+  return GRAPH_OK;
+}
+
+graph_status bfs_lanes_create(graph* g, uint32_t nlanes, BfsLanes** out) {
+  if (nlanes < 1 || nlanes > GRAPH_BATCH_MAX) {
+    set_error("lanes %u outside 1..%u", nlanes, GRAPH_BATCH_MAX);
+    return GRAPH_EINVAL;
+  }
+  BfsLanes* b = new BfsLanes();
+  b->nlanes = nlanes;
+  const graph_status s = lanes_alloc(g, b);
+  if (s != GRAPH_OK) {
+    bfs_lanes_destroy(g, b);
+    return s;
+  }
+  *out = b;
+  return GRAPH_OK;
+}
+
+uint64_t bfs_lanes_free(const BfsLanes* b) { return lanes_mask(b->nlanes) & ~b->active; }
+
+bool bfs_lanes_busy(const BfsLanes* b) { return b->in_flight; }
+
+graph_status bfs_lanes_admit(BfsLanes* b, int lane, uint32_t source, uint32_t* dst,
+                             int dst_mem) {
+  const u64 bit = 1ull << lane;
+  if (b->in_flight || lane < 0 || lane >= (int)b->nlanes || (b->active & bit)) {
+    set_error("lane %d cannot be admitted now", lane);
+    return GRAPH_ESTATE;
+  }
+  b->active |= bit;
+  b->pending |= bit;
+  b->src[lane] = source;
+  b->dst[lane] = dst;
+  b->dst_mem[lane] = dst_mem;
+  return GRAPH_OK;
+}
+
+graph_status bfs_lanes_launch(graph* g, BfsLanes* b) {
+  if (b->in_flight || !b->active) return GRAPH_OK;
+  if (b->pending) {
+    MsSeeds S;
+    memset(&S, 0, sizeof(S));
+    for (u64 f = b->pending; f; f &= f - 1) {
+      const int l = __builtin_ctzll(f);
+      S.lane[S.count] = (uint32_t)l;
+      S.src[S.count] = b->src[l];
+      S.count++;
+      b->start[l] = b->L;
+    }
+    const MsArgs A0 = make_args_ws(g, &b->ws, (MsCounters*)b->ctr.p, b->cur, b->active, b->L);
+    k_ms_seed<<<1, GRAPH_BATCH_MAX, 0, b->st>>>(A0, S, (const uint32_t*)g->g2l.p);
+    GG_CUDA(cudaGetLastError());
+    b->pending = 0;
+  }
+  // Beamer's rule on the last superstep's counts (pull when the frontier's edges, weighted
+  // by alpha = 15, exceed the edges of vertices some search has not reached).
+  const bool pull = b->have_counts && (double)b->mf * 15.0 > (double)b->mu;
+  const MsArgs A = make_args_ws(g, &b->ws, (MsCounters*)b->ctr.p, b->cur, b->active, b->L);
+  int64_t launches = 0;
+  GG_TRY(launch_superstep(g, A, b->plan, pull, b->st, nullptr, &launches));
+  GG_CUDA(cudaMemcpyAsync(b->hc, b->ctr.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, b->st));
+  GG_CUDA(cudaEventRecord(b->ev, b->st));
+  b->stepped = b->active;
+  b->in_flight = true;
+  return GRAPH_OK;
+}
+
+int bfs_lanes_poll(graph* g, BfsLanes* b, uint64_t* finished, int* steps,
+                   cudaEvent_t done_ev) {
+  *finished = 0;
+  if (!b->in_flight) return 0;
+  const cudaError_t q = cudaEventQuery(b->ev);
+  if (q == cudaErrorNotReady) return 0;
+  if (q != cudaSuccess) return cuda_fail(q, "bfs lanes event", __FILE__, __LINE__);
+  b->in_flight = false;
+  b->cur = 1 - b->cur;
+  b->L++;
+  b->mf = b->hc->mf;
+  b->mu = b->hc->mu;
+  b->have_counts = true;
+  const u64 fin = b->stepped & ~b->hc->gained;
+  if (fin) {
+    MsLaneOut O;
+    memset(&O, 0, sizeof(O));
+    O.F = fin;
+    for (u64 f = fin; f; f &= f - 1) {
+      const int l = __builtin_ctzll(f);
+      O.out[l] = b->dst_mem[l] == GRAPH_MEM_DEVICE ? b->dst[l]
+                                                   : (uint32_t*)b->stage.p + (size_t)l * g->n;
+      O.start[l] = b->start[l];
+      steps[l] = (int)(b->L - b->start[l]);
+    }
+    const MsArgs A = make_args_ws(g, &b->ws, (MsCounters*)b->ctr.p, b->cur, b->active, b->L);
+    k_ms_lane_collect<<<grid_for(g->n, 256), 256, 0, b->st>>>(A, O, g->n,
+                                                              (const uint32_t*)g->g2l.p);
+    GG_CUDA(cudaGetLastError());
+    for (u64 f = fin; f; f &= f - 1) {
+      const int l = __builtin_ctzll(f);
+      if (b->dst_mem[l] != GRAPH_MEM_DEVICE)
+        GG_CUDA(cudaMemcpyAsync(b->dst[l], O.out[l], 4ull * g->n, cudaMemcpyDeviceToHost,
+                                b->st));
+    }
+    GG_CUDA(cudaEventRecord(done_ev, b->st));
+    b->active &= ~fin;
+    if (!b->active) b->have_counts = false;
+  }
+  *finished = fin;
+  return 1;
+}
+
 }  // namespace gg
 
 using namespace gg;
@@ -466,19 +756,7 @@ extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t 
   GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
   GG_CUDA(cudaStreamSynchronize(st));
   timer.mark(2);
-  // Both directions walk the same dense plan: hub chunks, then buckets 1..3 of each part.
-  Plan pl;
-  memset(&pl, 0, sizeof(pl));
-  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
-  for (int p = 0; p < 2; ++p) {
-    const PartView V = g->part[p].view();
-    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
-    for (int b = 1; b < kNBucket; ++b)
-      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
-  }
-  const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
-  const uint64_t nvt = (uint64_t)g->part[0].nv + g->part[1].nv;
-  const unsigned sweep_grid = 152 * 8;
+  const Plan pl = make_plan(g);
   int64_t traversed = (int64_t)hc->traversed, inspected = 0, messages = 0, launches = 1;
   int push_steps = 0, pull_steps = 0;
   uint64_t mu = (uint64_t)g->m;
@@ -496,33 +774,10 @@ extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t 
     if (at.direction == GRAPH_BFS_TOPDOWN) pull = false;
     else if (at.direction == GRAPH_BFS_BOTTOMUP) pull = L > 0;
     else pull = L > 0 && (double)c.mf * alpha > (double)mu;
-    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(MsCounters), st));
     const MsArgs A = make_args(g, cur, k, (uint32_t)L);
-    timer.mark(2);
-    if (!pull) {
-      if (pl.nblocks) k_ms_push<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
-      GG_CUDA(cudaGetLastError());
-      timer.mark(0);
-      if (nout) k_ms_exchange<<<sweep_grid, kThreads, 0, st>>>(A);
-      GG_CUDA(cudaGetLastError());
-      timer.mark(1);
-      launches += (pl.nblocks ? 1 : 0) + (nout ? 1 : 0);
-      push_steps++;
-    } else {
-      if (nout) k_ms_publish<<<sweep_grid, 256, 0, st>>>(A);
-      GG_CUDA(cudaGetLastError());
-      timer.mark(1);
-      if (pl.nblocks) k_ms_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
-      GG_CUDA(cudaGetLastError());
-      timer.mark(0);
-      launches += (pl.nblocks ? 1 : 0) + (nout ? 1 : 0);
-      pull_steps++;
-    }
-    k_ms_advance<<<grid_for(nvt, 256) < sweep_grid ? grid_for(nvt, 256) : sweep_grid, 256, 0,
-                   st>>>(A);
-    GG_CUDA(cudaGetLastError());
-    launches++;
-    timer.mark(2);
+    GG_TRY(launch_superstep(g, A, pl, pull, st, &timer, &launches));
+    if (pull) pull_steps++;
+    else push_steps++;
     GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;

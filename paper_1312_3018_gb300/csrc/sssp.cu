@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "jobs.cuh"
 
 namespace gg {
 
@@ -271,10 +272,7 @@ __global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t nv0,
   if (lane_id() == 0 && d) atomicAdd(reached_degree, d);
 }
 
-graph_status alloc_ws(graph* g) {
-  if (g->sssp) return GRAPH_OK;
-  SsspWs* w = new SsspWs();
-  g->sssp = w;
+graph_status alloc_ws_into(graph* g, SsspWs* w) {
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
     // bitmap words rounded to whole warps (the filter assigns one lane per word)
@@ -290,6 +288,23 @@ graph_status alloc_ws(graph* g) {
     GG_TRY(dalloc(g, w->omsg[p], 4ull * P.nout));
     GG_TRY(dalloc(g, w->odirty[p], 4 * w->owords[p]));
   }
+  return GRAPH_OK;
+}
+
+void free_ws_buffers(graph* g, SsspWs* w) {
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->touched[p], &w->queue[p][0],
+                     &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1], &w->omsg[p],
+                     &w->odirty[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+}
+
+graph_status alloc_ws(graph* g) {
+  if (g->sssp) return GRAPH_OK;
+  SsspWs* w = new SsspWs();
+  g->sssp = w;
+  GG_TRY(alloc_ws_into(g, w));
   if (g->counters.bytes < sizeof(SsspCounters) || !g->counters.p) {
     dfree(g, g->counters);
     GG_TRY(dalloc(g, g->counters, 1024));
@@ -304,8 +319,7 @@ graph_status ensure_ws(graph* g) {
   return s;
 }
 
-SsspArgs make_args(graph* g, int cur) {
-  SsspWs* w = g->sssp;
+SsspArgs make_args(graph* g, SsspWs* w, SsspCounters* ctr, int cur) {
   SsspArgs A;
   memset(&A, 0, sizeof(A));
   for (int p = 0; p < 2; ++p) {
@@ -319,11 +333,211 @@ SsspArgs make_args(graph* g, int cur) {
     S.omsg = (uint32_t*)w->omsg[p].p;
     S.odirty = (uint32_t*)w->odirty[p].p;
   }
-  A.ctr = (SsspCounters*)g->counters.p;
+  A.ctr = ctr;
   return A;
 }
 
+// Resets a workspace and seeds the source (round 0's active set).
+graph_status launch_start(graph* g, SsspWs* w, SsspCounters* ctr, uint32_t source,
+                          cudaStream_t st) {
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->touched[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * P.nout, st));
+    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
+  }
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
+  const SsspArgs A = make_args(g, w, ctr, 0);
+  k_sssp_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
+                               (uint32_t*)w->queue[0][0].p, (uint32_t*)w->queue[1][0].p,
+                               (uint32_t*)w->hubq[0][0].p, (uint32_t*)w->hubq[1][0].p);
+  GG_CUDA(cudaGetLastError());
+  return GRAPH_OK;
+}
+
+uint64_t active_count(const SsspCounters& c) {
+  uint64_t a = 0;
+  for (int p = 0; p < 2; ++p)
+    for (int b = 0; b < kNBucket; ++b) a += c.tail[p][b];
+  return a;
+}
+
+// One round: relax the active set c describes (queues `cur`), apply the outbox, filter.
+graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCounters& c,
+                          int cur, cudaStream_t st, PhaseTimer* timer, int64_t* launches) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
+  const SsspArgs A = make_args(g, w, ctr, cur);
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);  // chunks
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
+               gsh[b], b);
+  }
+  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  if (timer) timer->mark(2);
+  if (pl.nblocks) k_sssp_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(0);
+  if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(1);
+  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(0);
+  *launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+  return GRAPH_OK;
+}
+
+// Distances in global order into out (device) and the reached-degree / clamped reduction
+// into ctr.
+graph_status launch_collect(graph* g, SsspWs* w, SsspCounters* ctr, int cur, uint32_t* out,
+                            cudaStream_t st) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
+  const SsspArgs A = make_args(g, w, ctr, cur);
+  k_sssp_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, out,
+                                                       &ctr->reached_degree, &ctr->clamped);
+  GG_CUDA(cudaGetLastError());
+  return GRAPH_OK;
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Stepwise SSSP jobs for the query server: the same rounds as sssp(), issued one at a time
+// on the job's own stream and advanced when the round's event has completed.
+// ---------------------------------------------------------------------------------------
+struct SsspJob {
+  SsspWs ws;
+  DevBuf ctr;                  // SsspCounters (device)
+  SsspCounters* hc = nullptr;  // pinned mirror
+  DevBuf stage;                // result staging for host destinations
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint32_t* dst = nullptr;
+  int dst_mem = 0;
+  int cur = 0;
+  int phase = 0;               // 0 idle, 1 round in flight, 2 collect in flight
+  int64_t rounds = 0;
+  bool overflow = false;
+};
+
+size_t sssp_job_bytes(const graph* g) {
+  size_t b = 1024 + 4ull * g->n;
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    const size_t words = ((P.nv + 31) / 32 + 31) & ~(size_t)31;
+    const size_t owords = ((P.nout + 31) / 32 + 31) & ~(size_t)31;
+    b += 16ull * P.nv + 4 * words + 8ull * P.nchunk + 4ull * P.nout + 4 * owords;
+  }
+  return b;
+}
+
+void sssp_job_destroy(graph* g, SsspJob* j) {
+  if (!j) return;
+  if (j->st) cudaStreamSynchronize(j->st);
+  free_ws_buffers(g, &j->ws);
+  dfree(g, j->ctr);
+  dfree(g, j->stage);
+  if (j->hc) cudaFreeHost(j->hc);
+  if (j->ev) cudaEventDestroy(j->ev);
+  if (j->st) cudaStreamDestroy(j->st);
+  delete j;
+}
+
+static graph_status job_alloc(graph* g, SsspJob* j) {
+  GG_TRY(alloc_ws_into(g, &j->ws));
+  GG_TRY(dalloc(g, j->ctr, 1024));
+  GG_TRY(dalloc(g, j->stage, 4ull * g->n));
+  GG_CUDA(cudaMallocHost(&j->hc, sizeof(SsspCounters)));
+  GG_CUDA(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
+  GG_CUDA(cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming));
+  return GRAPH_OK;
+}
+
+graph_status sssp_job_create(graph* g, SsspJob** out) {
+  SsspJob* j = new SsspJob();
+  const graph_status s = job_alloc(g, j);
+  if (s != GRAPH_OK) {
+    sssp_job_destroy(g, j);
+    return s;
+  }
+  *out = j;
+  return GRAPH_OK;
+}
+
+graph_status sssp_job_start(graph* g, SsspJob* j, uint32_t source, uint32_t* dst,
+                            int dst_mem) {
+  j->dst = dst;
+  j->dst_mem = dst_mem;
+  j->cur = 0;
+  j->rounds = 0;
+  j->overflow = false;
+  SsspCounters* dc = (SsspCounters*)j->ctr.p;
+  GG_TRY(launch_start(g, &j->ws, dc, source, j->st));
+  GG_CUDA(cudaMemcpyAsync(j->hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, j->st));
+  GG_CUDA(cudaEventRecord(j->ev, j->st));
+  j->phase = 1;
+  return GRAPH_OK;
+}
+
+static int job_fail(SsspJob* j, graph_status s) {
+  j->phase = 0;
+  return s;
+}
+
+int sssp_job_poll(graph* g, SsspJob* j, int* rounds) {
+  if (j->phase == 0) return 0;
+  const cudaError_t q = cudaEventQuery(j->ev);
+  if (q == cudaErrorNotReady) return 0;
+  if (q != cudaSuccess) return job_fail(j, cuda_fail(q, "sssp job event", __FILE__, __LINE__));
+  if (rounds) *rounds = (int)j->rounds;
+  SsspCounters* dc = (SsspCounters*)j->ctr.p;
+  if (j->phase == 2) {
+    j->phase = 0;
+    if (j->overflow && j->hc->clamped) {
+      set_error("a shortest distance reached 2^32 - 1");
+      return GRAPH_ERANGE;
+    }
+    return 1;
+  }
+  const SsspCounters c = *j->hc;
+  j->overflow |= c.overflow != 0;
+  if (active_count(c) == 0) {
+    uint32_t* out = j->dst_mem == GRAPH_MEM_DEVICE ? j->dst : (uint32_t*)j->stage.p;
+    graph_status s = launch_collect(g, &j->ws, dc, j->cur, out, j->st);
+    if (s != GRAPH_OK) return job_fail(j, s);
+    cudaError_t e = cudaSuccess;
+    if (j->dst_mem != GRAPH_MEM_DEVICE)
+      e = cudaMemcpyAsync(j->dst, out, 4ull * g->n, cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(j->hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+    if (e != cudaSuccess) return job_fail(j, cuda_fail(e, "sssp job collect", __FILE__, __LINE__));
+    j->phase = 2;
+    return 0;
+  }
+  if (j->rounds >= (int64_t)g->n + 1) {
+    set_error("sssp job reached the superstep cap");
+    return job_fail(j, GRAPH_ETIMEOUT);
+  }
+  int64_t launches = 0;
+  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches);
+  if (s != GRAPH_OK) return job_fail(j, s);
+  cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, j->st);
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+  if (e != cudaSuccess) return job_fail(j, cuda_fail(e, "sssp job round", __FILE__, __LINE__));
+  j->cur = 1 - j->cur;
+  j->rounds++;
+  return 0;
+}
+
 }  // namespace gg
 
 using namespace gg;
@@ -357,70 +571,29 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
   GG_TRY(ensure_ws(g));
   SsspWs* w = g->sssp;
   cudaStream_t st = g->stream;
+  SsspCounters* dc = (SsspCounters*)g->counters.p;
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
-  for (int p = 0; p < 2; ++p) {
-    const Part& P = g->part[p];
-    GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * P.nv, st));
-    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * P.nv, st));
-    GG_CUDA(cudaMemsetAsync(w->touched[p].p, 0, 4 * w->words[p], st));
-    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * P.nout, st));
-    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
-  }
-  GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(SsspCounters), st));
-  int cur = 0;
-  {
-    SsspArgs A = make_args(g, cur);
-    k_sssp_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
-                                 (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p,
-                                 (uint32_t*)w->hubq[0][cur].p, (uint32_t*)w->hubq[1][cur].p);
-    GG_CUDA(cudaGetLastError());
-  }
+  GG_TRY(launch_start(g, w, dc, source, st));
   SsspCounters* hc = (SsspCounters*)g->host_counters;
-  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
   GG_CUDA(cudaStreamSynchronize(st));
   timer.mark(2);
   int64_t inspected = 0, messages = 0, launches = 1;
   bool overflow = false;
   int64_t rounds = 0;
-  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
-  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  int cur = 0;
   for (;; ++rounds) {
-    SsspCounters c = *hc;
-    uint64_t active = 0;
-    for (int p = 0; p < 2; ++p)
-      for (int b = 0; b < kNBucket; ++b) active += c.tail[p][b];
-    if (active == 0) break;
+    const SsspCounters c = *hc;
+    if (active_count(c) == 0) break;
     if (rounds >= cap) {
       set_error("sssp reached the superstep cap (%lld)", (long long)cap);
       timer.finish(nullptr);
       return GRAPH_ETIMEOUT;
     }
-    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(SsspCounters), st));
-    SsspArgs A = make_args(g, cur);
-    Plan pl;
-    memset(&pl, 0, sizeof(pl));
-    const int gsh[kNBucket] = {8, 5, kSubShift, 0};
-    for (int p = 0; p < 2; ++p) {
-      const PartView V = g->part[p].view();
-      plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);  // chunks
-      for (int b = 1; b < kNBucket; ++b)
-        plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
-                 gsh[b], b);
-    }
-    timer.mark(2);
-    if (pl.nblocks) k_sssp_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(0);
-    if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(1);
-    k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(0);
-    launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
-    GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches));
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;
     messages += (int64_t)hc->messages;
@@ -432,15 +605,8 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
     GG_TRY(ensure_stage(g, 4ull * g->n + 64));
     dd = (uint32_t*)g->stage.p;
   }
-  SsspCounters* dc = (SsspCounters*)g->counters.p;
-  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SsspCounters), st));
-  {
-    SsspArgs A = make_args(g, cur);
-    k_sssp_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, dd,
-                                                         &dc->reached_degree, &dc->clamped);
-    GG_CUDA(cudaGetLastError());
-    launches++;
-  }
+  GG_TRY(launch_collect(g, w, dc, cur, dd, st));
+  launches++;
   if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
   timer.mark(2);
