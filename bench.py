@@ -62,6 +62,8 @@ def parse():
                     help="time the threshold candidates even if the cache has this graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the PageRank error report against the FP64 oracle")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the query-server (continuous batching) measurement")
     ap.add_argument("--serve-scale", type=int, default=23)
@@ -99,6 +101,30 @@ def recorded_traffic(profile, source, threshold):
         if line.startswith("traffic_bytes_per_launch:"):
             return int(line.split(":")[1])
     return None
+
+
+def precision_report(G, H, g, iters_oracle=3, iters_step=20):
+    """PageRank error per precision: L1 and max-abs against the FP64 oracle after
+    iters_oracle iterations (the oracle is single-threaded, so a few iterations bound its
+    time), and after the step's iters_step iterations against the GPU's FP64 run (which the
+    tests hold to 1e-12 of the oracle)."""
+    import oracle
+    t = time.perf_counter()
+    ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=iters_oracle)
+    ts = time.perf_counter() - t
+    rep = {"vs_oracle": {"iterations": iters_oracle, "oracle_s": round(ts, 1)},
+           "vs_gpu_fp64": {"iterations": iters_step}}
+    for prec in ("fp64", "fp32", "fp16"):
+        r, _ = G.pagerank(H, max_iter=iters_oracle, precision=prec, out="host")
+        d = np.abs(r - ref)
+        rep["vs_oracle"][prec] = {"l1": float(d.sum()), "max_abs": float(d.max())}
+    r64, _ = G.pagerank(H, max_iter=iters_step, precision="fp64", out="host")
+    for prec in ("fp32", "fp16"):
+        r, _ = G.pagerank(H, max_iter=iters_step, precision=prec, out="host")
+        d = np.abs(r - r64)
+        rep["vs_gpu_fp64"][prec] = {"l1": float(d.sum()), "max_abs": float(d.max())}
+    rep["target"] = "FP32 L1 <= 1e-6 against FP64; FP16 reported without a target"
+    return rep
 
 
 def serving_bench(G, a, torch):
@@ -604,6 +630,7 @@ def main():
 
     if rank != 0:
         return
+    precision = None if a.no_precision else precision_report(G, H, g, iters_step=a.pr_iters)
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(g, srcs[0], a.cpu_budget_s)
@@ -643,6 +670,7 @@ def main():
         "batch_bfs": batch,
         "batch_pagerank": batch_pr,
         "serving": serving,
+        "pagerank_precision": precision,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),
