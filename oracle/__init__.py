@@ -1,7 +1,8 @@
 """CPU oracle -- TEST INFRASTRUCTURE ONLY.
 
 Python access to ``oracle.c``: plain, single-threaded reference computations of BFS
-levels, shortest-path distances, FP64 PageRank and the two-way partition, plus validators.
+levels, shortest-path distances, FP64 PageRank, the two-way partition, betweenness
+centrality and connected components, plus validators.
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg (and its
 ``--impl reference`` arm) may import this package. The CUDA library never calls it, and it
 shares no code with the CUDA sources; the two meet only in the seeded inputs of ``synth``.
@@ -57,6 +58,10 @@ def _configure(lib):
     lib.orc_check_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
     lib.orc_traversed.restype = i64
     lib.orc_traversed.argtypes = [u32, vp, vp]
+    lib.orc_bc.restype = i32
+    lib.orc_bc.argtypes = [u32, vp, vp, u32, vp, vp, vp]
+    lib.orc_cc.restype = i32
+    lib.orc_cc.argtypes = [u32, vp, vp, vp]
     return lib
 
 
@@ -192,3 +197,26 @@ def edge_share_threshold(offsets, share):
     # that prefix's last degree joins (ties included).
     k = min(int(np.searchsorted(csum, need, side="left")), len(ds) - 1)
     return int(ds[k])
+
+
+def bc(n, offsets, cols, sources):
+    """FP64 betweenness scores summed over the sources (Brandes), and the TEPS numerator
+    (twice the degree sum of the reached vertices, per source)."""
+    off, col = _c(offsets, np.int64), _c(cols, np.uint32)
+    src = _c(sources, np.uint32)
+    out = np.zeros(max(n, 1), np.float64)
+    trav = ctypes.c_int64(0)
+    rc = _load().orc_bc(n, _p(off), _p(col), len(src), _p(src), _p(out), ctypes.addressof(trav))
+    if rc:
+        raise OracleError(f"orc_bc rc={rc}")
+    return out[:n], trav.value
+
+
+def cc(n, offsets, cols):
+    """Component label of every vertex: the smallest vertex id of its component."""
+    off, col = _c(offsets, np.int64), _c(cols, np.uint32)
+    out = np.empty(max(n, 1), np.uint32)
+    rc = _load().orc_cc(n, _p(off), _p(col), _p(out))
+    if rc:
+        raise OracleError(f"orc_cc rc={rc}")
+    return out[:n]

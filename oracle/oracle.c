@@ -36,6 +36,16 @@
  *   orc_check_sssp     Optimality certificate for shortest-path distances.
  *   orc_traversed      TEPS numerator of Section 5: sum of the degrees of the vertices
  *                      that were reached.
+ *   orc_bc             Betweenness centrality summed over a list of sources, Section 7.2
+ *                      and Figure 18 (Brandes' algorithm, the paper's reference [Brandes
+ *                      2001]): a BFS counts the shortest paths sigma from the source, then
+ *                      vertices in reverse BFS order accumulate the dependency
+ *                      delta(v) = sum over successors w (neighbours one level further) of
+ *                      sigma(v) / sigma(w) * (1 + delta(w)), and every vertex other than the
+ *                      source adds delta(v) to its score. FP64 throughout.
+ *   orc_cc             Connected components (Section 9.4): every vertex labelled with the
+ *                      smallest vertex id of its component, found by a BFS from each
+ *                      still unlabelled vertex in increasing id order.
  *
  * Graph format: CSR with int64 offsets[n+1] and uint32 cols[m]; optional uint32 weights.
  * INF is 0xFFFFFFFF for levels, parents and distances.
@@ -440,4 +450,94 @@ int64_t orc_traversed(uint32_t n, const int64_t* off, const uint32_t* value) {
   for (uint32_t v = 0; v < n; ++v)
     if (value[v] != ORC_INF) s += off[v + 1] - off[v];
   return s;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Betweenness centrality (Brandes)                                                      */
+/* ------------------------------------------------------------------------------------ */
+
+/* bc[v] += sum over the sources s of delta_s(v) for v != s; traversed (optional) receives
+ * twice the degree sum of the vertices each source reaches (Section 5: forward and
+ * backward phases), summed over the sources. */
+int orc_bc(uint32_t n, const int64_t* off, const uint32_t* col, uint32_t nsrc,
+           const uint32_t* sources, double* bc, int64_t* traversed) {
+  uint32_t* dist = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+  double* sigma = (double*)malloc(sizeof(double) * (n ? n : 1));
+  double* delta = (double*)malloc(sizeof(double) * (n ? n : 1));
+  if (!dist || !order || !sigma || !delta) {
+    free(dist); free(order); free(sigma); free(delta);
+    return ORC_ENOMEM;
+  }
+  for (uint32_t v = 0; v < n; ++v) bc[v] = 0.0;
+  int64_t trav = 0;
+  for (uint32_t k = 0; k < nsrc; ++k) {
+    const uint32_t s = sources[k];
+    if (s >= n) {
+      free(dist); free(order); free(sigma); free(delta);
+      return ORC_EINVAL;
+    }
+    for (uint32_t v = 0; v < n; ++v) {
+      dist[v] = ORC_INF;
+      sigma[v] = 0.0;
+      delta[v] = 0.0;
+    }
+    /* forward: BFS in FIFO order, counting shortest paths */
+    uint32_t head = 0, tail = 0;
+    dist[s] = 0;
+    sigma[s] = 1.0;
+    order[tail++] = s;
+    while (head < tail) {
+      const uint32_t v = order[head++];
+      for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const uint32_t w = col[e];
+        if (dist[w] == ORC_INF) {
+          dist[w] = dist[v] + 1;
+          order[tail++] = w;
+        }
+        if (dist[w] == dist[v] + 1) sigma[w] += sigma[v];
+      }
+    }
+    /* backward: reverse BFS order, so every successor's dependency is final */
+    for (uint32_t i = tail; i-- > 0;) {
+      const uint32_t v = order[i];
+      for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const uint32_t w = col[e];
+        if (dist[w] == dist[v] + 1) delta[v] += sigma[v] / sigma[w] * (1.0 + delta[w]);
+      }
+      if (v != s) bc[v] += delta[v];
+      trav += 2 * (off[v + 1] - off[v]);
+    }
+  }
+  if (traversed) *traversed = trav;
+  free(dist); free(order); free(sigma); free(delta);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Connected components                                                                  */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_cc(uint32_t n, const int64_t* off, const uint32_t* col, uint32_t* label) {
+  uint32_t* queue = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+  if (!queue) return ORC_ENOMEM;
+  for (uint32_t v = 0; v < n; ++v) label[v] = ORC_INF;
+  for (uint32_t r = 0; r < n; ++r) {
+    if (label[r] != ORC_INF) continue;
+    uint32_t head = 0, tail = 0;
+    label[r] = r;
+    queue[tail++] = r;
+    while (head < tail) {
+      const uint32_t v = queue[head++];
+      for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const uint32_t w = col[e];
+        if (label[w] == ORC_INF) {
+          label[w] = r;
+          queue[tail++] = w;
+        }
+      }
+    }
+  }
+  free(queue);
+  return ORC_OK;
 }

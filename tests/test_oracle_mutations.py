@@ -34,6 +34,12 @@ PART_PINS = [lambda: pins.test_partition_is_an_exact_relabelling("deg16"),
 CHECK_PINS = [lambda: pins.test_bfs_validator_rejects_planted_mistakes(),
               lambda: pins.test_bfs_validator_rejects_level_jump_on_a_non_tree_edge(),
               lambda: pins.test_sssp_certificate_rejects_planted_mistakes()]
+BC_PINS = [lambda: pins.test_bc_path_closed_form(6),
+           lambda: pins.test_bc_star_closed_form(9),
+           lambda: pins.test_bc_matches_pair_dependency_definition(0),
+           lambda: pins.test_bc_sum_is_total_interior_length()]
+CC_PINS = [lambda: pins.test_cc_closed_forms(),
+           lambda: pins.test_cc_matches_scipy(12, 2)]
 
 MUTANTS = [
     ("bfs level +2", "level[u] = level[v] + 1;", "level[u] = level[v] + 2;", BFS_PINS),
@@ -65,6 +71,14 @@ MUTANTS = [
     ("bfs validator skips parent edge", "if (!has_edge(off, col, v, p)) return 4;", "",
      CHECK_PINS),
     ("sssp certificate skips tightness", "if (!tight) return 3;", "", CHECK_PINS),
+    ("bc drops the 1 +", "* (1.0 + delta[w]);", "* delta[w];", BC_PINS),
+    ("bc scores the source", "if (v != s) bc[v] += delta[v];", "bc[v] += delta[v];", BC_PINS),
+    ("bc copies sigma", "if (dist[w] == dist[v] + 1) sigma[w] += sigma[v];",
+     "if (dist[w] == dist[v] + 1) sigma[w] = sigma[v];", BC_PINS),
+    ("bc ratio inverted", "delta[v] += sigma[v] / sigma[w]", "delta[v] += sigma[w] / sigma[v]",
+     BC_PINS),
+    ("cc labels by largest id", "for (uint32_t r = 0; r < n; ++r) {\n    if (label[r] != ORC_INF)",
+     "for (uint32_t r = n; r-- > 0;) {\n    if (label[r] != ORC_INF)", CC_PINS),
 ]
 
 

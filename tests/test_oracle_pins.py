@@ -465,3 +465,137 @@ def test_edge_share_threshold_brute_force():
                    if deg[deg >= t].sum() >= share * m)
         assert T == best
     assert oracle.edge_share_threshold(g.offsets, 0.0) == int(deg.max()) + 1
+
+
+# ---------------------------------------------------------------- betweenness centrality
+
+def dense_adjacency(g):
+    A = np.zeros((g.n, g.n), dtype=np.float64)
+    for u in range(g.n):
+        for e in range(g.offsets[u], g.offsets[u + 1]):
+            A[u, int(g.cols[e])] = 1.0
+    return A
+
+
+def path_counts(g):
+    """Distances and numbers of shortest paths for all pairs from powers of the adjacency
+    matrix: d(s,t) is the first k with (A^k)[s,t] > 0, and every walk of that length is a
+    shortest path, so sigma(s,t) = (A^d)[s,t]."""
+    A = dense_adjacency(g)
+    n = g.n
+    d = np.full((n, n), np.inf)
+    sig = np.zeros((n, n))
+    np.fill_diagonal(d, 0)
+    np.fill_diagonal(sig, 1)
+    P = np.eye(n)
+    for k in range(1, n):
+        P = P @ A
+        new = (P > 0) & ~np.isfinite(d)
+        d[new] = k
+        sig[new] = P[new]
+    return d, sig
+
+
+def bc_by_pair_dependencies(g, sources):
+    """Definition of betweenness: BC(v) = sum over sources s and targets t (s, t, v
+    distinct) of sigma(s,v) sigma(v,t) / sigma(s,t) when v lies on a shortest s-t path."""
+    d, sig = path_counts(g)
+    bc = np.zeros(g.n)
+    for s in sources:
+        for t in range(g.n):
+            if t == s or not np.isfinite(d[s, t]):
+                continue
+            for v in range(g.n):
+                if v in (s, t):
+                    continue
+                if d[s, v] + d[v, t] == d[s, t]:
+                    bc[v] += sig[s, v] * sig[v, t] / sig[s, t]
+    return bc
+
+
+@pytest.mark.parametrize("n", [2, 6, 31])
+def test_bc_path_closed_form(n):
+    g = synth.path(n)
+    bc, trav = oracle.bc(g.n, g.offsets, g.cols, np.arange(n))
+    i = np.arange(n)
+    assert np.array_equal(bc, 2.0 * i * (n - 1 - i))
+    assert trav == n * 2 * g.m
+
+
+@pytest.mark.parametrize("k", [1, 2, 9])
+def test_bc_star_closed_form(k):
+    g = synth.star(k)
+    bc, _ = oracle.bc(g.n, g.offsets, g.cols, np.arange(k + 1))
+    assert bc[0] == k * (k - 1) and np.all(bc[1:] == 0)
+    # from the centre alone nothing is between; from one leaf the centre carries k-1
+    assert np.all(oracle.bc(g.n, g.offsets, g.cols, [0])[0] == 0)
+    assert oracle.bc(g.n, g.offsets, g.cols, [1])[0][0] == k - 1
+
+
+def test_bc_complete_graph_is_zero():
+    g = synth.complete(7)
+    assert np.all(oracle.bc(g.n, g.offsets, g.cols, np.arange(7))[0] == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_bc_matches_pair_dependency_definition(seed):
+    rng = np.random.default_rng(seed)
+    n = 11
+    g = synth.erdos_renyi(n, 0.28, seed=seed + 40)
+    srcs = sorted(rng.choice(n, size=4, replace=False).tolist())
+    for S in (srcs, list(range(n))):
+        bc, _ = oracle.bc(g.n, g.offsets, g.cols, S)
+        assert np.allclose(bc, bc_by_pair_dependencies(g, S), rtol=1e-12, atol=1e-12)
+
+
+def test_bc_cycle_and_grid_pair_definition():
+    for g in (synth.cycle(9), synth.cycle(10), synth.grid(4, 3)):
+        bc, _ = oracle.bc(g.n, g.offsets, g.cols, np.arange(g.n))
+        assert np.allclose(bc, bc_by_pair_dependencies(g, range(g.n)), rtol=1e-12)
+
+
+def test_bc_matches_networkx():
+    nx = pytest.importorskip("networkx")
+    g = synth.rmat(9, 8, seed=5)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    for u in range(g.n):
+        for e in range(g.offsets[u], g.offsets[u + 1]):
+            G.add_edge(u, int(g.cols[e]))
+    ref = nx.betweenness_centrality(G, normalized=False)  # unordered pairs
+    bc, _ = oracle.bc(g.n, g.offsets, g.cols, np.arange(g.n))
+    assert np.allclose(bc, 2 * np.array([ref[v] for v in range(g.n)]), rtol=1e-9, atol=1e-9)
+
+
+def test_bc_sum_is_total_interior_length():
+    """Every connected ordered pair (s, t) spreads exactly d(s,t) - 1 over the interior
+    vertices of its shortest paths."""
+    g = synth.rmat(7, 6, seed=8)
+    d = floyd_warshall(g, weighted=False)
+    fin = np.isfinite(d) & (d > 0)
+    bc, _ = oracle.bc(g.n, g.offsets, g.cols, np.arange(g.n))
+    assert abs(bc.sum() - (d[fin] - 1).sum()) <= 1e-9 * max(1.0, bc.sum())
+
+
+# ---------------------------------------------------------------- connected components
+
+def test_cc_closed_forms():
+    parts = [synth.path(5), synth.star(3), synth.from_edges(1, []), synth.cycle(4),
+             synth.from_edges(2, [])]
+    u, vb = synth.disjoint_union(parts)
+    lab = oracle.cc(u.n, u.offsets, u.cols)
+    expect = np.concatenate([np.full(p.n, vb[i]) if i != 4 else vb[i] + np.arange(p.n)
+                             for i, p in enumerate(parts)]).astype(np.uint32)
+    assert np.array_equal(lab, expect)
+
+
+@pytest.mark.parametrize("scale,ef", [(12, 2), (10, 1), (13, 16)])
+def test_cc_matches_scipy(scale, ef):
+    g = synth.rmat(scale, ef, seed=scale)
+    A = sp.csr_matrix((np.ones(g.m), np.asarray(g.cols), np.asarray(g.offsets)),
+                      shape=(g.n, g.n))
+    k, comp = csg.connected_components(A, directed=False)
+    mins = np.full(k, g.n, np.int64)
+    np.minimum.at(mins, comp, np.arange(g.n))
+    lab = oracle.cc(g.n, g.offsets, g.cols)
+    assert np.array_equal(lab, mins[comp].astype(np.uint32))
