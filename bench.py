@@ -602,6 +602,36 @@ def main():
                     "note": "pagerank_multi (iterations replayed as one CUDA graph) vs one "
                             "pagerank() call per graph; FP32, device ranks, best of 3 / 2"}
 
+    # Betweenness (4 of the step's sources) and connected components on the same graph.
+    more = None
+    if not a.no_batch:
+        sc = torch.empty(n, dtype=torch.float64, device="cuda")
+        G.betweenness(H, srcs[:1], sc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, bst = G.betweenness(H, srcs[:4], sc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1)
+        G.connected_components(H, lv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, cst = G.connected_components(H, lv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        del sc
+        more = {"betweenness": {"sources": 4, "ms": round(bms, 3),
+                                "gteps": bst["edges_traversed"] / (bms / 1e3) / 1e9,
+                                "supersteps": bst["supersteps"],
+                                "note": "TEPS numerator: twice the degree sum of the reached "
+                                        "vertices per source (forward + backward)"},
+                "connected_components": {"ms": round(cms, 3), "supersteps": cst["supersteps"],
+                                         "gedges_per_s": m / (cms / 1e3) / 1e9,
+                                         "edges_relaxed": cst["edges_inspected"]}}
+
     serving = None if a.no_serve else serving_bench(G, a, torch)
 
     # End to end through the public API with pinned host result buffers.
@@ -670,6 +700,7 @@ def main():
         "batch_bfs": batch,
         "batch_pagerank": batch_pr,
         "serving": serving,
+        "bc_cc": more,
         "pagerank_precision": precision,
         "gpu_launches": launches,
         "clocks": clk,

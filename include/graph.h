@@ -230,6 +230,50 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
                   graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * betweenness -- betweenness centrality summed over a list of sources (Section 7.2,
+ * Figure 18; Brandes' algorithm). Per source, a forward BSP cycle finds BFS levels and the
+ * number of shortest paths sigma (each new vertex sums sigma over its neighbours one level
+ * up; boundary neighbours through published ghost copies), and a backward cycle from the
+ * deepest level up accumulates the dependency delta(v) = sum over neighbours w one level
+ * further of sigma(v) / sigma(w) * (1 + delta(w)).
+ *   sources  k uint32 source ids in host memory, each < n (k >= 1, repeats allowed)
+ *   scores   n doubles, global order: sum over the sources s of delta_s(v), v != s (host
+ *            or device per attr->out_mem). Scores of ordered pairs: an undirected
+ *            graph's textbook betweenness (unordered pairs) is half of the all-source sum.
+ * The stored graph must be symmetric (successors are taken from the same adjacency that
+ * gives predecessors). Path counts are FP64; they are exact while below 2^53.
+ * stats->edges_traversed: twice the degree sum of the vertices each source reaches
+ * (Section 5: forward and backward phases), summed over the sources.
+ * Errors: EINVAL, ESTATE, ETIMEOUT, ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int out_mem;
+  int timing;
+} bc_attr;
+
+graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_t k, double* scores,
+                         const bc_attr* attr, graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
+ * connected_components -- label propagation (Section 9.4's connected components, with the
+ * minimum label reduced at the source as Section 3.4 describes): every vertex starts with
+ * its own global id as label; each superstep, vertices whose label dropped send it to
+ * their neighbours (atomic minimum; boundary neighbours through their outbox slot,
+ * applied to the owner in the exchange); it ends when no label changes.
+ *   labels  n uint32, global order: the smallest vertex id of the vertex's component.
+ * The stored graph must be symmetric. Weights are not needed. stats->edges_traversed = m.
+ * Errors: EINVAL, ESTATE, ETIMEOUT (max_supersteps), ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int out_mem;
+  int max_supersteps; /* <= 0: no cap other than n + 1 */
+  int timing;
+} cc_attr;
+
+graph_status connected_components(graph_t* g, uint32_t* labels, const cc_attr* attr,
+                                  graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
  * pagerank -- pull PageRank (Section 7.1, Figure 14). Each iteration every vertex sums
  * its neighbours' contributions x[u] = r[u] / deg(u) and sets
  *     r'[v] = (1 - d)/n + d * (sum + D/n)

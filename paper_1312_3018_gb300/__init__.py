@@ -19,7 +19,7 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "bfs_batch", "sssp", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "betweenness", "connected_components", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
            "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
@@ -237,6 +237,38 @@ def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_superstep
     st = _lib.load().sssp(g.handle, int(source), pd, C.byref(attr), C.byref(stats))
     _lib.check(st, "sssp")
     return dist, stats.as_dict()
+
+
+def betweenness(g: Graph, sources, scores=None, *, out: str = "device", timing: bool = False):
+    """Betweenness centrality summed over the sources (FP64, global order), and stats."""
+    torch = _torch()
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64))
+    if src.ndim != 1 or np.any(src < 0) or np.any(src >= 2**32):
+        raise ValueError("sources must be a 1-D list of vertex ids")
+    src = src.astype(np.uint32)
+    if scores is None:
+        scores = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"
+                  else np.empty(g.n, dtype=np.float64))
+    ps, mem = _ptr(scores)
+    attr = _lib.bc_attr(mem, int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().betweenness(g.handle, src.ctypes.data, len(src), ps, C.byref(attr),
+                                 C.byref(stats))
+    _lib.check(st, "betweenness")
+    return scores, stats.as_dict()
+
+
+def connected_components(g: Graph, labels=None, *, out: str = "device", max_supersteps: int = 0,
+                         timing: bool = False):
+    """Component labels (the smallest vertex id of each component, uint32) and stats."""
+    torch = _torch()
+    labels = _out_u32(torch, g.n, out, labels)
+    pl, mem = _ptr(labels)
+    attr = _lib.cc_attr(mem, int(max_supersteps), int(timing))
+    stats = _lib.graph_stats()
+    st = _lib.load().connected_components(g.handle, pl, C.byref(attr), C.byref(stats))
+    _lib.check(st, "connected_components")
+    return labels, stats.as_dict()
 
 
 def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float = 0.0,

@@ -54,6 +54,14 @@ class graph_partition_info(C.Structure):
                 ("cls_end", (C.c_uint32 * 34) * 2), ("bytes_graph", C.c_int64)]
 
 
+class bc_attr(C.Structure):
+    _fields_ = [("out_mem", C.c_int), ("timing", C.c_int)]
+
+
+class cc_attr(C.Structure):
+    _fields_ = [("out_mem", C.c_int), ("max_supersteps", C.c_int), ("timing", C.c_int)]
+
+
 class graph_server_attr(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("bfs_lanes", C.c_uint32), ("max_sssp", C.c_uint32),
                 ("out_mem", C.c_int)]
@@ -115,6 +123,8 @@ SIGNATURES = {
     "bfs": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "bfs_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
+    "betweenness": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bc_attr), C.POINTER(graph_stats)]),
+    "connected_components": (_int, [_vp, _vp, C.POINTER(cc_attr), C.POINTER(graph_stats)]),
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
     "pagerank_multi": (_int, [_vp, _u32, _vp, C.POINTER(pagerank_attr), _vp, _vp,
                               C.POINTER(graph_stats)]),

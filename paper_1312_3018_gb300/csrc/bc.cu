@@ -1,0 +1,493 @@
+// Betweenness centrality (Section 7.2, Figure 18; Brandes' algorithm) on the partitioned
+// graph, summed over a list of sources. Each source runs two BSP cycles:
+//
+// Forward cycle, one superstep per level L (the BFS of Figure 18's forward kernel, with
+// the path counts gathered instead of scattered):
+//  - compute (push): vertices at level L mark undiscovered neighbours with L + 1; a
+//    boundary neighbour is marked in its outbox slot.
+//  - communication: marked outbox slots give their owner level L + 1; then every outbox
+//    slot publishes its owner's level and path count into the ghost arrays (pull).
+//  - compute (pull): every vertex at level L + 1 sums the path counts sigma of its
+//    neighbours at level L. Path counts are integers held in FP64, exact in any summation
+//    order below 2^53, so no atomics race on them except the chunk sums of hub vertices.
+//  - termination: no vertex was discovered.
+// Backward cycle, one superstep per level L from the deepest down to 1 (Figure 18's
+// backward kernel): every vertex at level L sums c(w) = (1 + delta(w)) / sigma(w) over its
+// neighbours at level L + 1 (ghost copies for boundary neighbours, published first), sets
+// delta(v) = sigma(v) * sum, c(v), and adds delta(v) to its score. Writing the dependency
+// as sigma(v) times a sum of per-vertex quotients needs one division per vertex instead of
+// one per edge (this GPU's FP64 rate is low).
+#include <string.h>
+
+#include "common.cuh"
+
+namespace gg {
+
+struct BcCounters {
+  unsigned long long discovered;
+  unsigned long long reached_degree;
+  unsigned long long inspected;
+  unsigned long long messages;
+};
+
+struct BcWs {
+  DevBuf dist[2], sigma[2], cq[2], score[2], hacc[2];
+  DevBuf odist[2], gdist[2], gval[2];
+};
+
+void free_bc(graph* g) {
+  if (!g->bc) return;
+  BcWs* w = g->bc;
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->dist[p], &w->sigma[p], &w->cq[p], &w->score[p], &w->hacc[p],
+                     &w->odist[p], &w->gdist[p], &w->gval[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  delete w;
+  g->bc = nullptr;
+}
+
+namespace {
+
+struct BcSide {
+  PartView P;
+  uint32_t* dist;
+  double* sigma;
+  double* cq;     // (1 + delta) / sigma of vertices whose dependency is final
+  double* score;  // betweenness summed over the sources so far
+  double* hacc;   // hub partial sums
+  uint32_t* odist;  // level given to each outbox target by this partition (INF: none)
+  uint32_t* gdist;  // published level of each outbox target
+  double* gval;     // published sigma (forward) or c (backward) of each outbox target
+};
+
+struct BcArgs {
+  BcSide side[2];
+  BcCounters* ctr;
+  uint32_t L;
+};
+
+struct Cnt {
+  unsigned long long disc = 0, deg = 0, insp = 0, msg = 0;
+};
+
+__device__ void flush(const Cnt& c, BcCounters* ctr) {
+  __shared__ unsigned long long s[4];
+  if (threadIdx.x < 4) s[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long v[4] = {warp_sum(c.disc), warp_sum(c.deg), warp_sum(c.insp),
+                                   warp_sum(c.msg)};
+  if (lane_id() == 0)
+    for (int j = 0; j < 4; ++j)
+      if (v[j]) atomicAdd(&s[j], v[j]);
+  __syncthreads();
+  if (threadIdx.x < 4 && s[threadIdx.x])
+    atomicAdd(&((unsigned long long*)ctr)[threadIdx.x], s[threadIdx.x]);
+}
+
+__device__ __forceinline__ double group_sum_d(double v, int gshift) {
+  for (int o = 1; o < (1 << gshift); o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Forward push from the vertices at level L over edges first, first + stride, ...
+__device__ __forceinline__ void discover_edges(const BcSide& S, uint32_t L, const uint32_t* Ep,
+                                               int first, int deg, int stride, Cnt& c) {
+  const uint64_t pol = l2_evict_first_policy();
+  for (int i = first; i < deg; i += stride) {
+    c.insp++;
+    const uint32_t x = ld_stream(Ep + i, pol);
+    if (!(x & kRemote)) {
+      if (S.dist[x] == kInf && atomicCAS(&S.dist[x], kInf, L + 1) == kInf) {
+        c.disc++;
+        c.deg += (unsigned long long)(S.P.off[x + 1] - S.P.off[x]);
+      }
+    } else {
+      const uint32_t idx = x & kIdMask;
+      if (S.odist[idx] == kInf) atomicCAS(&S.odist[idx], kInf, L + 1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bc_discover(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A) {
+  Cnt c;
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const BcSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      const uint32_t ch = G.v0 + rel;
+      const uint32_t v = S.P.chunk_vertex[ch];
+      if (S.dist[v] != A.L) continue;  // CTA-uniform
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      discover_edges(S, A.L, S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, c);
+    } else {
+      const int gs = G.gshift;
+      const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+      if (gi >= G.count) continue;
+      const uint32_t v = G.v0 + gi;
+      if (S.dist[v] != A.L) continue;
+      const int64_t s = S.P.off[v], t = S.P.off[v + 1];
+      discover_edges(S, A.L, S.P.E + s, threadIdx.x & ((1 << gs) - 1), (int)(t - s), 1 << gs, c);
+    }
+  }
+  flush(c, A.ctr);
+}
+
+// Outbox slots marked with level L + 1 this superstep give their owner that level.
+__global__ void __launch_bounds__(kThreads) k_bc_exchange(const __grid_constant__ BcArgs A) {
+  Cnt c;
+  const uint64_t n0 = A.side[0].P.nout, total = n0 + A.side[1].P.nout;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int p = i < n0 ? 0 : 1;
+    const uint32_t idx = (uint32_t)(p == 0 ? i : i - n0);
+    const BcSide& S = A.side[p];
+    if (S.odist[idx] != A.L + 1) continue;
+    c.msg++;
+    const BcSide& Q = A.side[1 - p];
+    const uint32_t u = S.P.outbox[idx];
+    if (Q.dist[u] == kInf && atomicCAS(&Q.dist[u], kInf, A.L + 1) == kInf) {
+      c.disc++;
+      c.deg += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
+    }
+  }
+  flush(c, A.ctr);
+}
+
+// Pull publication: level and sigma (forward) or c (backward) of every outbox target.
+__global__ void k_bc_publish(const __grid_constant__ BcArgs A, int backward) {
+  const uint64_t n0 = A.side[0].P.nout, total = n0 + A.side[1].P.nout;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int p = i < n0 ? 0 : 1;
+    const uint32_t idx = (uint32_t)(p == 0 ? i : i - n0);
+    const BcSide& S = A.side[p];
+    const BcSide& Q = A.side[1 - p];
+    const uint32_t u = S.P.outbox[idx];
+    const uint32_t d = Q.dist[u];
+    S.gdist[idx] = d;
+    S.gval[idx] = backward ? Q.cq[u] : Q.sigma[u];
+  }
+}
+
+// Sum over the neighbours at level `want` of sigma (forward) or c (backward).
+__device__ __forceinline__ double pull_one(const BcSide& S, uint32_t x, uint32_t want,
+                                           int backward) {
+  if (x & kRemote) {
+    const uint32_t idx = x & kIdMask;
+    return S.gdist[idx] == want ? S.gval[idx] : 0.0;
+  }
+  return S.dist[x] == want ? (backward ? S.cq[x] : S.sigma[x]) : 0.0;
+}
+
+__device__ __forceinline__ void finish_vertex(const BcSide& S, uint32_t v, double sum,
+                                              int backward) {
+  if (!backward) {
+    S.sigma[v] = sum;
+  } else {
+    const double sg = S.sigma[v];
+    const double delta = sg * sum;
+    S.cq[v] = (1.0 + delta) / sg;
+    S.score[v] += delta;
+  }
+}
+
+// Pull over the vertices at level `at` (forward: the new level, summing sigma of level
+// at - 1; backward: level at, summing c of level at + 1). Hub vertices are summed chunk by
+// chunk into hacc and finished by k_bc_hubs.
+__global__ void __launch_bounds__(kThreads)
+k_bc_pull(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A, uint32_t at,
+          int backward) {
+  Cnt c;
+  const uint32_t want = backward ? at + 1 : at - 1;
+  __shared__ double red[kThreads / 32];
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const BcSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      const uint32_t ch = G.v0 + rel;
+      const uint32_t v = S.P.chunk_vertex[ch];
+      if (S.dist[v] != at) continue;  // CTA-uniform
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      double s = 0;
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+        c.insp++;
+        s += pull_one(S, S.P.E[e], want, backward);
+      }
+      s = group_sum_d(s, 5);
+      if (lane_id() == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+        if (t != 0.0) atomicAdd(&S.hacc[v], t);
+      }
+      __syncthreads();
+      continue;
+    }
+    const int gs = G.gshift;
+    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+    const int gl = threadIdx.x & ((1 << gs) - 1);
+    bool act = false;
+    uint32_t v = 0;
+    int64_t s0 = 0, t0 = 0;
+    if (gi < G.count) {
+      v = G.v0 + gi;
+      if (S.dist[v] == at) {
+        act = true;
+        s0 = S.P.off[v];
+        t0 = S.P.off[v + 1];
+      }
+    }
+    double s = 0;
+    for (int64_t e = s0 + gl; e < t0; e += (1 << gs)) {
+      c.insp++;
+      s += pull_one(S, S.P.E[e], want, backward);
+    }
+    s = group_sum_d(s, gs);
+    if (act && gl == 0) finish_vertex(S, v, s, backward);
+  }
+  flush(c, A.ctr);
+}
+
+// Hub vertices at level `at`: finish from their chunk sums.
+__global__ void k_bc_hubs(const __grid_constant__ BcArgs A, uint32_t at, int backward) {
+  for (int p = 0; p < 2; ++p) {
+    const BcSide& S = A.side[p];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < S.P.bstart[1];
+         v += gridDim.x * blockDim.x) {
+      if (S.dist[v] != at) continue;
+      finish_vertex(S, v, S.hacc[v], backward);
+      S.hacc[v] = 0.0;
+    }
+  }
+}
+
+__global__ void k_bc_source(const __grid_constant__ BcArgs A, const uint32_t* g2l,
+                            uint32_t source) {
+  const uint32_t gl = g2l[source];
+  const BcSide& S = A.side[gl >> 31];
+  const uint32_t lid = gl & kIdMask;
+  S.dist[lid] = 0;
+  S.sigma[lid] = 1.0;
+  A.ctr->discovered = 1;
+  A.ctr->reached_degree = (unsigned long long)(S.P.off[lid + 1] - S.P.off[lid]);
+}
+
+__global__ void k_bc_collect(const __grid_constant__ BcArgs A, uint32_t nv0, uint32_t n,
+                             double* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = i < nv0 ? 0 : 1;
+  const uint32_t lid = p == 0 ? i : i - nv0;
+  const BcSide& S = A.side[p];
+  out[S.P.l2g[lid]] = S.score[lid];
+}
+
+graph_status alloc_ws(graph* g) {
+  if (g->bc) return GRAPH_OK;
+  BcWs* w = new BcWs();
+  g->bc = w;
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_TRY(dalloc(g, w->dist[p], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->sigma[p], 8ull * P.nv));
+    GG_TRY(dalloc(g, w->cq[p], 8ull * P.nv));
+    GG_TRY(dalloc(g, w->score[p], 8ull * P.nv));
+    GG_TRY(dalloc(g, w->hacc[p], 8ull * P.nhub));
+    GG_TRY(dalloc(g, w->odist[p], 4ull * P.nout));
+    GG_TRY(dalloc(g, w->gdist[p], 4ull * P.nout));
+    GG_TRY(dalloc(g, w->gval[p], 8ull * P.nout));
+  }
+  if (g->counters.bytes < sizeof(BcCounters) || !g->counters.p) {
+    dfree(g, g->counters);
+    GG_TRY(dalloc(g, g->counters, 1024));
+  }
+  return ensure_host_counters(g, 1024);
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g) {
+  const graph_status s = alloc_ws(g);
+  if (s != GRAPH_OK) free_bc(g);
+  return s;
+}
+
+BcArgs make_args(graph* g, uint32_t L) {
+  BcWs* w = g->bc;
+  BcArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int p = 0; p < 2; ++p) {
+    BcSide& S = A.side[p];
+    S.P = g->part[p].view();
+    S.dist = (uint32_t*)w->dist[p].p;
+    S.sigma = (double*)w->sigma[p].p;
+    S.cq = (double*)w->cq[p].p;
+    S.score = (double*)w->score[p].p;
+    S.hacc = (double*)w->hacc[p].p;
+    S.odist = (uint32_t*)w->odist[p].p;
+    S.gdist = (uint32_t*)w->gdist[p].p;
+    S.gval = (double*)w->gval[p].p;
+  }
+  A.ctr = (BcCounters*)g->counters.p;
+  A.L = L;
+  return A;
+}
+
+Plan dense_plan(graph* g) {
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+  }
+  return pl;
+}
+
+}  // namespace
+}  // namespace gg
+
+using namespace gg;
+
+extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_t k,
+                                    double* scores, const bc_attr* attr, graph_stats* stats) {
+  if (!g || !sources || !scores || k == 0) {
+    set_error("graph, sources or scores is NULL, or k is 0");
+    return GRAPH_EINVAL;
+  }
+  for (uint32_t i = 0; i < k; ++i)
+    if (sources[i] >= g->n) {
+      set_error("sources[%u] = %u >= n %u", i, sources[i], g->n);
+      return GRAPH_EINVAL;
+    }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before betweenness");
+    return GRAPH_ESTATE;
+  }
+  bc_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) {
+    set_error("bad out_mem");
+    return GRAPH_EINVAL;
+  }
+  GG_TRY(ensure_ws(g));
+  BcWs* w = g->bc;
+  cudaStream_t st = g->stream;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  const Plan pl = dense_plan(g);
+  const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
+  const unsigned sweep = 152 * 8;
+  const unsigned hub_grid = 152;
+  BcCounters* hc = (BcCounters*)g->host_counters;
+  BcCounters* dc = (BcCounters*)g->counters.p;
+  for (int p = 0; p < 2; ++p) {
+    GG_CUDA(cudaMemsetAsync(w->score[p].p, 0, 8ull * g->part[p].nv, st));
+    GG_CUDA(cudaMemsetAsync(w->hacc[p].p, 0, 8ull * g->part[p].nhub, st));
+  }
+  int64_t launches = 0, traversed = 0, inspected = 0, messages = 0, steps = 0;
+  for (uint32_t si = 0; si < k; ++si) {
+    for (int p = 0; p < 2; ++p) {
+      const Part& P = g->part[p];
+      GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * P.nv, st));
+      GG_CUDA(cudaMemsetAsync(w->sigma[p].p, 0, 8ull * P.nv, st));
+      GG_CUDA(cudaMemsetAsync(w->odist[p].p, 0xFF, 4ull * P.nout, st));
+    }
+    GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(BcCounters), st));
+    k_bc_source<<<1, 1, 0, st>>>(make_args(g, 0), (const uint32_t*)g->g2l.p, sources[si]);
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    int64_t reached = (int64_t)hc->reached_degree;
+    launches++;
+    // Forward cycle.
+    uint32_t L = 0;
+    for (;; ++L) {
+      if (L >= g->n) {
+        set_error("betweenness reached the level cap");
+        timer.finish(nullptr);
+        return GRAPH_ETIMEOUT;
+      }
+      const BcArgs A = make_args(g, L);
+      GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(BcCounters), st));
+      timer.mark(2);
+      if (pl.nblocks) k_bc_discover<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      if (nout) {
+        k_bc_exchange<<<sweep, kThreads, 0, st>>>(A);
+        k_bc_publish<<<sweep, 256, 0, st>>>(A, 0);
+      }
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      if (pl.nblocks) {
+        k_bc_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A, L + 1, 0);
+        k_bc_hubs<<<hub_grid, 256, 0, st>>>(A, L + 1, 0);
+      }
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      launches += (pl.nblocks ? 3 : 0) + (nout ? 2 : 0);
+      GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+      inspected += (int64_t)hc->inspected;
+      messages += (int64_t)hc->messages;
+      reached += (int64_t)hc->reached_degree;
+      steps++;
+      if (hc->discovered == 0) break;
+    }
+    // L is now the deepest level (the ghost levels published last are final). Backward
+    // cycle: levels L .. 1; the deepest level has no successors.
+    for (uint32_t lv = L; lv >= 1; --lv) {
+      const BcArgs A = make_args(g, lv);
+      GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(BcCounters), st));
+      timer.mark(2);
+      if (nout && lv < L) k_bc_publish<<<sweep, 256, 0, st>>>(A, 1);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      if (pl.nblocks) {
+        k_bc_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A, lv, 1);
+        k_bc_hubs<<<hub_grid, 256, 0, st>>>(A, lv, 1);
+      }
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      launches += (pl.nblocks ? 2 : 0) + (nout && lv < L ? 1 : 0);
+      GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+      inspected += (int64_t)hc->inspected;
+      steps++;
+    }
+    traversed += 2 * reached;
+  }
+  double* out = scores;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 8ull * g->n));
+    out = (double*)g->stage.p;
+  }
+  k_bc_collect<<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, 0), g->part[0].nv, g->n, out);
+  GG_CUDA(cudaGetLastError());
+  launches++;
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, scores, out, 8ull * g->n, GRAPH_MEM_HOST));
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)steps;
+    stats->edges_traversed = traversed;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+  }
+  timer.finish(stats);
+  return s;
+}

@@ -297,6 +297,7 @@ struct BfsWs;
 struct SsspWs;
 struct PrWs;
 struct MsWs;
+struct BcWs;
 
 }  // namespace gg
 
@@ -321,6 +322,7 @@ struct graph {
   gg::SsspWs* sssp = nullptr;
   gg::PrWs* pr = nullptr;
   gg::MsWs* ms = nullptr;     // batched BFS workspace
+  gg::BcWs* bc = nullptr;     // betweenness workspace
 };
 
 namespace gg {
@@ -362,6 +364,7 @@ void free_bfs(graph* g);
 void free_sssp(graph* g);
 void free_pr(graph* g);
 void free_msbfs(graph* g);
+void free_bc(graph* g);
 
 inline unsigned grid_for(uint64_t work, unsigned per_block) {
   uint64_t b = (work + per_block - 1) / per_block;

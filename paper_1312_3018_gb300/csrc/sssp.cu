@@ -113,7 +113,9 @@ __device__ void flush_ssp(unsigned long long insp, unsigned long long msg, bool 
 }
 
 // Relaxes edges i = first, first + stride, ... < deg of one vertex whose adjacency starts at
-// Ep / Wp. Lowering a distance is a fire-and-forget reduction plus a touched mark.
+// Ep / Wp. Lowering a distance is a fire-and-forget reduction plus a touched mark. CC:
+// label propagation, every weight zero (Wp unused), distances are component labels.
+template <bool CC>
 __device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, const uint32_t* Ep,
                                             const uint32_t* Wp, int first, int deg, int stride,
                                             unsigned long long& insp, bool& ovf) {
@@ -123,7 +125,7 @@ __device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, cons
     insp++;
     const uint32_t x = ld_stream(Ep + i, pol);
     bool o = false;
-    const uint32_t nd = sat_add(dv, ld_stream(Wp + i, pol), o);
+    const uint32_t nd = CC ? dv : sat_add(dv, ld_stream(Wp + i, pol), o);
     if (!(x & kRemote)) {
       if (nd < S.dist[x]) {
         ovf |= o;
@@ -141,6 +143,7 @@ __device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, cons
   }
 }
 
+template <bool CC>
 __global__ void __launch_bounds__(kThreads)
 k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs A) {
   unsigned long long insp = 0;
@@ -156,8 +159,8 @@ k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs
       const int64_t e0 = S.P.chunk_first[ch];
       const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
       const uint32_t dv = __ldcg(&S.snap[v]);  // the distance the hub was queued with
-      relax_edges(S, dv, S.P.E + e0, S.P.W + e0, threadIdx.x, (int)(e1 - e0), kThreads, insp,
-                  ovf);
+      relax_edges<CC>(S, dv, S.P.E + e0, CC ? nullptr : S.P.W + e0, threadIdx.x,
+                      (int)(e1 - e0), kThreads, insp, ovf);
     } else {
       const int gs = G.gshift;
       const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
@@ -167,7 +170,8 @@ k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs
         const int64_t s = S.P.off[v], t = S.P.off[v + 1];
         const uint32_t dv = __ldcg(&S.dist[v]);
         if (gl == 0) S.snap[v] = dv;
-        relax_edges(S, dv, S.P.E + s, S.P.W + s, gl, (int)(t - s), 1 << gs, insp, ovf);
+        relax_edges<CC>(S, dv, S.P.E + s, CC ? nullptr : S.P.W + s, gl, (int)(t - s), 1 << gs,
+                        insp, ovf);
       }
     }
   }
@@ -272,6 +276,39 @@ __global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t nv0,
   if (lane_id() == 0 && d) atomicAdd(reached_degree, d);
 }
 
+// Connected components start: every vertex labelled with its global id, every vertex
+// with edges active (queued with its label; hub vertices as all of their chunks).
+__global__ void k_cc_init(const __grid_constant__ SsspArgs A, uint32_t nv0, uint32_t ntot,
+                          uint32_t* queue0, uint32_t* queue1, uint32_t* hubq0,
+                          uint32_t* hubq1) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntot) return;
+  const int p = i < nv0 ? 0 : 1;
+  const uint32_t v = p == 0 ? i : i - nv0;
+  const SsspSide& S = A.side[p];
+  const uint32_t label = S.P.l2g[v];
+  S.dist[v] = label;
+  S.snap[v] = label;
+  const int b = bucket_of(S.P, v);
+  if (b == 0) {
+    const int64_t deg = S.P.off[v + 1] - S.P.off[v];
+    const uint32_t c0 = S.P.hub_chunk0[v];
+    const uint32_t c1 = c0 + (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
+    for (uint32_t c = c0; c < c1; ++c) (p == 0 ? hubq0 : hubq1)[c] = c;
+  } else if (b < kNBucket) {
+    (p == 0 ? queue0 : queue1)[v] = v;
+  }
+}
+
+__global__ void k_cc_tails(const __grid_constant__ SsspArgs A) {
+  if (threadIdx.x != 0) return;
+  for (int p = 0; p < 2; ++p) {
+    const PartView& P = A.side[p].P;
+    A.ctr->tail[p][0] = P.nchunk;
+    for (int b = 1; b < kNBucket; ++b) A.ctr->tail[p][b] = P.bstart[b + 1] - P.bstart[b];
+  }
+}
+
 graph_status alloc_ws_into(graph* g, SsspWs* w) {
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
@@ -366,7 +403,8 @@ uint64_t active_count(const SsspCounters& c) {
 
 // One round: relax the active set c describes (queues `cur`), apply the outbox, filter.
 graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCounters& c,
-                          int cur, cudaStream_t st, PhaseTimer* timer, int64_t* launches) {
+                          int cur, cudaStream_t st, PhaseTimer* timer, int64_t* launches,
+                          bool cc = false) {
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
   const SsspArgs A = make_args(g, w, ctr, cur);
   Plan pl;
@@ -382,7 +420,10 @@ graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCoun
   const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
   const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
   if (timer) timer->mark(2);
-  if (pl.nblocks) k_sssp_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+  if (pl.nblocks) {
+    if (cc) k_sssp_relax<true><<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+    else k_sssp_relax<false><<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+  }
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(0);
   if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
@@ -627,5 +668,89 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
     set_error("a shortest distance reached 2^32 - 1");
     return GRAPH_ERANGE;
   }
+  return s;
+}
+
+extern "C" graph_status connected_components(graph_t* g, uint32_t* labels,
+                                             const cc_attr* attr, graph_stats* stats) {
+  if (!g || !labels) {
+    set_error("graph or labels is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before connected_components");
+    return GRAPH_ESTATE;
+  }
+  cc_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) {
+    set_error("bad out_mem");
+    return GRAPH_EINVAL;
+  }
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  GG_TRY(ensure_ws(g));
+  SsspWs* w = g->sssp;
+  cudaStream_t st = g->stream;
+  SsspCounters* dc = (SsspCounters*)g->counters.p;
+  SsspCounters* hc = (SsspCounters*)g->host_counters;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->touched[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * P.nout, st));
+    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
+  }
+  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SsspCounters), st));
+  {
+    const SsspArgs A = make_args(g, w, dc, 0);
+    k_cc_init<<<grid_for(g->n, 256), 256, 0, st>>>(
+        A, g->part[0].nv, g->n, (uint32_t*)w->queue[0][0].p, (uint32_t*)w->queue[1][0].p,
+        (uint32_t*)w->hubq[0][0].p, (uint32_t*)w->hubq[1][0].p);
+    k_cc_tails<<<1, 32, 0, st>>>(A);
+    GG_CUDA(cudaGetLastError());
+  }
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
+  int64_t inspected = 0, messages = 0, launches = 2, rounds = 0;
+  int cur = 0;
+  for (;; ++rounds) {
+    const SsspCounters c = *hc;
+    if (active_count(c) == 0) break;
+    if (rounds >= cap) {
+      set_error("connected_components reached the superstep cap (%lld)", (long long)cap);
+      timer.finish(nullptr);
+      return GRAPH_ETIMEOUT;
+    }
+    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches, true));
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
+    messages += (int64_t)hc->messages;
+    cur = 1 - cur;
+  }
+  uint32_t* out = labels;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 4ull * g->n + 64));
+    out = (uint32_t*)g->stage.p;
+  }
+  GG_TRY(launch_collect(g, w, dc, cur, out, st));
+  launches++;
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, labels, out, 4ull * g->n, GRAPH_MEM_HOST));
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)rounds;
+    stats->edges_traversed = g->m;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+  }
+  timer.finish(stats);
   return s;
 }

@@ -172,3 +172,19 @@ def test_many_graph_pagerank_256_uneven_rmat(gpu):
         assert np.abs(r[vb[i]:vb[i + 1]] - ref).sum() <= 1e-6, f"component {i}"
         assert abs(res[i] - rres[-1]) <= 2e-6
     H.free()
+
+
+def test_rmat22_betweenness_four_sources(gpu, rmat22, loaded22):
+    g = rmat22
+    srcs = synth.sources(g, 4, seed=9)
+    sc, st = gpu.betweenness(loaded22, srcs, out="host")
+    ref, trav = oracle.bc(g.n, g.offsets, g.cols, srcs)
+    err = np.abs(sc - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() <= 1e-9
+    assert st["edges_traversed"] == trav
+
+
+def test_rmat22_and_rmat25_connected_components(gpu, rmat22, loaded22, rmat25, loaded25):
+    for g, H in ((rmat22, loaded22), (rmat25, loaded25)):
+        lab, _ = gpu.connected_components(H, out="host")
+        assert np.array_equal(lab, oracle.cc(g.n, g.offsets, g.cols))
