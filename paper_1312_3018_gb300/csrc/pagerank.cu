@@ -7,9 +7,11 @@
 //  - compute: every vertex sums the contributions of its neighbours (local ones from x,
 //    boundary ones from the ghost slots) and sets r' = (1-d)/n + d (sum + D/n), then its
 //    own contribution x' = r'/deg.
-//  - reduction: per-block partial sums of the L1 residual; the last block to finish adds
-//    them in block order in FP64 and forms the next iteration's constant term (no extra
-//    launch).
+//  - reduction: each block adds its partial sum of the L1 residual to one of kSlots FP64
+//    slots (a reduction nobody waits for, so a block frees its SM slot as soon as its
+//    vertices are written); a one-block kernel then sums the slots, forms the next
+//    iteration's constant term and clears them. The FP64 additions happen in arrival
+//    order, so the residual's last bits can differ between runs; the ranks cannot.
 //
 // Work items (one CTA each): hub vertices (degree >= 2048; the CTA walks the adjacency in
 // chunks of kHubChunk edges, two chunks in flight: the bulk copy of chunk c+2 is issued as
@@ -55,8 +57,7 @@ struct PrWs {
   size_t esize = 0;  // bytes per stored contribution
   size_t rsize = 0;  // bytes per stored rank
   DevBuf r[2], x[2][2], ghost[2];
-  DevBuf partials, scal, resid, done;
-  uint32_t nblocks = 0;
+  DevBuf slots, scal, resid;
   int max_iter = 0;
   MultiWs* multi = nullptr;
 };
@@ -81,10 +82,9 @@ void free_pr(graph* g) {
     DevBuf* all[] = {&w->r[p], &w->x[p][0], &w->x[p][1], &w->ghost[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
-  dfree(g, w->partials);
+  dfree(g, w->slots);
   dfree(g, w->scal);
   dfree(g, w->resid);
-  dfree(g, w->done);
   delete w;
   g->pr = nullptr;
 }
@@ -104,13 +104,13 @@ struct PrSide {
 // Device scalars (doubles): [0] constant term of this iteration, (1-d)/n + d D/n;
 // [1] D; [2] last residual; [3] rank of degree-zero vertices before this iteration;
 // [4] the constant term rounded to FP32 (stored as a float in the first half).
+constexpr uint32_t kSlots = 1024;  // FP64 residual slots (block b adds to slot b % kSlots)
+
 struct PrArgs {
   PrSide side[2];
   double* scal;
-  float* partials;    // per block residual partial (FP32; FP64 mode: double, see below)
-  double* partials64;
+  double* slots;      // [kSlots] residual partial sums, zero between iterations
   double* resid;      // residual history
-  uint32_t* done;     // blocks finished this iteration
   double damping, n;
   float damping_f, n_f, d_over_n_f;
   double nzero;       // number of degree-zero vertices
@@ -231,11 +231,15 @@ struct Desc {
   uint8_t kind, part, gshift, pad;
 };
 
+// Range holding `item` (item0 increases strictly along the ranges): a binary search, so
+// the CTA's first bulk copy is not held up by a scan of the parameter table.
 __device__ __forceinline__ int find_range(const PrPlan& P, uint32_t item) {
-  int lo = 0;
-  #pragma unroll 1
-  for (int i = 1; i < P.nr; ++i)
-    if (item >= P.r[i].item0) lo = i;
+  int lo = 0, hi = P.nr;  // P.r[lo].item0 <= item, and item < P.r[hi].item0 when hi < nr
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P.r[mid].item0 <= item) lo = mid;
+    else hi = mid;
+  }
   return lo;
 }
 
@@ -354,7 +358,6 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
   __shared__ uint64_t bar, bar2;
   __shared__ Desc dsh;
   __shared__ AT red[kThreads / 32];
-  __shared__ int flag;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_init(&bar2, 1);
@@ -423,13 +426,31 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
       }
       __syncthreads();
       const AT* vv = vals + shift;
-      const int gs = d.gshift;
-      const int gl = lane_id() & ((1 << gs) - 1);
-      const int per_warp = 32 >> gs;
+      const int gs = d.gshift;  // 2^gs threads per vertex
       const int nvt = (int)(d.v1 - d.v0);
       const int64_t* so = sOff + d.oshift;
-      for (int jb = (threadIdx.x >> 5) * per_warp; jb < nvt; jb += (kThreads / 32) * per_warp) {
-        const int j = jb + (int)(lane_id() >> gs);
+      if (gs <= 5) {
+        const int gl = lane_id() & ((1 << gs) - 1);
+        const int per_warp = 32 >> gs;
+        for (int jb = (threadIdx.x >> 5) * per_warp; jb < nvt; jb += (kThreads / 32) * per_warp) {
+          const int j = jb + (int)(lane_id() >> gs);
+          AT s = 0;
+          int es = 0, ee = 0;
+          if (j < nvt) {
+            es = (int)(so[j] - d.e0);
+            ee = (int)(so[j + 1] - d.e0);
+            for (int i = es + gl; i < ee; i += (1 << gs)) s += vv[i];
+          }
+          s = group_sum(s, gs);
+          if (j < nvt && gl == 0)
+            res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, s, ee - es,
+                                            (AT)sR[d.rshift + j]);
+        }
+      } else {
+        // Several warps per vertex (tiles of at most four vertices): warp sums meet in
+        // shared memory and the group's first thread updates the vertex.
+        const int j = (int)(threadIdx.x >> gs);
+        const int gl = (int)(threadIdx.x & ((1u << gs) - 1));
         AT s = 0;
         int es = 0, ee = 0;
         if (j < nvt) {
@@ -437,10 +458,16 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
           ee = (int)(so[j + 1] - d.e0);
           for (int i = es + gl; i < ee; i += (1 << gs)) s += vv[i];
         }
-        s = group_sum(s, gs);
-        if (j < nvt && gl == 0)
-          res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, s, ee - es,
+        s = warp_sum(s);
+        if (lane_id() == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (j < nvt && gl == 0) {
+          AT t = 0;
+          for (int k = 0; k < (1 << (gs - 5)); ++k) t += red[(threadIdx.x >> 5) + k];
+          res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, t, ee - es,
                                           (AT)sR[d.rshift + j]);
+        }
+        __syncthreads();  // red is reused by the residual sum
       }
     } else {
       // Degree-zero vertices: the rank is the constant term, the contribution zero.
@@ -455,23 +482,20 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
   }
   // Components keep no global scalars: their constants come from the host's table.
   if (MULTI) return;
-  // Residual partial of this block; the last block adds all of them in block order.
   res = block_sum<AT>(res, red);
-  if (threadIdx.x == 0) {
-    if (sizeof(AT) == 4) A.partials[blockIdx.x] = (float)res;
-    else A.partials64[blockIdx.x] = (double)res;
-    __threadfence();
-    flag = (atomicAdd(A.done, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!flag) return;
-  __threadfence();
+  if (threadIdx.x == 0) atomicAdd(A.slots + (blockIdx.x % kSlots), (double)res);
+}
+
+// End of an iteration (one block): the residual is the sum of the slots plus the
+// degree-zero vertices' closed-form share; the next constant term follows from the
+// dangling mass D, which degree-zero vertices hold as count x constant.
+__global__ void __launch_bounds__(kThreads) k_pr_finalize(const __grid_constant__ PrArgs A,
+                                                          int iter, int dangling) {
   __shared__ double rd[kThreads / 32];
   double a = 0;
-  if (sizeof(AT) == 4) {
-    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) a += (double)__ldcg(A.partials + i);
-  } else {
-    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) a += __ldcg(A.partials64 + i);
+  for (uint32_t i = threadIdx.x; i < kSlots; i += kThreads) {
+    a += A.slots[i];
+    A.slots[i] = 0.0;
   }
   a = block_sum<double>(a, rd);
   if (threadIdx.x == 0) {
@@ -485,7 +509,6 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
     A.scal[0] = base;
     ((float*)(A.scal + 4))[0] = (float)base;
     A.resid[iter] = a;
-    *A.done = 0;
   }
 }
 
@@ -535,6 +558,15 @@ __global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t nv0, uin
   out[S.P.l2g[v]] = (double)((const RT*)S.r)[v];
 }
 
+// Threads per vertex (log2) of a class-c tile: kLeafEdges >> (c-1) vertices share the
+// CTA's kThreads threads, so every vertex gets 2^(c-3) of them (one round, 4 to 8 edges
+// per thread); classes 1-3 take one thread per vertex.
+#ifndef PR_GS_OLD
+inline int leaf_gshift(int c) { return std::max(0, c - 3); }
+#else
+inline int leaf_gshift(int c) { return std::min(c - 1, 5); }
+#endif
+
 PrPlan make_plan(graph* g) {
   PrPlan pl;
   memset(&pl, 0, sizeof(pl));
@@ -557,7 +589,7 @@ PrPlan make_plan(graph* g) {
     for (int c = kClassHub - 1; c >= 1; --c) {
       const uint32_t v0 = P.cls_end[c + 1], v1 = P.cls_end[c];
       const uint32_t per = std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1));
-      add((v1 - v0 + per - 1) / per, v0, v1, per, kItemLeaf, p, std::min(c - 1, 5));
+      add((v1 - v0 + per - 1) / per, v0, v1, per, kItemLeaf, p, leaf_gshift(c));
     }
     const uint32_t z0 = P.cls_end[1], z1 = P.nv;
     add((z1 - z0 + kTileV - 1) / kTileV, z0, z1, kTileV, kItemZero, p, 0);
@@ -577,12 +609,10 @@ graph_status prepare_kernel() {
   return GRAPH_OK;
 }
 
-graph_status alloc_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
+graph_status alloc_ws(graph* g, int prec, int max_iter) {
   const size_t es = prec == GRAPH_PR_FP64 ? 8 : (prec == GRAPH_PR_FP16 ? 2 : 4);
   const size_t rs = prec == GRAPH_PR_FP64 ? 8 : 4;
-  const size_t as = prec == GRAPH_PR_FP64 ? 8 : 4;
-  if (g->pr && (g->pr->prec != prec || g->pr->max_iter < max_iter || g->pr->nblocks < nblocks))
-    free_pr(g);
+  if (g->pr && (g->pr->prec != prec || g->pr->max_iter < max_iter)) free_pr(g);
   if (g->pr) return GRAPH_OK;
   PrWs* w = new PrWs();
   g->pr = w;
@@ -590,7 +620,6 @@ graph_status alloc_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
   w->esize = es;
   w->rsize = rs;
   w->max_iter = max_iter;
-  w->nblocks = nblocks;
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
     GG_TRY(dalloc(g, w->r[p], rs * ((size_t)P.nv + 8)));  // bulk copies read 16-B granules
@@ -598,16 +627,15 @@ graph_status alloc_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
     GG_TRY(dalloc(g, w->x[p][1], es * P.nv));
     GG_TRY(dalloc(g, w->ghost[p], es * P.nout));
   }
-  GG_TRY(dalloc(g, w->partials, as * (size_t)(nblocks + 1)));
+  GG_TRY(dalloc(g, w->slots, sizeof(double) * kSlots));
   GG_TRY(dalloc(g, w->scal, 8 * sizeof(double)));
   GG_TRY(dalloc(g, w->resid, sizeof(double) * (size_t)(max_iter + 1)));
-  GG_TRY(dalloc(g, w->done, sizeof(uint32_t)));
   return GRAPH_OK;
 }
 
 // A failed allocation leaves no half-built workspace behind for the next call.
-graph_status ensure_ws(graph* g, int prec, int max_iter, uint32_t nblocks) {
-  const graph_status s = alloc_ws(g, prec, max_iter, nblocks);
+graph_status ensure_ws(graph* g, int prec, int max_iter) {
+  const graph_status s = alloc_ws(g, prec, max_iter);
   if (s != GRAPH_OK) free_pr(g);
   return s;
 }
@@ -628,10 +656,8 @@ PrArgs make_args(graph* g, int cur, double damping) {
     zero += P.nv - P.cls_end[1];
   }
   A.scal = (double*)w->scal.p;
-  A.partials = (float*)w->partials.p;
-  A.partials64 = (double*)w->partials.p;
+  A.slots = (double*)w->slots.p;
   A.resid = (double*)w->resid.p;
-  A.done = (uint32_t*)w->done.p;
   A.damping = damping;
   A.n = (double)g->n;
   A.damping_f = (float)damping;
@@ -647,14 +673,14 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   cudaStream_t st = g->stream;
   const PrPlan pl = make_plan(g);
   GG_TRY((prepare_kernel<PR, false>()));
-  GG_TRY(ensure_ws(g, at.precision, at.max_iter, std::max<uint32_t>(pl.nitems, 1)));
+  GG_TRY(ensure_ws(g, at.precision, at.max_iter));
   PrWs* w = g->pr;
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
   const uint32_t nv0 = g->part[0].nv;
   int cur = 0;
-  GG_CUDA(cudaMemsetAsync(w->done.p, 0, sizeof(uint32_t), st));
+  GG_CUDA(cudaMemsetAsync(w->slots.p, 0, sizeof(double) * kSlots, st));
   {
     PrArgs A = make_args(g, cur, at.damping);
     k_pr_init<PR, false><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, MultiArgs{});
@@ -678,11 +704,13 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     timer.mark(2);
     if (nout) k_pr_publish<typename PR::XT><<<grid_for(nout, 256), 256, 0, st>>>(A);
     timer.mark(1);
-    if (pl.nitems)
+    if (pl.nitems) {
       k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
                                                                  MultiArgs{});
+      k_pr_finalize<<<1, kThreads, 0, st>>>(A, it, at.dangling);
+    }
     timer.mark(0);
-    launches += (nout ? 1 : 0) + (pl.nitems ? 1 : 0);
+    launches += (nout ? 1 : 0) + (pl.nitems ? 2 : 0);
     GG_CUDA(cudaGetLastError());
     cur = 1 - cur;
     ++it;
@@ -823,7 +851,7 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
   cudaStream_t st = g->stream;
   const PrPlan pl = make_plan(g);
   GG_TRY((prepare_kernel<PR, true>()));
-  GG_TRY(ensure_ws(g, at.precision, at.max_iter, std::max<uint32_t>(pl.nitems, 1)));
+  GG_TRY(ensure_ws(g, at.precision, at.max_iter));
   PrWs* w = g->pr;
   {
     const graph_status s = prepare_multi(g, w, G, vbase);
