@@ -13,13 +13,18 @@
 //    iteration's constant term and clears them. The FP64 additions happen in arrival
 //    order, so the residual's last bits can differ between runs; the ranks cannot.
 //
-// Work items (one CTA each): hub vertices (degree >= 2048; the CTA walks the adjacency in
-// chunks of kHubChunk edges, two chunks in flight: the bulk copy of chunk c+2 is issued as
-// soon as chunk c has been gathered), class tiles (kLeafEdges >> (c-1) vertices of degree
-// class c, so at most kTileE edges; one lane, a lane group or a warp per vertex), and
-// tiles of degree-zero vertices. A CTA stages its item's edge ids, offsets and previous
-// ranks into shared memory with bulk copies (TMA engine) completing on an mbarrier, issues
-// all of its gathers before consuming any, then reduces per vertex from shared memory.
+// Work items (one CTA each): hub chunks (kHubChunk edges of a vertex of degree >= 2048;
+// the chunk's partial sum goes to hubsum[item], and k_pr_hubs then adds each hub's chunk
+// sums in chunk order and updates the hub), class tiles (kLeafEdges >> (c-1) vertices of
+// degree class c, so at most kTileE edges; 2^(c-3) threads per vertex, one round) and
+// tiles of degree-zero vertices. Items are resolved once per workspace into a table of
+// 32-byte records (edge range, vertex range, kind), read with an L2 keep-resident hint, so
+// a CTA issues its bulk copies after one L2 hit. A CTA stages its item's edge ids, offsets
+// and previous ranks into shared memory with bulk copies (TMA engine) completing on an
+// mbarrier, issues all of its gathers before consuming any, then reduces per vertex from
+// shared memory. Nothing in a CTA waits for another CTA: short-lived CTAs keep 8 per SM
+// resident, and the number of gathers in flight per SM is what sets the speed (the
+// kernel is bound by gather latency, not by bandwidth).
 //
 // Degree-zero vertices: their neighbour sum is empty, so each of them holds exactly the
 // iteration's constant term. Their share of the dangling mass D and of the residual is
@@ -58,6 +63,8 @@ struct PrWs {
   size_t rsize = 0;  // bytes per stored rank
   DevBuf r[2], x[2][2], ghost[2];
   DevBuf slots, scal, resid;
+  DevBuf items, hubsum;      // resolved work items and hub-chunk partial sums
+  uint32_t items_n = 0;      // items resolved for the current partition (0: not yet)
   int max_iter = 0;
   MultiWs* multi = nullptr;
 };
@@ -83,6 +90,8 @@ void free_pr(graph* g) {
     for (DevBuf* b : all) dfree(g, *b);
   }
   dfree(g, w->slots);
+  dfree(g, w->items);
+  dfree(g, w->hubsum);
   dfree(g, w->scal);
   dfree(g, w->resid);
   delete w;
@@ -106,8 +115,12 @@ struct PrSide {
 // [4] the constant term rounded to FP32 (stored as a float in the first half).
 constexpr uint32_t kSlots = 1024;  // FP64 residual slots (block b adds to slot b % kSlots)
 
+struct PrItem;
+
 struct PrArgs {
   PrSide side[2];
+  const PrItem* items;  // [nitems] resolved work items
+  void* hubsum;         // [nitems] partial sum of each hub-chunk item (accumulation type)
   double* scal;
   double* slots;      // [kSlots] residual partial sums, zero between iterations
   double* resid;      // residual history
@@ -220,6 +233,7 @@ struct PrPlan {
   PrRange r[kMaxRange];
   int nr;
   uint32_t nitems;
+  uint32_t hub_item0[2];  // first hub-chunk item of each partition
 };
 
 struct Desc {
@@ -243,44 +257,95 @@ __device__ __forceinline__ int find_range(const PrPlan& P, uint32_t item) {
   return lo;
 }
 
-// Thread 0: describe `item` and start the bulk copies of its edge ids (and offsets, for
-// class tiles) into shared memory; `bar` completes when the bytes have landed.
+// One work item, resolved once per workspace by k_pr_items so that a CTA starts its bulk
+// copies after a single (L2-resident) 32-byte load instead of a search of the range table
+// and two dependent offset loads from DRAM.
+struct PrItem {
+  int64_t e0, e1;     // edge range (a hub chunk's edges, a class tile's adjacencies)
+  uint32_t v0, v1;    // vertex range (hub chunk: its vertex, v1 = v0 + 1)
+  uint8_t kind, part, gshift, pad;
+  uint32_t pad2;
+};
+static_assert(sizeof(PrItem) == 32, "PrItem is two 16-byte loads");
+
+__global__ void k_pr_items(const __grid_constant__ PrPlan P, const __grid_constant__ PrArgs A,
+                           PrItem* items) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.nitems) return;
+  const PrRange& R = P.r[find_range(P, k)];
+  const PartView& V = A.side[R.part].P;
+  const uint32_t j = k - R.item0;
+  PrItem it;
+  it.kind = R.kind;
+  it.part = R.part;
+  it.gshift = R.gshift;
+  it.pad = 0;
+  it.pad2 = 0;
+  if (R.kind == kItemHub) {  // hub chunk j of the partition
+    it.v0 = V.chunk_vertex[j];
+    it.v1 = it.v0 + 1;
+    it.e0 = V.chunk_first[j];
+    it.e1 = min(it.e0 + (int64_t)kHubChunk, V.off[it.v0 + 1]);
+  } else {
+    it.v0 = R.first + j * R.per;
+    it.v1 = min(it.v0 + R.per, R.end);
+    it.e0 = R.kind == kItemLeaf ? V.off[it.v0] : 0;
+    it.e1 = R.kind == kItemLeaf ? V.off[it.v1] : 0;
+  }
+  items[k] = it;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ PrItem load_item(const PrItem* p) {
+  const uint64_t pol = l2_evict_last_policy();
+  uint64_t a, b, c, d;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+               : "=l"(a), "=l"(b) : "l"(p), "l"(pol));
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+               : "=l"(c), "=l"(d) : "l"(reinterpret_cast<const char*>(p) + 16), "l"(pol));
+  PrItem it;
+  it.e0 = (int64_t)a;
+  it.e1 = (int64_t)b;
+  it.v0 = (uint32_t)c;
+  it.v1 = (uint32_t)(c >> 32);
+  it.kind = (uint8_t)d;
+  it.part = (uint8_t)(d >> 8);
+  it.gshift = (uint8_t)(d >> 16);
+  it.pad = 0;
+  it.pad2 = 0;
+  return it;
+}
+
+// Thread 0: describe item k and start the bulk copies of its edge ids (and, for class
+// tiles, offsets and previous ranks) into shared memory; `bar` completes when the bytes
+// have landed.
 template <class RT>
-__device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc& d,
-                           uint32_t* sE, int64_t* sOff, RT* sR, uint64_t* bar) {
-  const PrRange& R = P.r[find_range(P, item)];
-  const PrSide& S = A.side[R.part];
-  d.kind = R.kind;
-  d.part = R.part;
-  d.gshift = R.gshift;
+__device__ void issue_item(const PrArgs& A, uint32_t k, Desc& d, uint32_t* sE, int64_t* sOff,
+                           RT* sR, uint64_t* bar) {
+  const PrItem it = load_item(A.items + k);
+  const PrSide& S = A.side[it.part];
+  d.kind = it.kind;
+  d.part = it.part;
+  d.gshift = it.gshift;
   d.pad = 0;
   d.eshift = d.oshift = d.rshift = 0;
-  const uint32_t j = item - R.item0;
-  if (R.kind == kItemHub) {
-    d.v0 = R.first + j;
-    d.v1 = d.v0 + 1;
-    d.e0 = S.P.off[d.v0];
-    d.e1 = S.P.off[d.v0 + 1];
-  } else {
-    d.v0 = R.first + j * R.per;
-    d.v1 = min(d.v0 + R.per, R.end);
-    d.e0 = d.e1 = 0;
-    if (R.kind == kItemLeaf) {
-      d.e0 = S.P.off[d.v0];
-      d.e1 = S.P.off[d.v1];
-    }
-  }
+  d.v0 = it.v0;
+  d.v1 = it.v1;
+  d.e0 = it.e0;
+  d.e1 = it.e1;
   uint32_t ebytes = 0, obytes = 0, rbytes = 0, o0 = 0, q0 = 0;
   int64_t a0 = 0;
-  if (R.kind != kItemZero) {
-    // hubs: the first chunk only; the kernel streams the rest
-    const int64_t e1 = R.kind == kItemHub ? min(d.e1, d.e0 + (int64_t)kHubChunk) : d.e1;
+  if (it.kind != kItemZero) {
     a0 = d.e0 & ~(int64_t)3;
-    const int64_t a1 = (e1 + 3) & ~(int64_t)3;
+    const int64_t a1 = (d.e1 + 3) & ~(int64_t)3;
     d.eshift = (uint32_t)(d.e0 - a0);
     ebytes = (uint32_t)((a1 - a0) * 4);
   }
-  if (R.kind == kItemLeaf) {
+  if (it.kind == kItemLeaf) {
     o0 = d.v0 & ~1u;
     const uint32_t o1 = (d.v1 + 2) & ~1u;
     d.oshift = d.v0 - o0;
@@ -297,16 +362,6 @@ __device__ void issue_item(const PrPlan& P, const PrArgs& A, uint32_t item, Desc
   if (ebytes) bulk_g2s_stream(sE, S.P.E + a0, ebytes, bar, pol);
   if (obytes) bulk_g2s_stream(sOff, S.P.off + o0, obytes, bar, pol);
   if (rbytes) bulk_g2s_stream(sR, (const RT*)S.r + q0, rbytes, bar, pol);
-}
-
-// Bulk copy of hub chunk c of the adjacency [e0, e1) into buf (16-byte granules).
-__device__ __forceinline__ void issue_chunk(const uint32_t* E, int64_t e0, int64_t e1, int c,
-                                            uint32_t* buf, uint64_t* bar) {
-  const int64_t cs = e0 + (int64_t)c * kHubChunk, ce = min(cs + (int64_t)kHubChunk, e1);
-  const int64_t a0 = cs & ~(int64_t)3, a1 = (ce + 3) & ~(int64_t)3;
-  const uint32_t bytes = (uint32_t)((a1 - a0) * 4);
-  mbar_expect_tx(bar, bytes);
-  bulk_g2s_stream(buf, E + a0, bytes, bar, l2_evict_first_policy());
 }
 
 template <class PR>
@@ -355,16 +410,13 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
                               : reinterpret_cast<AT*>(smem);
   using RT = typename PR::RT;
   RT* sR = reinterpret_cast<RT*>(smem + ranks_offset<PR>());
-  __shared__ uint64_t bar, bar2;
+  __shared__ uint64_t bar;
   __shared__ Desc dsh;
   __shared__ AT red[kThreads / 32];
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
-    mbar_init(&bar2, 1);
     fence_mbar_init();
-    issue_item<RT>(plan, A, blockIdx.x, dsh, sE, sOff, sR, &bar);
-    if (dsh.kind == kItemHub && dsh.e1 - dsh.e0 > kHubChunk)
-      issue_chunk(A.side[dsh.part].P.E, dsh.e0, dsh.e1, 1, reinterpret_cast<uint32_t*>(sOff), &bar2);
+    issue_item<RT>(A, blockIdx.x, dsh, sE, sOff, sR, &bar);
   }
   __syncthreads();
   const bool ok = mbar_wait_bounded(&bar, 0, A.err);
@@ -373,37 +425,25 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
     const Desc d = dsh;
     const PrSide& S = A.side[d.part];
     if (d.kind == kItemHub) {
-      // Stream the hub's adjacency: chunk c sits in buffer c & 1 (edge-id stage or the
-      // offset stage reused), completing on bar / bar2 in alternating phases.
-      const int nch = (int)((d.e1 - d.e0 + kHubChunk - 1) / kHubChunk);
-      uint32_t* buf[2] = {sE, reinterpret_cast<uint32_t*>(sOff)};
-      AT s = 0;
-      bool ok2 = true;
-      for (int c = 0; c < nch; ++c) {
-        const int b = c & 1;
-        if (c > 0) {
-          ok2 = mbar_wait_bounded(b ? &bar2 : &bar, (c >> 1) & 1, A.err);
-          if (!__syncthreads_and(ok2)) break;
-        }
-        const int64_t cs = d.e0 + (int64_t)c * kHubChunk;
-        const int cnt = (int)(min(cs + (int64_t)kHubChunk, d.e1) - cs);
-        const uint32_t* src = buf[b] + (cs & 3);
-        uint32_t e[kPerThread];
-        #pragma unroll
-        for (int u = 0; u < kPerThread; ++u) {
-          const int i = threadIdx.x + u * kThreads;
-          e[u] = i < cnt ? src[i] : 0u;
-        }
-        #pragma unroll
-        for (int u = 0; u < kPerThread; ++u)
-          if (threadIdx.x + u * kThreads < cnt) s += gather<PR>(S, e[u]);
-        __syncthreads();  // buffer b fully read
-        if (threadIdx.x == 0 && c + 2 < nch) issue_chunk(S.P.E, d.e0, d.e1, c + 2, buf[b], b ? &bar2 : &bar);
+      // One chunk (at most kHubChunk edges) of a hub's adjacency: its partial sum goes to
+      // hubsum[item]; k_pr_hubs adds a hub's chunks in order and updates the vertex.
+      const int cnt = (int)(d.e1 - d.e0);
+      const uint32_t* src = sE + d.eshift;
+      uint32_t e[kPerThread];
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        e[u] = i < cnt ? src[i] : 0u;
       }
-      const AT sum = block_sum<AT>(s, red);
-      if (threadIdx.x == 0 && ok2)
-        res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0, sum, (int)(d.e1 - d.e0),
-                                        (AT)((const RT*)S.r)[d.v0]);
+      AT v[kPerThread];
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u)
+        v[u] = (threadIdx.x + u * kThreads < cnt) ? gather<PR>(S, e[u]) : (AT)0;
+      AT sum = 0;
+      #pragma unroll
+      for (int u = 0; u < kPerThread; ++u) sum += v[u];
+      sum = block_sum<AT>(sum, red);
+      if (threadIdx.x == 0) ((AT*)A.hubsum)[blockIdx.x] = sum;
     } else if (d.kind == kItemLeaf) {
       const int cnt = (int)(d.e1 - d.e0);
       const uint32_t* src = sE + d.eshift;
@@ -481,6 +521,37 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
     }
   }
   // Components keep no global scalars: their constants come from the host's table.
+  if (MULTI) return;
+  res = block_sum<AT>(res, red);
+  if (threadIdx.x == 0) atomicAdd(A.slots + (blockIdx.x % kSlots), (double)res);
+}
+
+// Hub vertices (degree >= kHubChunk), one warp each: the sum of the vertex's chunk partial
+// sums in chunk order, then the vertex update. Runs after k_pr_compute in every iteration.
+template <class PR, bool MULTI>
+__global__ void __launch_bounds__(kThreads)
+k_pr_hubs(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs A, int iter,
+          const __grid_constant__ MultiArgs M) {
+  using AT = typename PR::AT;
+  using RT = typename PR::RT;
+  __shared__ AT red[kThreads / 32];
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nh0 = A.side[0].P.bstart[1], nh1 = A.side[1].P.bstart[1];
+  AT res = 0;
+  if (w < nh0 + nh1) {
+    const int p = w < nh0 ? 0 : 1;
+    const uint32_t v = p ? w - nh0 : w;
+    const PrSide& S = A.side[p];
+    const int64_t deg = S.P.off[v + 1] - S.P.off[v];
+    const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
+    const AT* hs = (const AT*)A.hubsum + plan.hub_item0[p] + S.P.hub_chunk0[v];
+    AT sum = 0;
+    for (uint32_t c = lane_id(); c < nch; c += 32) sum += hs[c];
+    sum = warp_sum(sum);
+    if (lane_id() == 0)
+      res = update_vertex<PR, MULTI>(S, A, M, p, iter, v, sum, (int)deg,
+                                     (AT)((const RT*)S.r)[v]);
+  }
   if (MULTI) return;
   res = block_sum<AT>(res, red);
   if (threadIdx.x == 0) atomicAdd(A.slots + (blockIdx.x % kSlots), (double)res);
@@ -585,7 +656,8 @@ PrPlan make_plan(graph* g) {
   };
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
-    add(P.nhub, 0, P.nhub, 1, kItemHub, p, 8);
+    pl.hub_item0[p] = pl.nitems;
+    add(P.nchunk, 0, P.nchunk, 1, kItemHub, p, 8);
     for (int c = kClassHub - 1; c >= 1; --c) {
       const uint32_t v0 = P.cls_end[c + 1], v1 = P.cls_end[c];
       const uint32_t per = std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1));
@@ -640,6 +712,25 @@ graph_status ensure_ws(graph* g, int prec, int max_iter) {
   return s;
 }
 
+PrArgs make_args(graph* g, int cur, double damping);
+
+// Resolves the plan's work items once per workspace (the partition and the plan do not
+// change while the workspace lives).
+template <class PR>
+graph_status prepare_items(graph* g, PrWs* w, const PrPlan& pl) {
+  if (w->items_n == pl.nitems || pl.nitems == 0) return GRAPH_OK;
+  dfree(g, w->items);
+  dfree(g, w->hubsum);
+  w->items_n = 0;
+  GG_TRY(dalloc(g, w->items, sizeof(PrItem) * (size_t)pl.nitems));
+  GG_TRY(dalloc(g, w->hubsum, sizeof(typename PR::AT) * (size_t)pl.nitems));
+  k_pr_items<<<grid_for(pl.nitems, 256), 256, 0, g->stream>>>(pl, make_args(g, 0, 0.85),
+                                                              (PrItem*)w->items.p);
+  GG_CUDA(cudaGetLastError());
+  w->items_n = pl.nitems;
+  return GRAPH_OK;
+}
+
 PrArgs make_args(graph* g, int cur, double damping) {
   PrWs* w = g->pr;
   PrArgs A;
@@ -657,6 +748,8 @@ PrArgs make_args(graph* g, int cur, double damping) {
   }
   A.scal = (double*)w->scal.p;
   A.slots = (double*)w->slots.p;
+  A.items = (const PrItem*)w->items.p;
+  A.hubsum = w->hubsum.p;
   A.resid = (double*)w->resid.p;
   A.damping = damping;
   A.n = (double)g->n;
@@ -675,6 +768,7 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   GG_TRY((prepare_kernel<PR, false>()));
   GG_TRY(ensure_ws(g, at.precision, at.max_iter));
   PrWs* w = g->pr;
+  GG_TRY(prepare_items<PR>(g, w, pl));
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
@@ -695,6 +789,7 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     GG_CUDA(cudaStreamSynchronize(st));
   }
   const uint32_t nout = g->part[0].nout + g->part[1].nout;
+  const uint32_t nhubs = g->part[0].nhub + g->part[1].nhub;
   const size_t smem = smem_bytes<PR>();
   int it = 0;
   int64_t launches = 1;
@@ -707,10 +802,13 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     if (pl.nitems) {
       k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
                                                                  MultiArgs{});
+      if (nhubs)
+        k_pr_hubs<PR, false><<<grid_for(nhubs, kThreads / 32), kThreads, 0, st>>>(pl, A, it,
+                                                                                   MultiArgs{});
       k_pr_finalize<<<1, kThreads, 0, st>>>(A, it, at.dangling);
     }
     timer.mark(0);
-    launches += (nout ? 1 : 0) + (pl.nitems ? 2 : 0);
+    launches += (nout ? 1 : 0) + (pl.nitems ? 2 : 0) + (pl.nitems && nhubs ? 1 : 0);
     GG_CUDA(cudaGetLastError());
     cur = 1 - cur;
     ++it;
@@ -853,6 +951,7 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
   GG_TRY((prepare_kernel<PR, true>()));
   GG_TRY(ensure_ws(g, at.precision, at.max_iter));
   PrWs* w = g->pr;
+  GG_TRY(prepare_items<PR>(g, w, pl));
   {
     const graph_status s = prepare_multi(g, w, G, vbase);
     if (s != GRAPH_OK) {
@@ -915,6 +1014,7 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
   timer.mark(2);
   // The K supersteps (publish + compute) as one CUDA graph, captured on a private stream
   // and replayed while the layout, the workspace, K and the damping stay the same.
+  const uint32_t nhubs = g->part[0].nhub + g->part[1].nhub;
   const uint32_t nout = g->part[0].nout + g->part[1].nout;
   const size_t smem = smem_bytes<PR>();
   if (!m->exec || m->iters != K || m->damping != d || m->dangling != at.dangling) {
@@ -930,6 +1030,9 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
       if (pl.nitems)
         k_pr_compute<PR, true><<<pl.nitems, kThreads, smem, m->capture>>>(pl, A, it,
                                                                           at.dangling, M);
+      if (pl.nitems && nhubs)
+        k_pr_hubs<PR, true><<<grid_for(nhubs, kThreads / 32), kThreads, 0, m->capture>>>(
+            pl, A, it, M);
       cur = 1 - cur;
     }
     cudaGraph_t graph = nullptr;
@@ -974,7 +1077,8 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
     stats->edges_inspected = g->m * (int64_t)K;
     stats->messages = (int64_t)nout * K;
     stats->residual = total;
-    stats->launches = 2 + (int64_t)K * ((nout ? 1 : 0) + (pl.nitems ? 1 : 0));
+    stats->launches =
+        2 + (int64_t)K * ((nout ? 1 : 0) + (pl.nitems ? 1 : 0) + (pl.nitems && nhubs ? 1 : 0));
   }
   timer.finish(stats);
   return s;
