@@ -216,6 +216,11 @@ graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t k, uint32_t
  * atomic minimum on the target (boundary targets reduce into their outbox slot), and the
  * exchange applies the outbox minima to the owner. Rounds end when no vertex is active.
  *   dist   n uint32: shortest distance, INF if unreachable. Requires weights.
+ *   attr->delta  0: every improved vertex is active in the next round (Figure 20).
+ *          > 0: near-far order, an extension not in the paper: only improved vertices with
+ *          distance below a threshold are active; the others wait, and when no vertex is
+ *          active the threshold becomes the smallest waiting distance + delta. Same
+ *          distances, fewer wasted relaxations.
  * Sums saturate below INF; if a true distance would reach 2^32 - 1 the call returns
  * ERANGE. Errors: EINVAL (source >= n, NULL dist, no weights), ESTATE, ETIMEOUT, ERANGE,
  * ENOMEM, ECUDA.
@@ -224,6 +229,7 @@ typedef struct {
   int out_mem;
   int max_supersteps; /* <= 0: no cap other than n + 1 */
   int timing;
+  uint32_t delta;     /* 0: plain active-set rounds; > 0: near-far bucket width */
 } sssp_attr;
 
 graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* attr,
@@ -361,6 +367,7 @@ typedef struct {
   uint32_t bfs_lanes;  /* BFS lanes, 1..64 (0: 64) */
   uint32_t max_sssp;   /* upper bound on SSSP slots (0: 64); the budget may allow fewer */
   int out_mem;         /* GRAPH_MEM_HOST (pinned recommended) or _DEVICE for outputs */
+  uint32_t sssp_delta; /* SSSP queries: near-far bucket width (0: plain rounds), as sssp() */
 } graph_server_attr;
 
 typedef struct {

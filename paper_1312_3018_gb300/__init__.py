@@ -227,12 +227,13 @@ def bfs_batch(g: Graph, sources, levels=None, *, direction: str = "auto", alpha:
 
 
 def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_supersteps: int = 0,
-         timing: bool = False):
-    """Shortest distances (uint32, INF unreachable) in global vertex order, and stats."""
+         timing: bool = False, delta: int = 0):
+    """Shortest distances (uint32, INF unreachable) in global vertex order, and stats.
+    delta = 0: plain active-set rounds (Figure 20); delta > 0: near-far order."""
     torch = _torch()
     dist = _out_u32(torch, g.n, out, dist)
     pd, mem = _ptr(dist)
-    attr = _lib.sssp_attr(mem, max_supersteps, int(timing))
+    attr = _lib.sssp_attr(mem, max_supersteps, int(timing), int(delta))
     stats = _lib.graph_stats()
     st = _lib.load().sssp(g.handle, int(source), pd, C.byref(attr), C.byref(stats))
     _lib.check(st, "sssp")
@@ -323,12 +324,13 @@ class Server:
     KINDS = {"bfs": _lib.GRAPH_QUERY_BFS, "sssp": _lib.GRAPH_QUERY_SSSP}
 
     def __init__(self, g: Graph, *, mem_budget: int = 0, bfs_lanes: int = 0, max_sssp: int = 0,
-                 out: str = "device"):
+                 out: str = "device", sssp_delta: int = 0):
         _torch()
         self.g = g
         self.out = out
         mem = GRAPH_MEM_DEVICE if out == "device" else GRAPH_MEM_HOST
-        attr = _lib.graph_server_attr(int(mem_budget), int(bfs_lanes), int(max_sssp), mem)
+        attr = _lib.graph_server_attr(int(mem_budget), int(bfs_lanes), int(max_sssp), mem,
+                                      int(sssp_delta))
         h = C.c_void_p(0)
         _lib.check(_lib.load().graph_server_create(g.handle, C.byref(attr), C.byref(h)),
                    "graph_server_create")

@@ -64,7 +64,7 @@ class cc_attr(C.Structure):
 
 class graph_server_attr(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("bfs_lanes", C.c_uint32), ("max_sssp", C.c_uint32),
-                ("out_mem", C.c_int)]
+                ("out_mem", C.c_int), ("sssp_delta", C.c_uint32)]
 
 
 class graph_completion(C.Structure):
@@ -103,7 +103,8 @@ class bfs_attr(C.Structure):
 
 
 class sssp_attr(C.Structure):
-    _fields_ = [("out_mem", C.c_int), ("max_supersteps", C.c_int), ("timing", C.c_int)]
+    _fields_ = [("out_mem", C.c_int), ("max_supersteps", C.c_int), ("timing", C.c_int),
+                ("delta", C.c_uint32)]
 
 
 class pagerank_attr(C.Structure):

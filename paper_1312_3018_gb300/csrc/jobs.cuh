@@ -15,9 +15,10 @@ size_t sssp_job_bytes(const graph* g);  // device bytes one job holds
 graph_status sssp_job_create(graph* g, SsspJob** out);
 void sssp_job_destroy(graph* g, SsspJob* j);
 // Starts a search from source; the distances go to dst (n uint32, global order; host
-// memory should be pinned) when the job finishes.
+// memory should be pinned) when the job finishes. delta: near-far bucket width (0: plain
+// active-set rounds).
 graph_status sssp_job_start(graph* g, SsspJob* j, uint32_t source, uint32_t* dst,
-                            int dst_mem);
+                            int dst_mem, uint32_t delta);
 // Non-blocking: 0 while running, 1 once dst holds the result, < 0 a graph_status error
 // (the job is then idle). *rounds receives the supersteps run so far.
 int sssp_job_poll(graph* g, SsspJob* j, int* rounds);

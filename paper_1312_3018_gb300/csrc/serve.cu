@@ -55,6 +55,7 @@ using namespace gg;
 struct graph_server {
   graph* g = nullptr;
   int out_mem = GRAPH_MEM_HOST;
+  uint32_t sssp_delta = 0;  // near-far bucket width of the SSSP jobs
   Clock::time_point t0;
   BfsLanes* lanes = nullptr;
   uint32_t nlanes = 0;
@@ -228,7 +229,8 @@ bool step_jobs(graph_server* s, std::deque<Query>& pend) {
       Query q = pend.front();
       pend.pop_front();
       q.t_admit = s->now();
-      const graph_status st = sssp_job_start(g, s->jobs[i], q.source, q.out, s->out_mem);
+      const graph_status st =
+          sssp_job_start(g, s->jobs[i], q.source, q.out, s->out_mem, s->sssp_delta);
       if (st != GRAPH_OK) {
         emit(s, q, st, s->now());
       } else {
@@ -362,6 +364,7 @@ graph_status graph_server_create(graph_t* g, const graph_server_attr* attr,
   if (!s) return GRAPH_ENOMEM;
   s->g = g;
   s->out_mem = at.out_mem;
+  s->sssp_delta = at.sssp_delta;
   s->t0 = Clock::now();
   graph_status st = build(s, at);
   if (st == GRAPH_OK) {

@@ -17,6 +17,12 @@
 //    hubs as edge chunks); the search ends when that set is empty. A non-hub vertex lowered
 //    while it waits in the current round is relaxed with its newest distance and not
 //    re-queued, the paper's same-round activation.
+//  - optional near-far order (delta > 0): only improved vertices with distance below a
+//    threshold are activated; the others keep their touched mark and wait. When the
+//    active set runs dry the threshold moves to the smallest waiting distance + delta and
+//    the filter runs again. Every improved vertex is still relaxed with its final
+//    distance, so the distances are the same; fewer relaxations are wasted on distances
+//    that later improve.
 // Distances are uint32; a relaxation saturates at 0xFFFFFFFE and flags an overflow.
 #include <string.h>
 
@@ -28,7 +34,8 @@ namespace gg {
 struct SsspCounters {
   uint32_t tail[2][kNBucket];  // next-round work: [0] hub chunks, [1..3] vertices
   uint32_t overflow;
-  uint32_t pad;
+  uint32_t far;                // improved vertices left pending at or above the threshold
+  uint32_t far_key;            // max of ~dist over them (so zero-initialised counters work)
   unsigned long long inspected;
   unsigned long long messages;
   unsigned long long reached_degree;  // filled by the final reduction
@@ -209,15 +216,17 @@ __global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constan
 }
 
 // Filter: touched vertices whose distance dropped below the value they were last relaxed
-// with form the next active set. One lane per bitmap word; lanes walk their set bits in
-// step so that appends stay warp-aggregated.
+// with form the next active set, when that distance is below tau; the others stay touched
+// (pending) and are counted, with their smallest distance. One lane per bitmap word; lanes
+// walk their set bits in step so that appends stay warp-aggregated.
 __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant__ SsspArgs A,
-                                                          uint32_t words0, uint32_t words) {
+                                                          uint32_t words0, uint32_t words,
+                                                          uint32_t tau) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
   const SsspSide& S = A.side[p];
-  uint32_t bits = 0;
+  uint32_t bits = 0, keep = 0, nfar = 0, key = 0;
   if (i < words) {
     bits = S.touched[word];
     if (bits) S.touched[word] = 0;
@@ -231,12 +240,25 @@ __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant_
       x = word * 32 + b;
       const uint32_t d = S.dist[x];
       if (d < S.snap[x]) {
-        S.snap[x] = d;  // queued with d
-        act = true;
+        if (d < tau) {
+          S.snap[x] = d;  // queued with d
+          act = true;
+        } else {
+          keep |= 1u << b;
+          nfar++;
+          key = max(key, ~d);
+        }
       }
     }
     warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
                          S.nhubq);
+  }
+  if (keep) S.touched[word] = keep;
+  nfar = warp_sum(nfar);
+  key = __reduce_max_sync(kFull, key);
+  if (lane_id() == 0 && nfar) {
+    atomicAdd(&A.ctr->far, nfar);
+    atomicMax(&A.ctr->far_key, key);
   }
 }
 
@@ -404,7 +426,7 @@ uint64_t active_count(const SsspCounters& c) {
 // One round: relax the active set c describes (queues `cur`), apply the outbox, filter.
 graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCounters& c,
                           int cur, cudaStream_t st, PhaseTimer* timer, int64_t* launches,
-                          bool cc = false) {
+                          bool cc = false, uint32_t tau = kInf) {
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
   const SsspArgs A = make_args(g, w, ctr, cur);
   Plan pl;
@@ -429,10 +451,29 @@ graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCoun
   if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(1);
-  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(0);
   *launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+  return GRAPH_OK;
+}
+
+// Near-far: the active set is empty but improved vertices wait at or above the threshold.
+// The next threshold is their smallest distance + delta; the filter alone then queues
+// those below it for the round that reads queues `cur`.
+uint32_t next_threshold(const SsspCounters& c, uint32_t delta) {
+  const uint64_t t = (uint64_t)(~c.far_key) + delta;
+  return t >= kInf ? kInf : (uint32_t)t;
+}
+
+graph_status launch_refilter(graph* g, SsspWs* w, SsspCounters* ctr, int cur, uint32_t tau,
+                             cudaStream_t st, int64_t* launches) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
+  const SsspArgs A = make_args(g, w, ctr, 1 - cur);  // appends into queues `cur`
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
+  GG_CUDA(cudaGetLastError());
+  *launches += 1;
   return GRAPH_OK;
 }
 
@@ -467,6 +508,8 @@ struct SsspJob {
   int phase = 0;               // 0 idle, 1 round in flight, 2 collect in flight
   int64_t rounds = 0;
   bool overflow = false;
+  uint32_t delta = 0;          // near-far bucket width (0: plain rounds)
+  uint32_t tau = kInf;         // current near-far threshold
 };
 
 size_t sssp_job_bytes(const graph* g) {
@@ -514,7 +557,9 @@ graph_status sssp_job_create(graph* g, SsspJob** out) {
 }
 
 graph_status sssp_job_start(graph* g, SsspJob* j, uint32_t source, uint32_t* dst,
-                            int dst_mem) {
+                            int dst_mem, uint32_t delta) {
+  j->delta = delta;
+  j->tau = delta ? delta : kInf;
   j->dst = dst;
   j->dst_mem = dst_mem;
   j->cur = 0;
@@ -550,6 +595,17 @@ int sssp_job_poll(graph* g, SsspJob* j, int* rounds) {
   }
   const SsspCounters c = *j->hc;
   j->overflow |= c.overflow != 0;
+  if (active_count(c) == 0 && c.far != 0) {
+    // near-far: raise the threshold and queue the waiting vertices below it
+    int64_t launches = 0;
+    j->tau = next_threshold(c, j->delta);
+    graph_status s = launch_refilter(g, &j->ws, dc, j->cur, j->tau, j->st, &launches);
+    if (s != GRAPH_OK) return job_fail(j, s);
+    cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+    if (e != cudaSuccess) return job_fail(j, cuda_fail(e, "sssp job refilter", __FILE__, __LINE__));
+    return 0;
+  }
   if (active_count(c) == 0) {
     uint32_t* out = j->dst_mem == GRAPH_MEM_DEVICE ? j->dst : (uint32_t*)j->stage.p;
     graph_status s = launch_collect(g, &j->ws, dc, j->cur, out, j->st);
@@ -569,7 +625,8 @@ int sssp_job_poll(graph* g, SsspJob* j, int* rounds) {
     return job_fail(j, GRAPH_ETIMEOUT);
   }
   int64_t launches = 0;
-  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches);
+  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches, false,
+                                j->tau);
   if (s != GRAPH_OK) return job_fail(j, s);
   cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, j->st);
   if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
@@ -625,15 +682,24 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
   bool overflow = false;
   int64_t rounds = 0;
   int cur = 0;
+  uint32_t tau = at.delta ? at.delta : kInf;  // the source has distance 0 < delta
   for (;; ++rounds) {
-    const SsspCounters c = *hc;
+    SsspCounters c = *hc;
+    while (active_count(c) == 0 && c.far != 0) {
+      // near-far: nothing below the threshold; move it up to the waiting vertices
+      tau = next_threshold(c, at.delta);
+      GG_TRY(launch_refilter(g, w, dc, cur, tau, st, &launches));
+      GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+      c = *hc;
+    }
     if (active_count(c) == 0) break;
     if (rounds >= cap) {
       set_error("sssp reached the superstep cap (%lld)", (long long)cap);
       timer.finish(nullptr);
       return GRAPH_ETIMEOUT;
     }
-    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches));
+    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches, false, tau));
     GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;

@@ -8,8 +8,8 @@ with the oracle element by element for sampled sources, PageRank to an L1 residu
 RMAT scale 25 (33.5M vertices, ~1.05B edge entries): BFS levels against the oracle for one
 source and its parents validated; SSSP distances checked with the optimality certificate
 (every edge satisfies dist[v] <= dist[u] + w and every reached vertex has a tight
-predecessor, which fixes the distances exactly); PageRank after 3 iterations against the
-FP64 oracle.
+predecessor, which fixes the distances exactly), and the near-far order equal to them;
+PageRank after 3 iterations against the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -20,6 +20,7 @@ import synth
 pytestmark = pytest.mark.gpu
 INF = oracle.INF
 T = 2048
+NEAR_FAR_DELTA = 128
 
 
 @pytest.fixture(scope="module")
@@ -71,10 +72,11 @@ def test_rmat22_bfs_sixty_four_sources(gpu, rmat22, loaded22):
 def test_rmat22_sssp(gpu, rmat22, loaded22):
     g = rmat22
     for s in synth.sources(g, 2, seed=4):
-        d, st = gpu.sssp(loaded22, int(s), out="host")
         ref = oracle.sssp(g.n, g.offsets, g.cols, g.weights, int(s))
-        assert np.array_equal(d, ref)
-        assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+        for delta in (0, NEAR_FAR_DELTA):  # plain rounds, then the benchmark's near-far width
+            d, st = gpu.sssp(loaded22, int(s), out="host", delta=delta)
+            assert np.array_equal(d, ref), f"delta {delta}"
+            assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
 
 
 def test_rmat22_pagerank_to_residual_1e9(gpu, rmat22, loaded22):
@@ -106,6 +108,8 @@ def test_rmat25_sssp_certificate(gpu, rmat25, loaded25):
     d, st = gpu.sssp(loaded25, s, out="host")
     assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d) == 0
     assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, d)
+    d2, _ = gpu.sssp(loaded25, s, out="host", delta=NEAR_FAR_DELTA)
+    assert np.array_equal(d2, d)
 
 
 def test_rmat25_pagerank_three_iterations(gpu, rmat25, loaded25):

@@ -80,6 +80,17 @@ def test_server_mix_matches_oracle(gpu):
     H.free()
 
 
+def test_server_near_far_sssp_matches_oracle(gpu):
+    """SSSP jobs in near-far order (sssp_delta > 0): the same distances as the oracle, in a
+    mix with BFS queries."""
+    g = rmat_graph(14)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=64)
+    done, info = run_mix(gpu, H, g, mixed_queries(g, 80, 9), sssp_delta=16)
+    assert any(c["kind"] == "sssp" for c in done)
+    H.free()
+
+
 def test_server_lanes_join_while_others_run(gpu):
     """Staggered arrivals: some BFS query is admitted while another is still in flight, and
     both results are exact."""

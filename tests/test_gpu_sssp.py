@@ -89,3 +89,58 @@ def test_sssp_overflow_reports_range_error(gpu):
     with pytest.raises(gpu.GraphError, match="out of range"):
         gpu.sssp(H, 0)
     H.free()
+
+
+# Near-far order (delta > 0): the same distances with fewer wasted relaxations. Widths from
+# 1 (a bucket per distance value) to beyond every distance (one bucket: plain rounds).
+DELTAS = [1, 7, 64, 300, 1 << 30]
+
+
+@pytest.mark.parametrize("p", PARTITIONS, ids=part_id)
+def test_sssp_near_far_rmat14(gpu, p):
+    g = rmat_graph(14)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    apply_partition(gpu, H, g, p)
+    srcs = synth.sources(g, 2, seed=2)
+    refs = [oracle.sssp(g.n, g.offsets, g.cols, g.weights, int(s)) for s in srcs]
+    for delta in DELTAS:
+        for s, ref in zip(srcs, refs):
+            d, st = gpu.sssp(H, int(s), out="host", delta=delta)
+            assert np.array_equal(d, ref), f"delta {delta} src {s}"
+            assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+    H.free()
+
+
+def test_sssp_near_far_inspects_no_more_than_plain(gpu):
+    """On a power-law graph with wide weights, a moderate bucket width relaxes fewer edges
+    than plain rounds (and never a different distance)."""
+    g = rmat_graph(15, seed=3, wmax=255, wseed=4)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=256)
+    s = int(synth.sources(g, 1, seed=9)[0])
+    ref = oracle.sssp(g.n, g.offsets, g.cols, g.weights, s)
+    d0, st0 = gpu.sssp(H, s, out="host")
+    d1, st1 = gpu.sssp(H, s, out="host", delta=64)
+    assert np.array_equal(d0, ref) and np.array_equal(d1, ref)
+    assert st1["edges_inspected"] < st0["edges_inspected"]
+    H.free()
+
+
+def test_sssp_near_far_multi_chunk_hub_and_path(gpu):
+    g = star_plus(20000, extra_seed=6)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=3)
+    for s in (0, 5):
+        ref = oracle.sssp(g.n, g.offsets, g.cols, g.weights, s)
+        for delta in (1, 32):
+            d, _ = gpu.sssp(H, s, out="host", delta=delta)
+            assert np.array_equal(d, ref)
+    H.free()
+    n = 3000
+    w = np.random.default_rng(2).integers(1, 256, n - 1)
+    g = synth.from_edges(n, [(i, i + 1) for i in range(n - 1)], w=w)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(n, 0.5, 3))
+    d, st = gpu.sssp(H, n - 1, out="host", delta=100)
+    assert np.array_equal(d, np.concatenate([np.cumsum(w[::-1])[::-1], [0]]).astype(np.uint32))
+    H.free()
