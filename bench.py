@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched BFS and many-graph PageRank measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    ap.add_argument("--sssp-delta", type=int, default=64,
+                    help="near-far bucket width of the step's SSSP (0: plain active-set rounds)")
     return ap.parse_args()
 
 
@@ -142,10 +144,12 @@ def serving_bench(G, a, torch):
     srcs = synth.sources(g, 4096, seed=5)
     rng = np.random.default_rng(11)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    # near-far width scaled to this graph's weight range (1..64), in both forms
+    delta = max(1, round(a.sssp_delta * 64 / a.wmax)) if a.sssp_delta else 0
     # plain form: the same kind of queries one call at a time
     plain = []
     G.bfs(H, int(srcs[0]), out, want_parents=False)
-    G.sssp(H, int(srcs[0]), out)
+    G.sssp(H, int(srcs[0]), out, delta=delta)
     for i in range(100):
         s = int(srcs[rng.integers(len(srcs))])
         torch.cuda.synchronize()
@@ -153,14 +157,14 @@ def serving_bench(G, a, torch):
         if rng.random() < 0.7:
             G.bfs(H, s, out, want_parents=False)
         else:
-            G.sssp(H, s, out)
+            G.sssp(H, s, out, delta=delta)
         torch.cuda.synchronize()
         plain.append((time.perf_counter() - t) * 1e3)
     plain_qps = 1e3 * len(plain) / sum(plain)
     nbuf = 400
     bufs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)]
     points = []
-    with G.Server(H, out="device") as srv:
+    with G.Server(H, out="device", sssp_delta=delta) as srv:
         info0 = srv.info()
         for i in range(64):  # warm-up
             srv.submit("bfs" if i % 3 else "sssp", int(srcs[i]), bufs[i])
@@ -212,13 +216,14 @@ def serving_bench(G, a, torch):
             "sssp_slots": info["sssp_slots"], "max_lanes_busy": info["max_lanes_busy"],
             "max_slots_busy": info["max_slots_busy"],
             "bytes_lanes": info0["bytes_lanes"], "bytes_per_sssp": info0["bytes_per_sssp"],
-            "generate_s": round(gen_s, 2),
+            "generate_s": round(gen_s, 2), "sssp_delta": delta,
             "note": "graph_server (continuous batching: BFS lanes join and leave between "
                     "supersteps; SSSP jobs on their own streams); device outputs"}
 
 
 def workload_name(a):
-    return (f"rmat{a.scale}-ef{a.edge_factor} bfs+sssp(w1..{a.wmax})+pagerank-fp32x{a.pr_iters}"
+    sssp = f"sssp(w1..{a.wmax},near-far {a.sssp_delta})" if a.sssp_delta else f"sssp(w1..{a.wmax})"
+    return (f"rmat{a.scale}-ef{a.edge_factor} bfs+{sssp}+pagerank-fp32x{a.pr_iters}"
             f" degree-split T={a.threshold}")  # T may be 'auto' (chosen value in config)
 
 
@@ -405,7 +410,7 @@ def main():
         if out == "device":
             _, _, sb = G.bfs(H, s, lv, pa, out="device", timing=True)
             ev[1].record(stream)
-            _, ss = G.sssp(H, s, dd, out="device", timing=True)
+            _, ss = G.sssp(H, s, dd, out="device", timing=True, delta=a.sssp_delta)
             ev[2].record(stream)
             _, sp = G.pagerank(H, max_iter=a.pr_iters, precision="fp32", ranks=rr,
                                out="device", timing=True)
@@ -413,7 +418,7 @@ def main():
             hl, hp, hd, hr = bufs
             _, _, sb = G.bfs(H, s, hl, hp, out="host")
             ev[1].record(stream)
-            _, ss = G.sssp(H, s, hd, out="host")
+            _, ss = G.sssp(H, s, hd, out="host", delta=a.sssp_delta)
             ev[2].record(stream)
             _, sp = G.pagerank(H, max_iter=a.pr_iters, precision="fp32", ranks=hr, out="host")
         ev[3].record(stream)
@@ -481,8 +486,32 @@ def main():
                     "peak_kind": peak_kind}
     if pr_traffic:
         rl["k_pr_compute<fp32>"]["traffic"] = pr_traffic
+    rl["k_pr_compute<fp32>"]["timed"] = (
+        "CUDA events on the library's stream around each iteration's compute launches: "
+        "k_pr_compute plus the per-hub combine (k_pr_hubs) and the residual finalize "
+        "(k_pr_finalize), together about 1% of the interval")
 
     # FP64 and FP16-stored PageRank rates (same graph, same iteration count).
+    # SSSP in plain active-set rounds (Figure 20) on the step's sources, for reference
+    plain_sssp = {"delta": 0, "ms": 0.0, "edges_traversed": 0, "edges_relaxed": 0, "rounds": 0}
+    for k in range(min(a.steps, 4)):
+        s = int(srcs[k % len(srcs)])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, ss0 = G.sssp(H, s, dd, out="device", delta=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_sssp["ms"] += e0.elapsed_time(e1)
+        plain_sssp["edges_traversed"] += ss0["edges_traversed"]
+        plain_sssp["edges_relaxed"] += ss0["edges_inspected"]
+        plain_sssp["rounds"] += ss0["supersteps"]
+    nps = min(a.steps, 4)
+    plain_sssp = {"delta": 0, "ms_per_search": plain_sssp["ms"] / nps,
+                  "gteps": plain_sssp["edges_traversed"] / (plain_sssp["ms"] / 1e3) / 1e9,
+                  "edges_relaxed_per_search": plain_sssp["edges_relaxed"] / nps,
+                  "rounds_per_search": plain_sssp["rounds"] / nps}
+
     variants = {}
     for prec in ("fp64", "fp16"):
         G.pagerank(H, max_iter=a.pr_iters, precision=prec, ranks=rr, out="device")
@@ -692,6 +721,8 @@ def main():
             "sssp_rounds_per_search": sssp_rounds / a.steps,
             "bfs_edges_inspected_per_search": bfs_insp / a.steps,
             "sssp_edges_relaxed_per_search": sssp_insp / a.steps,
+            "sssp_delta": a.sssp_delta,
+            "sssp_plain_rounds": plain_sssp,
         },
         "roofline": dict(rl[dom], kernel=dom),
         "rooflines": rl,

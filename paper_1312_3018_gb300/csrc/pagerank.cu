@@ -383,19 +383,17 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return t;
 }
 
-// Values gathered for a class tile: in place over the staged edge ids when the
-// accumulator is 4 bytes wide, else in a separate buffer.
-template <class PR>
-__host__ __device__ constexpr size_t vals_bytes() {
-  return sizeof(typename PR::AT) == 4 ? 0 : sizeof(typename PR::AT) * kTileE;
-}
+// Shared memory of a CTA: the item's edge ids (at most kTileE), and for a class tile
+// (at most kPrTileV vertices: one round of the CTA's threads) its offsets and previous
+// ranks, each staged in whole 16-byte granules.
+constexpr int kPrTileV = kThreads;
 template <class PR>
 __host__ __device__ constexpr size_t ranks_offset() {
-  return 4 * (kTileE + 8) + 8 * (kTileV + 4) + vals_bytes<PR>();
+  return 4 * (kTileE + 8) + 8 * (kPrTileV + 4);
 }
 template <class PR>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return ranks_offset<PR>() + sizeof(typename PR::RT) * (kTileV + 8);
+  return ranks_offset<PR>() + sizeof(typename PR::RT) * (kPrTileV + 8);
 }
 
 template <class PR, bool MULTI>
@@ -406,8 +404,6 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sE = reinterpret_cast<uint32_t*>(smem);
   int64_t* sOff = reinterpret_cast<int64_t*>(smem + 4 * (kTileE + 8));
-  AT* vals = vals_bytes<PR>() ? reinterpret_cast<AT*>(smem + 4 * (kTileE + 8) + 8 * (kTileV + 4))
-                              : reinterpret_cast<AT*>(smem);
   using RT = typename PR::RT;
   RT* sR = reinterpret_cast<RT*>(smem + ranks_offset<PR>());
   __shared__ uint64_t bar;
@@ -445,61 +441,44 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
       sum = block_sum<AT>(sum, red);
       if (threadIdx.x == 0) ((AT*)A.hubsum)[blockIdx.x] = sum;
     } else if (d.kind == kItemLeaf) {
-      const int cnt = (int)(d.e1 - d.e0);
+      // Vertex j of the tile belongs to the 2^gs threads j << gs ...; they gather its edges
+      // at stride 2^gs (at most kPerThread each, since a class-c degree is below 2^c and
+      // 2^gs = 2^(c-3)) and add them in registers, so values never round-trip through
+      // shared memory.
+      const int gs = d.gshift;
+      const int nvt = (int)(d.v1 - d.v0);
+      const int64_t* so = sOff + d.oshift;
       const uint32_t* src = sE + d.eshift;
+      const int j = (int)(threadIdx.x >> gs);  // one round: nvt <= kThreads >> gs
+      const int gl = (int)(threadIdx.x & ((1u << gs) - 1));
+      int es = 0, ee = 0;
+      if (j < nvt) {
+        es = (int)(so[j] - d.e0);
+        ee = (int)(so[j + 1] - d.e0);
+      }
       uint32_t e[kPerThread];
       #pragma unroll
       for (int u = 0; u < kPerThread; ++u) {
-        const int i = threadIdx.x + u * kThreads;
-        e[u] = i < cnt ? src[i] : 0u;
+        const int i = es + gl + (u << gs);
+        e[u] = i < ee ? src[i] : 0u;
       }
       AT v[kPerThread];
       #pragma unroll
       for (int u = 0; u < kPerThread; ++u)
-        v[u] = (threadIdx.x + u * kThreads < cnt) ? gather<PR>(S, e[u]) : (AT)0;
-      // In-place values overwrite only the edge ids this thread itself read.
-      const int shift = vals_bytes<PR>() == 0 ? (int)d.eshift : 0;
+        v[u] = (es + gl + (u << gs) < ee) ? gather<PR>(S, e[u]) : (AT)0;
+      AT sm = 0;
       #pragma unroll
-      for (int u = 0; u < kPerThread; ++u) {
-        const int i = threadIdx.x + u * kThreads;
-        if (i < cnt) vals[shift + i] = v[u];
-      }
-      __syncthreads();
-      const AT* vv = vals + shift;
-      const int gs = d.gshift;  // 2^gs threads per vertex
-      const int nvt = (int)(d.v1 - d.v0);
-      const int64_t* so = sOff + d.oshift;
+      for (int u = 0; u < kPerThread; ++u) sm += v[u];
       if (gs <= 5) {
-        const int gl = lane_id() & ((1 << gs) - 1);
-        const int per_warp = 32 >> gs;
-        for (int jb = (threadIdx.x >> 5) * per_warp; jb < nvt; jb += (kThreads / 32) * per_warp) {
-          const int j = jb + (int)(lane_id() >> gs);
-          AT s = 0;
-          int es = 0, ee = 0;
-          if (j < nvt) {
-            es = (int)(so[j] - d.e0);
-            ee = (int)(so[j + 1] - d.e0);
-            for (int i = es + gl; i < ee; i += (1 << gs)) s += vv[i];
-          }
-          s = group_sum(s, gs);
-          if (j < nvt && gl == 0)
-            res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, s, ee - es,
-                                            (AT)sR[d.rshift + j]);
-        }
+        sm = group_sum(sm, gs);
+        if (j < nvt && gl == 0)
+          res += update_vertex<PR, MULTI>(S, A, M, d.part, iter, d.v0 + j, sm, ee - es,
+                                          (AT)sR[d.rshift + j]);
       } else {
         // Several warps per vertex (tiles of at most four vertices): warp sums meet in
         // shared memory and the group's first thread updates the vertex.
-        const int j = (int)(threadIdx.x >> gs);
-        const int gl = (int)(threadIdx.x & ((1u << gs) - 1));
-        AT s = 0;
-        int es = 0, ee = 0;
-        if (j < nvt) {
-          es = (int)(so[j] - d.e0);
-          ee = (int)(so[j + 1] - d.e0);
-          for (int i = es + gl; i < ee; i += (1 << gs)) s += vv[i];
-        }
-        s = warp_sum(s);
-        if (lane_id() == 0) red[threadIdx.x >> 5] = s;
+        sm = warp_sum(sm);
+        if (lane_id() == 0) red[threadIdx.x >> 5] = sm;
         __syncthreads();
         if (j < nvt && gl == 0) {
           AT t = 0;
@@ -660,7 +639,9 @@ PrPlan make_plan(graph* g) {
     add(P.nchunk, 0, P.nchunk, 1, kItemHub, p, 8);
     for (int c = kClassHub - 1; c >= 1; --c) {
       const uint32_t v0 = P.cls_end[c + 1], v1 = P.cls_end[c];
-      const uint32_t per = std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1));
+      // one round of the CTA's threads: at most kThreads >> gshift vertices
+      const uint32_t per = std::min<uint32_t>(std::max<uint32_t>(1u, (uint32_t)kLeafEdges >> (c - 1)),
+                                              (uint32_t)kPrTileV >> leaf_gshift(c));
       add((v1 - v0 + per - 1) / per, v0, v1, per, kItemLeaf, p, leaf_gshift(c));
     }
     const uint32_t z0 = P.cls_end[1], z1 = P.nv;
@@ -669,13 +650,21 @@ PrPlan make_plan(graph* g) {
   return pl;
 }
 
+// The kernel's 8 resident CTAs per SM need only part of the SM's 228 KB of shared
+// memory; the carveout hint leaves the rest to the L1 cache, which keeps the most-gathered
+// contributions (those of the highest-degree vertices) close to the SM.
 template <class PR, bool MULTI>
 graph_status prepare_kernel() {
   static bool done = false;
   if (!done) {
-    GG_CUDA(cudaFuncSetAttribute(k_pr_compute<PR, MULTI>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<PR>()));
+    auto fn = k_pr_compute<PR, MULTI>;
+    const int smem = (int)smem_bytes<PR>();
+    GG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+#ifndef PR_NO_CARVEOUT
+    const int pct = (int)((100.0 * 8 * (smem + 1024) + 228.0 * 1024 - 1) / (228.0 * 1024));
+    GG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 std::min(100, pct)));
+#endif
     done = true;
   }
   return GRAPH_OK;
