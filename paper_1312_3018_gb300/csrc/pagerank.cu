@@ -7,15 +7,15 @@
 //  - compute: every vertex sums the contributions of its neighbours (local ones from x,
 //    boundary ones from the ghost slots) and sets r' = (1-d)/n + d (sum + D/n), then its
 //    own contribution x' = r'/deg.
-//  - reduction: each block adds its partial sum of the L1 residual to one of kSlots FP64
+//  - reduction: each warp adds its partial sum of the L1 residual to one of kSlots FP64
 //    slots (a reduction nobody waits for, so a block frees its SM slot as soon as its
 //    vertices are written); a one-block kernel then sums the slots, forms the next
 //    iteration's constant term and clears them. The FP64 additions happen in arrival
 //    order, so the residual's last bits can differ between runs; the ranks cannot.
 //
 // Work items (one CTA each): hub chunks (kHubChunk edges of a vertex of degree >= 2048;
-// the chunk's partial sum goes to hubsum[item], and k_pr_hubs then adds each hub's chunk
-// sums in chunk order and updates the hub), class tiles (kLeafEdges >> (c-1) vertices of
+// each warp's partial sum of the chunk goes to hubsum[item][warp], and k_pr_hubs then adds
+// each hub's partials in chunk and warp order and updates the hub), class tiles (kLeafEdges >> (c-1) vertices of
 // degree class c, so at most kTileE edges; 2^(c-3) threads per vertex, one round) and
 // tiles of degree-zero vertices. Items are resolved once per workspace into a table of
 // 32-byte records (edge range, vertex range, kind), read with an L2 keep-resident hint, so
@@ -114,6 +114,7 @@ struct PrSide {
 // [1] D; [2] last residual; [3] rank of degree-zero vertices before this iteration;
 // [4] the constant term rounded to FP32 (stored as a float in the first half).
 constexpr uint32_t kSlots = 1024;  // FP64 residual slots (block b adds to slot b % kSlots)
+constexpr int kHubParts = kThreads / 32;  // partial sums per hub chunk (one per warp)
 
 struct PrItem;
 
@@ -417,12 +418,14 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
   __syncthreads();
   const bool ok = mbar_wait_bounded(&bar, 0, A.err);
   AT res = 0;
+  bool leaf = false;  // the CTA's item is a class tile (uniform over the CTA)
   if (__syncthreads_and(ok)) {
     const Desc d = dsh;
     const PrSide& S = A.side[d.part];
     if (d.kind == kItemHub) {
-      // One chunk (at most kHubChunk edges) of a hub's adjacency: its partial sum goes to
-      // hubsum[item]; k_pr_hubs adds a hub's chunks in order and updates the vertex.
+      // One chunk (at most kHubChunk edges) of a hub's adjacency: each warp's partial sum
+      // goes to hubsum[item][warp]; k_pr_hubs adds a hub's partials in order and updates
+      // the vertex.
       const int cnt = (int)(d.e1 - d.e0);
       const uint32_t* src = sE + d.eshift;
       uint32_t e[kPerThread];
@@ -438,9 +441,11 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
       AT sum = 0;
       #pragma unroll
       for (int u = 0; u < kPerThread; ++u) sum += v[u];
-      sum = block_sum<AT>(sum, red);
-      if (threadIdx.x == 0) ((AT*)A.hubsum)[blockIdx.x] = sum;
+      sum = warp_sum(sum);  // one partial per warp: no CTA-wide barrier
+      if (lane_id() == 0)
+        ((AT*)A.hubsum)[(size_t)blockIdx.x * kHubParts + (threadIdx.x >> 5)] = sum;
     } else if (d.kind == kItemLeaf) {
+      leaf = true;
       // Vertex j of the tile belongs to the 2^gs threads j << gs ...; they gather its edges
       // at stride 2^gs (at most kPerThread each, since a class-c degree is below 2^c and
       // 2^gs = 2^(c-3)) and add them in registers, so values never round-trip through
@@ -499,10 +504,12 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
       }
     }
   }
-  // Components keep no global scalars: their constants come from the host's table.
-  if (MULTI) return;
-  res = block_sum<AT>(res, red);
-  if (threadIdx.x == 0) atomicAdd(A.slots + (blockIdx.x % kSlots), (double)res);
+  // Components keep no global scalars: their constants come from the host's table. Only
+  // class tiles update vertices here (hub chunks and degree-zero tiles leave no residual).
+  if (MULTI || !leaf) return;
+  res = warp_sum(res);
+  if (lane_id() == 0 && res != (AT)0)
+    atomicAdd(A.slots + ((blockIdx.x * kHubParts + (threadIdx.x >> 5)) % kSlots), (double)res);
 }
 
 // Hub vertices (degree >= kHubChunk), one warp each: the sum of the vertex's chunk partial
@@ -523,9 +530,10 @@ k_pr_hubs(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs A,
     const PrSide& S = A.side[p];
     const int64_t deg = S.P.off[v + 1] - S.P.off[v];
     const uint32_t nch = (uint32_t)((deg + kHubChunk - 1) / kHubChunk);
-    const AT* hs = (const AT*)A.hubsum + plan.hub_item0[p] + S.P.hub_chunk0[v];
+    const AT* hs = (const AT*)A.hubsum +
+                   (size_t)(plan.hub_item0[p] + S.P.hub_chunk0[v]) * kHubParts;
     AT sum = 0;
-    for (uint32_t c = lane_id(); c < nch; c += 32) sum += hs[c];
+    for (uint32_t c = lane_id(); c < nch * kHubParts; c += 32) sum += hs[c];
     sum = warp_sum(sum);
     if (lane_id() == 0)
       res = update_vertex<PR, MULTI>(S, A, M, p, iter, v, sum, (int)deg,
@@ -712,7 +720,7 @@ graph_status prepare_items(graph* g, PrWs* w, const PrPlan& pl) {
   dfree(g, w->hubsum);
   w->items_n = 0;
   GG_TRY(dalloc(g, w->items, sizeof(PrItem) * (size_t)pl.nitems));
-  GG_TRY(dalloc(g, w->hubsum, sizeof(typename PR::AT) * (size_t)pl.nitems));
+  GG_TRY(dalloc(g, w->hubsum, sizeof(typename PR::AT) * kHubParts * (size_t)pl.nitems));
   k_pr_items<<<grid_for(pl.nitems, 256), 256, 0, g->stream>>>(pl, make_args(g, 0, 0.85),
                                                               (PrItem*)w->items.p);
   GG_CUDA(cudaGetLastError());
