@@ -236,6 +236,29 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
                   graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * sssp_batch -- k <= GRAPH_SSSP_BATCH_MAX shortest-path searches in one sequence of
+ * Bellman-Ford supersteps (Section 7.3, Figure 20, in plain rounds). The paper runs one
+ * search per call; here every vertex carries a row of 8 distances (one 32-byte sector,
+ * lane s belonging to search s), a vertex is queued for the searches whose distance
+ * improved, and one relaxation pass reads each of its edge ids and weights once for all of
+ * them; boundary targets reduce into an outbox row, which the exchange applies to the
+ * owner's row.
+ *   sources  k uint32 source ids in host memory (duplicates allowed), each < n
+ *   k        1 <= k <= GRAPH_SSSP_BATCH_MAX (other values: EINVAL)
+ *   dist     k * n uint32, row s (dist + s * n) = the distances sssp returns for
+ *            sources[s], global order, INF unreachable. Host or device per attr->out_mem.
+ * attr: out_mem, max_supersteps and timing as for sssp; delta must be 0.
+ * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator;
+ * edges_inspected counts edge entries read (once per pass, whatever the number of lanes).
+ * Device workspace: 76 bytes per vertex and 36 per outbox slot, kept with the graph until
+ * it is re-partitioned or freed. Errors: EINVAL, ESTATE, ETIMEOUT, ERANGE, ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_SSSP_BATCH_MAX 8u
+
+graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t k, uint32_t* dist,
+                        const sssp_attr* attr, graph_stats* stats);
+
+/* ---------------------------------------------------------------------------------------
  * betweenness -- betweenness centrality summed over a list of sources (Section 7.2,
  * Figure 18; Brandes' algorithm). Per source, a forward BSP cycle finds BFS levels and the
  * number of shortest paths sigma (each new vertex sums sigma over its neighbours one level

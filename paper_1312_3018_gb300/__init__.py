@@ -19,7 +19,7 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "bfs_batch", "sssp", "betweenness", "connected_components", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "sssp_batch", "betweenness", "connected_components", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
            "graph_free", "Graph",
            "GraphError", "INF", "library_path"]
 
@@ -237,6 +237,28 @@ def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_superstep
     stats = _lib.graph_stats()
     st = _lib.load().sssp(g.handle, int(source), pd, C.byref(attr), C.byref(stats))
     _lib.check(st, "sssp")
+    return dist, stats.as_dict()
+
+
+def sssp_batch(g: Graph, sources, dist=None, *, out: str = "device", max_supersteps: int = 0,
+               timing: bool = False):
+    """k = len(sources) <= SSSP_BATCH_MAX shortest-path searches in one pass of Bellman-Ford
+    supersteps; distances [k, n] uint32 (row s for sources[s], INF unreachable) and stats."""
+    torch = _torch()
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64))
+    if src.ndim != 1 or np.any(src < 0) or np.any(src >= 2**32):
+        raise ValueError("sources must be a 1-D list of vertex ids")
+    src = src.astype(np.uint32)
+    k = len(src)
+    if dist is None:
+        dist = (torch.empty((k, g.n), dtype=torch.int32, device="cuda") if out == "device"
+                else np.empty((k, g.n), dtype=np.uint32))
+    pd, mem = _ptr(dist)
+    attr = _lib.sssp_attr(mem, max_supersteps, int(timing), 0)
+    stats = _lib.graph_stats()
+    st = _lib.load().sssp_batch(g.handle, src.ctypes.data, k, pd, C.byref(attr),
+                                C.byref(stats))
+    _lib.check(st, "sssp_batch")
     return dist, stats.as_dict()
 
 

@@ -31,6 +31,7 @@ GRAPH_PR_FP64 = 1
 GRAPH_PR_FP16 = 2
 GRAPH_NOALLOC_MAX_VERTICES = 1 << 21
 GRAPH_BATCH_MAX = 64
+GRAPH_SSSP_BATCH_MAX = 8
 GRAPH_QUERY_BFS = 0
 GRAPH_QUERY_SSSP = 1
 
@@ -124,6 +125,7 @@ SIGNATURES = {
     "bfs": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "bfs_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
+    "sssp_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),
     "betweenness": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bc_attr), C.POINTER(graph_stats)]),
     "connected_components": (_int, [_vp, _vp, C.POINTER(cc_attr), C.POINTER(graph_stats)]),
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),

@@ -298,6 +298,7 @@ struct SsspWs;
 struct PrWs;
 struct MsWs;
 struct BcWs;
+struct SbWs;
 
 }  // namespace gg
 
@@ -323,6 +324,7 @@ struct graph {
   gg::PrWs* pr = nullptr;
   gg::MsWs* ms = nullptr;     // batched BFS workspace
   gg::BcWs* bc = nullptr;     // betweenness workspace
+  gg::SbWs* sb = nullptr;     // batched SSSP workspace
 };
 
 namespace gg {
@@ -365,6 +367,7 @@ void free_sssp(graph* g);
 void free_pr(graph* g);
 void free_msbfs(graph* g);
 void free_bc(graph* g);
+void free_ssspb(graph* g);
 
 inline unsigned grid_for(uint64_t work, unsigned per_block) {
   uint64_t b = (work + per_block - 1) / per_block;

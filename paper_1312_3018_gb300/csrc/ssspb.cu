@@ -1,0 +1,563 @@
+// Batched SSSP: up to kSbLanes single-source shortest-path searches share one sequence of
+// Bellman-Ford supersteps (Section 7.3, Figure 20, run for k sources at once). Every vertex
+// carries a row of kSbLanes distances (one 32-byte sector, vertex-major), so a relaxation
+// pass reads an edge id and its weight once for every search in which the source vertex is
+// active, and the target's row costs the same sector a single distance would.
+//   dist[v][l]   distance of v in search l
+//   snap[v][l]   distance v was last queued (and relaxed) with in search l (INF: never)
+//   tmask[v]     searches in which v was lowered this round; tbits: the same as a bitmap
+//   amask[v]     searches v was queued for in the current round
+// One superstep:
+//  - compute: every queued vertex relaxes its edges lane by lane (hub chunks with the
+//    distances the hub was queued with, other vertices with their newest distances):
+//    a lower candidate is written with an atomic minimum (a reduction no thread waits for)
+//    and marks the target's lane; a boundary target reduces into its outbox row.
+//  - communication: dirty outbox rows are applied to their owners the same way.
+//  - filter and termination: a touched vertex is queued for the lanes whose distance fell
+//    below their queued value; the searches end when no vertex is queued.
+// Results equal those of k separate sssp() calls (plain rounds): shortest distances are
+// unique.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace gg {
+
+constexpr int kSbLanes = 8;  // distances per vertex row (one 32-byte sector)
+
+struct SbCounters {
+  uint32_t tail[2][kNBucket];  // next-round work: [0] hub chunks, [1..3] vertices
+  uint32_t overflow;
+  uint32_t pad;
+  unsigned long long inspected;
+  unsigned long long messages;
+  unsigned long long reached_degree[kSbLanes];  // filled by the collect
+  uint32_t clamped;
+};
+
+struct SbWs {
+  DevBuf dist[2], snap[2], tmask[2], tbits[2], amask[2], queue[2][2], hubq[2][2], omsg[2],
+      odirty[2];
+  size_t words[2] = {0, 0}, owords[2] = {0, 0};
+};
+
+void free_ssspb(graph* g) {
+  if (!g->sb) return;
+  SbWs* w = g->sb;
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->tmask[p],    &w->tbits[p],
+                     &w->amask[p],    &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],
+                     &w->hubq[p][1],  &w->omsg[p],     &w->odirty[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  delete w;
+  g->sb = nullptr;
+}
+
+namespace {
+
+struct SbSide {
+  PartView P;
+  uint32_t* dist;    // [nv][kSbLanes]
+  uint32_t* snap;    // [nv][kSbLanes]
+  uint32_t* tmask;   // [nv]
+  uint32_t* tbits;   // [words]
+  uint32_t* amask;   // [nv]
+  uint32_t* nqueue;  // next active queue (bucketed)
+  uint32_t* nhubq;   // next hub chunk list
+  uint32_t* omsg;    // [nout][kSbLanes] outbox minima
+  uint32_t* odirty;  // [owords] outbox rows lowered this round
+};
+
+struct SbArgs {
+  SbSide side[2];
+  SbCounters* ctr;
+};
+
+__device__ __forceinline__ uint32_t sb_sat_add(uint32_t a, uint32_t b, bool& ovf) {
+  const uint64_t s = (uint64_t)a + (uint64_t)b;
+  if (s >= (uint64_t)kInf) {
+    ovf = true;
+    return kInf - 1;
+  }
+  return (uint32_t)s;
+}
+__device__ __forceinline__ void sb_red_min(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+__device__ __forceinline__ void sb_red_or(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
+// A 32-byte distance row (two 16-byte loads; rows are 32-byte aligned).
+struct Row {
+  uint32_t d[kSbLanes];
+};
+__device__ __forceinline__ Row load_row(const uint32_t* p) {
+  const uint4 a = __ldcg(reinterpret_cast<const uint4*>(p));
+  const uint4 b = __ldcg(reinterpret_cast<const uint4*>(p) + 1);
+  Row r;
+  r.d[0] = a.x; r.d[1] = a.y; r.d[2] = a.z; r.d[3] = a.w;
+  r.d[4] = b.x; r.d[5] = b.y; r.d[6] = b.z; r.d[7] = b.w;
+  return r;
+}
+
+__device__ void sb_flush(unsigned long long insp, unsigned long long msg, bool ovf,
+                         SbCounters* ctr) {
+  insp = warp_sum(insp);
+  msg = warp_sum(msg);
+  const bool any_ovf = __any_sync(kFull, ovf);
+  if (lane_id() == 0) {
+    if (insp) atomicAdd(&ctr->inspected, insp);
+    if (msg) atomicAdd(&ctr->messages, msg);
+    if (any_ovf) atomicOr(&ctr->overflow, 1u);
+  }
+}
+
+// Lowers the target row `row` with candidates dv[l] + w for the lanes in m; returns the
+// lanes lowered.
+__device__ __forceinline__ uint32_t relax_row(uint32_t* row, const uint32_t* dv, uint32_t m,
+                                              uint32_t w, bool& ovf) {
+  const Row t = load_row(row);
+  uint32_t low = 0;
+  #pragma unroll
+  for (int l = 0; l < kSbLanes; ++l) {
+    if (!((m >> l) & 1u)) continue;
+    bool o = false;
+    const uint32_t nd = sb_sat_add(dv[l], w, o);
+    if (nd < t.d[l]) {
+      ovf |= o;
+      sb_red_min(row + l, nd);
+      low |= 1u << l;
+    }
+  }
+  return low;
+}
+
+__device__ __forceinline__ void relax_edges_b(const SbSide& S, const uint32_t* dv, uint32_t m,
+                                              const uint32_t* Ep, const uint32_t* Wp, int first,
+                                              int deg, int stride, unsigned long long& insp,
+                                              bool& ovf) {
+  const uint64_t pol = l2_evict_first_policy();
+  for (int i = first; i < deg; i += 2 * stride) {
+    const bool two = i + stride < deg;
+    insp += two ? 2 : 1;
+    const uint32_t xa = ld_stream(Ep + i, pol), wa = ld_stream(Wp + i, pol);
+    const uint32_t xb = two ? ld_stream(Ep + i + stride, pol) : 0u;
+    const uint32_t wb = two ? ld_stream(Wp + i + stride, pol) : 0u;
+    uint32_t* ra = (xa & kRemote) ? S.omsg + (size_t)(xa & kIdMask) * kSbLanes
+                                  : S.dist + (size_t)xa * kSbLanes;
+    uint32_t* rb = (xb & kRemote) ? S.omsg + (size_t)(xb & kIdMask) * kSbLanes
+                                  : S.dist + (size_t)xb * kSbLanes;
+    const Row ta = load_row(ra);
+    const Row tb = two ? load_row(rb) : ta;
+    uint32_t la = 0, lb = 0;
+    #pragma unroll
+    for (int l = 0; l < kSbLanes; ++l) {
+      if (!((m >> l) & 1u)) continue;
+      bool o = false;
+      const uint32_t na = sb_sat_add(dv[l], wa, o);
+      if (na < ta.d[l]) { ovf |= o; sb_red_min(ra + l, na); la |= 1u << l; }
+      if (two) {
+        bool o2 = false;
+        const uint32_t nb = sb_sat_add(dv[l], wb, o2);
+        if (nb < tb.d[l]) { ovf |= o2; sb_red_min(rb + l, nb); lb |= 1u << l; }
+      }
+    }
+    if (la) {
+      if (!(xa & kRemote)) { sb_red_or(&S.tmask[xa], la); sb_red_or(&S.tbits[xa >> 5], 1u << (xa & 31u)); }
+      else sb_red_or(&S.odirty[(xa & kIdMask) >> 5], 1u << ((xa & kIdMask) & 31u));
+    }
+    if (lb) {
+      if (!(xb & kRemote)) { sb_red_or(&S.tmask[xb], lb); sb_red_or(&S.tbits[xb >> 5], 1u << (xb & 31u)); }
+      else sb_red_or(&S.odirty[(xb & kIdMask) >> 5], 1u << ((xb & kIdMask) & 31u));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sb_relax(const __grid_constant__ Plan plan, const __grid_constant__ SbArgs A) {
+  unsigned long long insp = 0;
+  bool ovf = false;
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const SbSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    uint32_t v, m;
+    int64_t e0, e1;
+    int first, stride;
+    bool have = false, hub = false;
+    if (G.gshift >= 8) {  // one hub chunk per plan block
+      const uint32_t ch = G.items[rel];
+      v = S.P.chunk_vertex[ch];
+      e0 = S.P.chunk_first[ch];
+      e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      first = threadIdx.x;
+      stride = kThreads;
+      have = true;
+      hub = true;
+    } else {
+      const int gs = G.gshift;
+      const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+      first = threadIdx.x & ((1 << gs) - 1);
+      stride = 1 << gs;
+      if (gi < G.count) {
+        v = G.items[gi];
+        e0 = S.P.off[v];
+        e1 = S.P.off[v + 1];
+        have = true;
+      }
+    }
+    if (have) {
+      m = __ldcg(&S.amask[v]);
+      // A hub's chunks all relax with the distances it was queued with; a vertex handled by
+      // one lane group relaxes with its newest distances (lowered since it was queued, they
+      // are better candidates) and records them as its queued values, so the filter does
+      // not queue it again for the same values (the paper's same-round activation).
+      uint32_t* sp = S.snap + (size_t)v * kSbLanes;
+      Row q = load_row(hub ? sp : S.dist + (size_t)v * kSbLanes);
+      if (!hub && first == 0) {
+        #pragma unroll
+        for (int l = 0; l < kSbLanes; ++l)
+          if ((m >> l) & 1u) sp[l] = q.d[l];
+      }
+      relax_edges_b(S, q.d, m, S.P.E + e0, S.P.W + e0, first, (int)(e1 - e0), stride, insp,
+                    ovf);
+    }
+  }
+  sb_flush(insp, 0, ovf, A.ctr);
+}
+
+// Communication phase: apply the dirty outbox rows of p to their owners in q.
+__global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant__ SbArgs A,
+                                                          uint32_t words0) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i < words0 ? 0 : 1;
+  const uint32_t word = p == 0 ? i : i - words0;
+  const SbSide& S = A.side[p];
+  const SbSide& Q = A.side[1 - p];
+  unsigned long long msgs = 0;
+  bool ovf = false;
+  if (word * 32 < S.P.nout) {
+    uint32_t bits = S.odirty[word];
+    if (bits) {
+      S.odirty[word] = 0;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t idx = word * 32 + b;
+        const uint32_t u = S.P.outbox[idx];
+        const Row mv = load_row(S.omsg + (size_t)idx * kSbLanes);
+        msgs++;
+        uint32_t fin = 0;  // lanes that carry a message
+        #pragma unroll
+        for (int l = 0; l < kSbLanes; ++l) fin |= (mv.d[l] != kInf ? 1u : 0u) << l;
+        const uint32_t low = relax_row(Q.dist + (size_t)u * kSbLanes, mv.d, fin, 0u, ovf);
+        if (low) {
+          sb_red_or(&Q.tmask[u], low);
+          sb_red_or(&Q.tbits[u >> 5], 1u << (u & 31u));
+        }
+      }
+    }
+  }
+  sb_flush(0, msgs, ovf, A.ctr);
+}
+
+// Filter: a touched vertex is queued for the lanes whose distance fell below their queued
+// value (which then becomes that distance). One lane per bitmap word; lanes walk their set
+// bits in step so that appends stay warp-aggregated.
+__global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ SbArgs A,
+                                                        uint32_t words0, uint32_t words) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
+  const uint32_t word = p == 0 ? i : i - words0;
+  const SbSide& S = A.side[p];
+  uint32_t bits = 0;
+  if (i < words) {
+    bits = S.tbits[word];
+    if (bits) S.tbits[word] = 0;
+  }
+  while (__any_sync(kFull, bits != 0)) {
+    bool act = false;
+    uint32_t x = 0;
+    if (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      x = word * 32 + b;
+      const uint32_t tm = S.tmask[x];
+      S.tmask[x] = 0;
+      const Row d = load_row(S.dist + (size_t)x * kSbLanes);
+      uint32_t* sp = S.snap + (size_t)x * kSbLanes;
+      const Row q = load_row(sp);
+      uint32_t am = 0;
+      #pragma unroll
+      for (int l = 0; l < kSbLanes; ++l) {
+        if (((tm >> l) & 1u) && d.d[l] < q.d[l]) {
+          sp[l] = d.d[l];
+          am |= 1u << l;
+        }
+      }
+      if (am) {
+        S.amask[x] = am;
+        act = true;
+      }
+    }
+    warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                         S.nhubq);
+  }
+}
+
+// Sources: distance 0 in their lane, touched for the first filter.
+struct SbSources {
+  uint32_t id[kSbLanes];
+};
+__global__ void k_sb_init(const __grid_constant__ SbArgs A, const uint32_t* g2l,
+                          const __grid_constant__ SbSources src, uint32_t k) {
+  const uint32_t l = threadIdx.x;
+  if (l >= k) return;
+  const uint32_t gl = g2l[src.id[l]];
+  const int p = gl >> 31;
+  const uint32_t v = gl & kIdMask;
+  const SbSide& S = A.side[p];
+  S.dist[(size_t)v * kSbLanes + l] = 0;
+  atomicOr(&S.tmask[v], 1u << l);
+  atomicOr(&S.tbits[v >> 5], 1u << (v & 31u));
+}
+
+// Lane l's distances into out + l * n (global order), and each lane's reached degree sum.
+__global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uint32_t n,
+                             uint32_t k, uint32_t* out, SbCounters* ctr) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long d[kSbLanes] = {0};
+  if (i < n) {
+    const int p = i < nv0 ? 0 : 1;
+    const uint32_t v = p == 0 ? i : i - nv0;
+    const SbSide& S = A.side[p];
+    const Row r = load_row(S.dist + (size_t)v * kSbLanes);
+    const uint32_t gid = S.P.l2g[v];
+    const unsigned long long deg = (unsigned long long)(S.P.off[v + 1] - S.P.off[v]);
+    for (uint32_t l = 0; l < k; ++l) {
+      out[(size_t)l * n + gid] = r.d[l];
+      if (r.d[l] != kInf) d[l] = deg;
+      if (r.d[l] == kInf - 1) atomicOr(&ctr->clamped, 1u);
+    }
+  }
+  for (uint32_t l = 0; l < k; ++l) {
+    const unsigned long long s = warp_sum(d[l]);
+    if (lane_id() == 0 && s) atomicAdd(&ctr->reached_degree[l], s);
+  }
+}
+
+graph_status alloc_ws(graph* g) {
+  if (g->sb) return GRAPH_OK;
+  SbWs* w = new SbWs();
+  g->sb = w;
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    // bitmap words rounded to whole warps (the filter assigns one lane per word)
+    w->words[p] = ((P.nv + 31) / 32 + 31) & ~(size_t)31;
+    w->owords[p] = ((P.nout + 31) / 32 + 31) & ~(size_t)31;
+    GG_TRY(dalloc(g, w->dist[p], 4ull * kSbLanes * P.nv));
+    GG_TRY(dalloc(g, w->snap[p], 4ull * kSbLanes * P.nv));
+    GG_TRY(dalloc(g, w->tmask[p], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->tbits[p], 4 * w->words[p]));
+    GG_TRY(dalloc(g, w->amask[p], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->queue[p][0], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->queue[p][1], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->hubq[p][0], 4ull * P.nchunk));
+    GG_TRY(dalloc(g, w->hubq[p][1], 4ull * P.nchunk));
+    GG_TRY(dalloc(g, w->omsg[p], 4ull * kSbLanes * P.nout));
+    GG_TRY(dalloc(g, w->odirty[p], 4 * w->owords[p]));
+  }
+  if (g->counters.bytes < sizeof(SbCounters) || !g->counters.p) {
+    dfree(g, g->counters);
+    GG_TRY(dalloc(g, g->counters, 1024));
+  }
+  return ensure_host_counters(g, 1024);
+}
+
+// A failed allocation leaves no half-built workspace behind for the next call.
+graph_status ensure_ws(graph* g) {
+  const graph_status s = alloc_ws(g);
+  if (s != GRAPH_OK) free_ssspb(g);
+  return s;
+}
+
+SbArgs make_args(graph* g, SbWs* w, SbCounters* ctr, int cur) {
+  SbArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int p = 0; p < 2; ++p) {
+    SbSide& S = A.side[p];
+    S.P = g->part[p].view();
+    S.dist = (uint32_t*)w->dist[p].p;
+    S.snap = (uint32_t*)w->snap[p].p;
+    S.tmask = (uint32_t*)w->tmask[p].p;
+    S.tbits = (uint32_t*)w->tbits[p].p;
+    S.amask = (uint32_t*)w->amask[p].p;
+    S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
+    S.nhubq = (uint32_t*)w->hubq[p][1 - cur].p;
+    S.omsg = (uint32_t*)w->omsg[p].p;
+    S.odirty = (uint32_t*)w->odirty[p].p;
+  }
+  A.ctr = ctr;
+  return A;
+}
+
+uint64_t active_count(const SbCounters& c) {
+  uint64_t a = 0;
+  for (int p = 0; p < 2; ++p)
+    for (int b = 0; b < kNBucket; ++b) a += c.tail[p][b];
+  return a;
+}
+
+}  // namespace
+}  // namespace gg
+
+using namespace gg;
+
+extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t k,
+                                   uint32_t* dist, const sssp_attr* attr, graph_stats* stats) {
+  if (!g || !sources || !dist) {
+    set_error("graph, sources or dist is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (k < 1 || k > (uint32_t)kSbLanes) {
+    set_error("k = %u searches; 1 <= k <= %d", k, kSbLanes);
+    return GRAPH_EINVAL;
+  }
+  for (uint32_t l = 0; l < k; ++l)
+    if (sources[l] >= g->n) {
+      set_error("source %u >= n %u", sources[l], g->n);
+      return GRAPH_EINVAL;
+    }
+  if (!g->weighted) {
+    set_error("sssp_batch needs edge weights (load the graph with weights)");
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before sssp_batch");
+    return GRAPH_ESTATE;
+  }
+  sssp_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) {
+    set_error("bad out_mem");
+    return GRAPH_EINVAL;
+  }
+  if (at.delta != 0) {
+    set_error("sssp_batch runs plain rounds: delta must be 0");
+    return GRAPH_EINVAL;
+  }
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  GG_TRY(ensure_ws(g));
+  SbWs* w = g->sb;
+  cudaStream_t st = g->stream;
+  SbCounters* dc = (SbCounters*)g->counters.p;
+  SbCounters* hc = (SbCounters*)g->host_counters;
+  PhaseTimer timer;
+  timer.start(at.timing != 0 && stats != nullptr, st);
+  timer.mark(2);
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->tmask[p].p, 0, 4ull * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->tbits[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * kSbLanes * P.nout, st));
+    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
+  }
+  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
+  SbSources src;
+  memset(&src, 0, sizeof(src));
+  for (uint32_t l = 0; l < k; ++l) src.id[l] = sources[l];
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
+  int cur = 0;
+  {
+    // round 0's active set: the sources, queued by the filter into queues `cur`
+    const SbArgs A = make_args(g, w, dc, 1);
+    k_sb_init<<<1, 32, 0, st>>>(A, (const uint32_t*)g->g2l.p, src, k);
+    GG_CUDA(cudaGetLastError());
+    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+    GG_CUDA(cudaGetLastError());
+  }
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
+  int64_t inspected = 0, messages = 0, launches = 2, rounds = 0;
+  bool overflow = false;
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (;; ++rounds) {
+    const SbCounters c = *hc;
+    if (active_count(c) == 0) break;
+    if (rounds >= cap) {
+      set_error("sssp_batch reached the superstep cap (%lld)", (long long)cap);
+      timer.finish(nullptr);
+      return GRAPH_ETIMEOUT;
+    }
+    GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
+    const SbArgs A = make_args(g, w, dc, cur);
+    Plan pl;
+    memset(&pl, 0, sizeof(pl));
+    for (int p = 0; p < 2; ++p) {
+      const PartView V = g->part[p].view();
+      plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);
+      for (int b = 1; b < kNBucket; ++b)
+        plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
+                 gsh[b], b);
+    }
+    timer.mark(2);
+    if (pl.nblocks) k_sb_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+    GG_CUDA(cudaGetLastError());
+    timer.mark(0);
+    if (owords) k_sb_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
+    GG_CUDA(cudaGetLastError());
+    timer.mark(1);
+    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+    GG_CUDA(cudaGetLastError());
+    timer.mark(0);
+    launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
+    messages += (int64_t)hc->messages;
+    overflow |= hc->overflow != 0;
+    cur = 1 - cur;
+  }
+  uint32_t* dd = dist;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 4ull * k * g->n + 64));
+    dd = (uint32_t*)g->stage.p;
+  }
+  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
+  {
+    const SbArgs A = make_args(g, w, dc, cur);
+    k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, dd, dc);
+    GG_CUDA(cudaGetLastError());
+    launches++;
+  }
+  if (at.out_mem == GRAPH_MEM_HOST)
+    GG_TRY(deliver(g, dist, dd, 4ull * k * g->n, GRAPH_MEM_HOST));
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
+  timer.mark(2);
+  GG_CUDA(cudaStreamSynchronize(st));
+  graph_status s = check_device_error(g);
+  if (!hc->clamped) overflow = false;  // a clamped relaxation was later improved upon
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)rounds;
+    int64_t trav = 0;
+    for (uint32_t l = 0; l < k; ++l) trav += (int64_t)hc->reached_degree[l];
+    stats->edges_traversed = trav;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+  }
+  timer.finish(stats);
+  if (s == GRAPH_OK && overflow) {
+    set_error("a shortest distance reached 2^32 - 1");
+    return GRAPH_ERANGE;
+  }
+  return s;
+}

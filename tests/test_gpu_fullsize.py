@@ -79,6 +79,21 @@ def test_rmat22_sssp(gpu, rmat22, loaded22):
             assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
 
 
+def test_rmat22_sssp_batch_eight_sources(gpu, rmat22, loaded22):
+    """Eight searches in one batch at full size: two rows against the oracle element by
+    element, every row through the optimality certificate."""
+    g = rmat22
+    srcs = [int(s) for s in synth.sources(g, 8, seed=4)]
+    d, st = gpu.sssp_batch(loaded22, srcs, out="host")
+    total = 0
+    for row, s in enumerate(srcs):
+        if row < 2:
+            assert np.array_equal(d[row], oracle.sssp(g.n, g.offsets, g.cols, g.weights, s))
+        assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d[row]) == 0
+        total += oracle.traversed(g.n, g.offsets, d[row])
+    assert st["edges_traversed"] == total
+
+
 def test_rmat22_pagerank_to_residual_1e9(gpu, rmat22, loaded22):
     g = rmat22
     ref, res, kstar = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=1000, tol=1e-9)
