@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched BFS and many-graph PageRank measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    ap.add_argument("--no-sssp-batch", action="store_true",
+                    help="serving: SSSP queries on single-query jobs only")
     ap.add_argument("--sssp-delta", type=int, default=64,
                     help="near-far bucket width of the step's SSSP (0: plain active-set rounds)")
     return ap.parse_args()
@@ -164,7 +166,7 @@ def serving_bench(G, a, torch):
     nbuf = 400
     bufs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)]
     points = []
-    with G.Server(H, out="device", sssp_delta=delta) as srv:
+    with G.Server(H, out="device", sssp_delta=delta, sssp_batch=not a.no_sssp_batch) as srv:
         info0 = srv.info()
         for i in range(64):  # warm-up
             srv.submit("bfs" if i % 3 else "sssp", int(srcs[i]), bufs[i])
@@ -217,8 +219,12 @@ def serving_bench(G, a, torch):
             "max_slots_busy": info["max_slots_busy"],
             "bytes_lanes": info0["bytes_lanes"], "bytes_per_sssp": info0["bytes_per_sssp"],
             "generate_s": round(gen_s, 2), "sssp_delta": delta,
+            "sssp_batch_slots": info["sssp_batch_slots"],
+            "sssp_batched_queries": info["sssp_batched"],
+            "max_batch_busy": info["max_batch_busy"],
             "note": "graph_server (continuous batching: BFS lanes join and leave between "
-                    "supersteps; SSSP jobs on their own streams); device outputs"}
+                    "supersteps; SSSP jobs on their own streams, waiting SSSP queries "
+                    "grouped into batched 8-lane jobs when enabled); device outputs"}
 
 
 def workload_name(a):

@@ -371,7 +371,9 @@ graph_status pagerank_multi(graph_t* g, uint32_t ngraphs, const uint32_t* vbase,
  *    query joins at the next superstep boundary on a free lane and leaves when a superstep
  *    adds no vertex to its search, so queries enter and leave while others run.
  *  - SSSP queries each run on an SSSP job with its own workspace and stream; up to
- *    sssp_slots jobs run at once, their supersteps overlapping on the device.
+ *    sssp_slots jobs run at once, their supersteps overlapping on the device. With
+ *    attr.sssp_batch, batched jobs are added: queries that wait together are started as
+ *    one sssp_batch search of up to GRAPH_SSSP_BATCH_MAX lanes (shared edge reads).
  *  - Admission is by device memory: at creation the server sizes the lanes and the job
  *    slots to mem_budget (per-query state: bfs_lanes_bytes once, sssp_job_bytes per
  *    slot) and allocates them; a query waits in FIFO order until a lane or a slot is free.
@@ -388,9 +390,14 @@ typedef struct graph_server graph_server_t;
 typedef struct {
   uint64_t mem_budget; /* bytes for per-query state; 0: half of the free device memory */
   uint32_t bfs_lanes;  /* BFS lanes, 1..64 (0: 64) */
-  uint32_t max_sssp;   /* upper bound on SSSP slots (0: 64); the budget may allow fewer */
+  uint32_t max_sssp;   /* upper bound on single-query SSSP slots (0: 64, or 4 next to
+                          batched jobs); the budget may allow fewer */
   int out_mem;         /* GRAPH_MEM_HOST (pinned recommended) or _DEVICE for outputs */
   uint32_t sssp_delta; /* SSSP queries: near-far bucket width (0: plain rounds), as sssp() */
+  uint32_t sssp_batch; /* 0: SSSP queries run one per job; 1: also on batched jobs, where up
+                          to GRAPH_SSSP_BATCH_MAX queries waiting together share one
+                          sssp_batch search (plain rounds), taken when no single-query slot
+                          is free or at least half a batch waits */
 } graph_server_attr;
 
 typedef struct {
@@ -410,6 +417,10 @@ typedef struct {
   uint64_t submitted, completed, pending;
   uint32_t max_lanes_busy, max_slots_busy; /* peak concurrency seen */
   uint64_t bfs_supersteps;                  /* supersteps of the lane search */
+  uint32_t sssp_batch_slots;                /* batched SSSP jobs */
+  uint32_t max_batch_busy;                  /* peak batched jobs running at once */
+  uint64_t bytes_per_sssp_batch;            /* device bytes per batched job */
+  uint64_t sssp_batched;                    /* SSSP queries answered by batched jobs */
 } graph_server_info;
 
 /* Creates a server on g (loaded, partitioned; SSSP slots need weights, else 0 slots).

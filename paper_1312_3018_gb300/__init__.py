@@ -346,13 +346,13 @@ class Server:
     KINDS = {"bfs": _lib.GRAPH_QUERY_BFS, "sssp": _lib.GRAPH_QUERY_SSSP}
 
     def __init__(self, g: Graph, *, mem_budget: int = 0, bfs_lanes: int = 0, max_sssp: int = 0,
-                 out: str = "device", sssp_delta: int = 0):
+                 out: str = "device", sssp_delta: int = 0, sssp_batch: bool = False):
         _torch()
         self.g = g
         self.out = out
         mem = GRAPH_MEM_DEVICE if out == "device" else GRAPH_MEM_HOST
         attr = _lib.graph_server_attr(int(mem_budget), int(bfs_lanes), int(max_sssp), mem,
-                                      int(sssp_delta))
+                                      int(sssp_delta), int(bool(sssp_batch)))
         h = C.c_void_p(0)
         _lib.check(_lib.load().graph_server_create(g.handle, C.byref(attr), C.byref(h)),
                    "graph_server_create")

@@ -65,7 +65,7 @@ class cc_attr(C.Structure):
 
 class graph_server_attr(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("bfs_lanes", C.c_uint32), ("max_sssp", C.c_uint32),
-                ("out_mem", C.c_int), ("sssp_delta", C.c_uint32)]
+                ("out_mem", C.c_int), ("sssp_delta", C.c_uint32), ("sssp_batch", C.c_uint32)]
 
 
 class graph_completion(C.Structure):
@@ -80,7 +80,9 @@ class graph_server_info(C.Structure):
                 ("mem_budget", C.c_uint64), ("submitted", C.c_uint64),
                 ("completed", C.c_uint64), ("pending", C.c_uint64),
                 ("max_lanes_busy", C.c_uint32), ("max_slots_busy", C.c_uint32),
-                ("bfs_supersteps", C.c_uint64)]
+                ("bfs_supersteps", C.c_uint64), ("sssp_batch_slots", C.c_uint32),
+                ("max_batch_busy", C.c_uint32), ("bytes_per_sssp_batch", C.c_uint64),
+                ("sssp_batched", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

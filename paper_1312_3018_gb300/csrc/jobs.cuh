@@ -23,6 +23,18 @@ graph_status sssp_job_start(graph* g, SsspJob* j, uint32_t source, uint32_t* dst
 // (the job is then idle). *rounds receives the supersteps run so far.
 int sssp_job_poll(graph* g, SsspJob* j, int* rounds);
 
+// ---- SSSP: up to sb_job_lanes() queries sharing one batched search (ssspb.cu) ---------
+struct SbJob;
+uint32_t sb_job_lanes();
+size_t sb_job_bytes(const graph* g);  // device bytes one batched job holds
+graph_status sb_job_create(graph* g, SbJob** out);
+void sb_job_destroy(graph* g, SbJob* j);
+// Starts k searches (plain rounds); search l's distances go to dst[l] when the job ends.
+graph_status sb_job_start(graph* g, SbJob* j, const uint32_t* sources, uint32_t k,
+                          uint32_t* const* dst, int dst_mem);
+// As sssp_job_poll, for all k searches at once.
+int sb_job_poll(graph* g, SbJob* j, int* rounds);
+
 // ---- BFS: up to 64 queries as bit lanes of one multi-source search (msbfs.cu) ----------
 struct BfsLanes;
 size_t bfs_lanes_bytes(const graph* g, uint32_t nlanes);

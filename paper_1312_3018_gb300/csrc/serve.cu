@@ -8,7 +8,11 @@
 //    keep running: the batch is never drained to admit new work.
 //  - SSSP slots: every running job whose round has completed issues its next round (or its
 //    result copy); a free slot takes the next queued SSSP query. Jobs run on their own
-//    streams, so rounds of different queries overlap on the device.
+//    streams, so rounds of different queries overlap on the device. Batched jobs (when
+//    enabled) take up to sb_job_lanes() queued SSSP queries at once as one multi-lane
+//    search that reads each edge once for all of them; the worker starts one when no
+//    single-query slot is free or when at least half a batch is waiting, so a lone query
+//    keeps the lower latency of a single job.
 //  - completions: a query is complete when the event recorded after its result writes has
 //    completed; it is then handed to graph_server_poll with its timestamps.
 // Nothing blocks on the device: the loop only queries events, and sleeps briefly (or until
@@ -56,11 +60,13 @@ struct graph_server {
   graph* g = nullptr;
   int out_mem = GRAPH_MEM_HOST;
   uint32_t sssp_delta = 0;  // near-far bucket width of the SSSP jobs
+  bool sssp_batch = false;  // batched SSSP jobs enabled
   Clock::time_point t0;
   BfsLanes* lanes = nullptr;
   uint32_t nlanes = 0;
   std::vector<SsspJob*> jobs;
-  uint64_t bytes_lanes = 0, bytes_job = 0, budget = 0;
+  std::vector<SbJob*> bjobs;
+  uint64_t bytes_lanes = 0, bytes_job = 0, bytes_bjob = 0, budget = 0;
 
   std::thread worker;
   std::mutex mu;
@@ -75,9 +81,12 @@ struct graph_server {
   Query lane_q[GRAPH_BATCH_MAX];
   std::vector<Query> job_q;
   std::vector<char> job_busy;
+  std::vector<std::vector<Query>> bjob_q;
+  std::vector<char> bjob_busy;
   std::vector<cudaEvent_t> ev_free;
   std::deque<LaneBatch> lane_batches;
-  std::atomic<uint32_t> max_lanes_busy{0}, max_slots_busy{0};
+  std::atomic<uint32_t> max_lanes_busy{0}, max_slots_busy{0}, max_batch_busy{0};
+  std::atomic<uint64_t> sssp_batched{0};
   std::atomic<uint64_t> bfs_steps{0};
   graph_status lane_error = GRAPH_OK;
 
@@ -212,41 +221,91 @@ bool finish_lane_batches(graph_server* s) {
 bool step_jobs(graph_server* s, std::deque<Query>& pend) {
   graph* g = s->g;
   bool prog = false;
-  uint32_t busy = 0;
+  // completions
   for (size_t i = 0; i < s->jobs.size(); ++i) {
-    if (s->job_busy[i]) {
-      int rounds = 0;
-      const int r = sssp_job_poll(g, s->jobs[i], &rounds);
-      if (r != 0) {
-        Query q = s->job_q[i];
-        q.supersteps = rounds;
-        emit(s, q, r == 1 ? GRAPH_OK : r, s->now());
-        s->job_busy[i] = 0;
-        prog = true;
-      }
-    }
-    if (!s->job_busy[i] && !pend.empty()) {
-      Query q = pend.front();
-      pend.pop_front();
-      q.t_admit = s->now();
-      const graph_status st =
-          sssp_job_start(g, s->jobs[i], q.source, q.out, s->out_mem, s->sssp_delta);
-      if (st != GRAPH_OK) {
-        emit(s, q, st, s->now());
-      } else {
-        s->job_q[i] = q;
-        s->job_busy[i] = 1;
-      }
+    if (!s->job_busy[i]) continue;
+    int rounds = 0;
+    const int r = sssp_job_poll(g, s->jobs[i], &rounds);
+    if (r != 0) {
+      Query q = s->job_q[i];
+      q.supersteps = rounds;
+      emit(s, q, r == 1 ? GRAPH_OK : r, s->now());
+      s->job_busy[i] = 0;
       prog = true;
     }
-    busy += s->job_busy[i] ? 1 : 0;
   }
-  if (s->jobs.empty())
+  for (size_t i = 0; i < s->bjobs.size(); ++i) {
+    if (!s->bjob_busy[i]) continue;
+    int rounds = 0;
+    const int r = sb_job_poll(g, s->bjobs[i], &rounds);
+    if (r != 0) {
+      const double t = s->now();
+      for (Query q : s->bjob_q[i]) {
+        q.supersteps = rounds;
+        emit(s, q, r == 1 ? GRAPH_OK : r, t);
+      }
+      s->sssp_batched += s->bjob_q[i].size();
+      s->bjob_q[i].clear();
+      s->bjob_busy[i] = 0;
+      prog = true;
+    }
+  }
+  // admission, oldest first
+  const size_t width = sb_job_lanes();
+  while (!pend.empty()) {
+    int fs = -1, fb = -1;
+    for (size_t i = 0; i < s->jobs.size() && fs < 0; ++i)
+      if (!s->job_busy[i]) fs = (int)i;
+    for (size_t i = 0; i < s->bjobs.size() && fb < 0; ++i)
+      if (!s->bjob_busy[i]) fb = (int)i;
+    if (fb >= 0 && (fs < 0 || pend.size() >= width / 2)) {
+      const size_t k = pend.size() < width ? pend.size() : width;
+      std::vector<Query> qs;
+      uint32_t src[GRAPH_SSSP_BATCH_MAX];
+      uint32_t* outs[GRAPH_SSSP_BATCH_MAX];
+      const double t = s->now();
+      for (size_t l = 0; l < k; ++l) {
+        Query q = pend.front();
+        pend.pop_front();
+        q.t_admit = t;
+        src[l] = q.source;
+        outs[l] = q.out;
+        qs.push_back(q);
+      }
+      const graph_status st = sb_job_start(g, s->bjobs[fb], src, (uint32_t)k, outs, s->out_mem);
+      if (st != GRAPH_OK) {
+        for (const Query& q : qs) emit(s, q, st, s->now());
+      } else {
+        s->bjob_q[fb] = std::move(qs);
+        s->bjob_busy[fb] = 1;
+      }
+      prog = true;
+      continue;
+    }
+    if (fs < 0) break;
+    Query q = pend.front();
+    pend.pop_front();
+    q.t_admit = s->now();
+    const graph_status st =
+        sssp_job_start(g, s->jobs[fs], q.source, q.out, s->out_mem, s->sssp_delta);
+    if (st != GRAPH_OK) {
+      emit(s, q, st, s->now());
+    } else {
+      s->job_q[fs] = q;
+      s->job_busy[fs] = 1;
+    }
+    prog = true;
+  }
+  if (s->jobs.empty() && s->bjobs.empty())
     while (!pend.empty()) {
       emit(s, pend.front(), GRAPH_EINVAL, s->now());
       pend.pop_front();
     }
+  uint32_t busy = 0, bbusy = 0;
+  for (char b : s->job_busy) busy += b ? 1 : 0;
+  for (char b : s->bjob_busy) bbusy += b ? 1 : 0;
   bump(s->max_slots_busy, busy);
+  bump(s->max_batch_busy, bbusy);
   return prog;
 }
 
@@ -256,6 +315,8 @@ bool idle(const graph_server* s) {
     return false;
   if (!s->lane_batches.empty()) return false;
   for (char b : s->job_busy)
+    if (b) return false;
+  for (char b : s->bjob_busy)
     if (b) return false;
   return true;
 }
@@ -292,10 +353,12 @@ void destroy_parts(graph_server* s) {
   graph* g = s->g;
   if (s->lanes) bfs_lanes_destroy(g, s->lanes);
   for (SsspJob* j : s->jobs) sssp_job_destroy(g, j);
+  for (SbJob* j : s->bjobs) sb_job_destroy(g, j);
   for (cudaEvent_t e : s->ev_free) cudaEventDestroy(e);
   for (LaneBatch& b : s->lane_batches) cudaEventDestroy(b.ev);
   s->lanes = nullptr;
   s->jobs.clear();
+  s->bjobs.clear();
   s->ev_free.clear();
   s->lane_batches.clear();
 }
@@ -310,13 +373,23 @@ graph_status build(graph_server* s, const graph_server_attr& at) {
   s->nlanes = nl;
   s->bytes_lanes = nl ? bfs_lanes_bytes(g, nl) : 0;
   s->bytes_job = sssp_job_bytes(g);
-  uint64_t slots = 0;
+  s->bytes_bjob = s->sssp_batch ? sb_job_bytes(g) : 0;
+  uint64_t slots = 0, bslots = 0;
   if (g->weighted) {
-    slots = (s->budget - s->bytes_lanes) / s->bytes_job;
-    const uint64_t cap = at.max_sssp ? at.max_sssp : 64;
+    uint64_t avail = s->budget - s->bytes_lanes;
+    if (s->sssp_batch) {
+      // batched jobs: up to half of the SSSP share of the budget, at most 8
+      bslots = (avail / 2) / s->bytes_bjob;
+      if (bslots > 8) bslots = 8;
+      avail -= bslots * s->bytes_bjob;
+    }
+    slots = avail / s->bytes_job;
+    // With batched jobs, a few single-query slots serve a light load at the lower latency
+    // of a single search; under load the waiting queries then gather into batches.
+    const uint64_t cap = at.max_sssp ? at.max_sssp : (s->sssp_batch && bslots ? 4 : 64);
     if (slots > cap) slots = cap;
   }
-  if (nl == 0 && slots == 0) {
+  if (nl == 0 && slots == 0 && bslots == 0) {
     set_error("mem_budget %llu holds neither a BFS lane set nor an SSSP job",
               (unsigned long long)s->budget);
     return GRAPH_ENOMEM;
@@ -329,6 +402,13 @@ graph_status build(graph_server* s, const graph_server_attr& at) {
   }
   s->job_q.assign(s->jobs.size(), Query());
   s->job_busy.assign(s->jobs.size(), 0);
+  for (uint64_t i = 0; i < bslots; ++i) {
+    SbJob* j = nullptr;
+    GG_TRY(sb_job_create(g, &j));
+    s->bjobs.push_back(j);
+  }
+  s->bjob_q.assign(s->bjobs.size(), std::vector<Query>());
+  s->bjob_busy.assign(s->bjobs.size(), 0);
   for (uint32_t i = 0; i < nl + 2; ++i) {
     cudaEvent_t e;
     GG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -365,6 +445,7 @@ graph_status graph_server_create(graph_t* g, const graph_server_attr* attr,
   s->g = g;
   s->out_mem = at.out_mem;
   s->sssp_delta = at.sssp_delta;
+  s->sssp_batch = at.sssp_batch != 0;
   s->t0 = Clock::now();
   graph_status st = build(s, at);
   if (st == GRAPH_OK) {
@@ -394,7 +475,8 @@ graph_status graph_server_submit(graph_server_t* s, int kind, uint32_t source, u
     set_error("source %u >= n %u", source, s->g->n);
     return GRAPH_EINVAL;
   }
-  if ((kind == GRAPH_QUERY_SSSP && s->jobs.empty()) || (kind == GRAPH_QUERY_BFS && !s->lanes)) {
+  if ((kind == GRAPH_QUERY_SSSP && s->jobs.empty() && s->bjobs.empty()) ||
+      (kind == GRAPH_QUERY_BFS && !s->lanes)) {
     set_error("the server has no %s capacity", kind == GRAPH_QUERY_SSSP ? "SSSP" : "BFS");
     return GRAPH_EINVAL;
   }
@@ -452,6 +534,10 @@ graph_status graph_server_info_get(graph_server_t* s, graph_server_info* info) {
   info->max_lanes_busy = s->max_lanes_busy.load();
   info->max_slots_busy = s->max_slots_busy.load();
   info->bfs_supersteps = s->bfs_steps.load();
+  info->sssp_batch_slots = (uint32_t)s->bjobs.size();
+  info->max_batch_busy = s->max_batch_busy.load();
+  info->bytes_per_sssp_batch = s->bytes_bjob;
+  info->sssp_batched = s->sssp_batched.load();
   return GRAPH_OK;
 }
 

@@ -5,7 +5,7 @@
 // active, and the target's row costs the same sector a single distance would.
 //   dist[v][l]   distance of v in search l
 //   snap[v][l]   distance v was last queued (and relaxed) with in search l (INF: never)
-//   tmask[v]     searches in which v was lowered this round; tbits: the same as a bitmap
+//   tbits        vertices lowered (in some search) this round, a bitmap
 //   amask[v]     searches v was queued for in the current round
 // One superstep:
 //  - compute: every queued vertex relaxes its edges lane by lane (hub chunks with the
@@ -13,7 +13,7 @@
 //    a lower candidate is written with an atomic minimum (a reduction no thread waits for)
 //    and marks the target's lane; a boundary target reduces into its outbox row.
 //  - communication: dirty outbox rows are applied to their owners the same way.
-//  - filter and termination: a touched vertex is queued for the lanes whose distance fell
+//  - filter and termination: a touched vertex is queued for the lanes whose distance is
 //    below their queued value; the searches end when no vertex is queued.
 // Results equal those of k separate sssp() calls (plain rounds): shortest distances are
 // unique.
@@ -36,8 +36,7 @@ struct SbCounters {
 };
 
 struct SbWs {
-  DevBuf dist[2], snap[2], tmask[2], tbits[2], amask[2], queue[2][2], hubq[2][2], omsg[2],
-      odirty[2];
+  DevBuf dist[2], snap[2], tbits[2], amask[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
 };
 
@@ -45,9 +44,9 @@ void free_ssspb(graph* g) {
   if (!g->sb) return;
   SbWs* w = g->sb;
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->tmask[p],    &w->tbits[p],
-                     &w->amask[p],    &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],
-                     &w->hubq[p][1],  &w->omsg[p],     &w->odirty[p]};
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->tbits[p],    &w->amask[p],
+                     &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1],
+                     &w->omsg[p],     &w->odirty[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
   delete w;
@@ -60,7 +59,6 @@ struct SbSide {
   PartView P;
   uint32_t* dist;    // [nv][kSbLanes]
   uint32_t* snap;    // [nv][kSbLanes]
-  uint32_t* tmask;   // [nv]
   uint32_t* tbits;   // [words]
   uint32_t* amask;   // [nv]
   uint32_t* nqueue;  // next active queue (bucketed)
@@ -165,11 +163,11 @@ __device__ __forceinline__ void relax_edges_b(const SbSide& S, const uint32_t* d
       }
     }
     if (la) {
-      if (!(xa & kRemote)) { sb_red_or(&S.tmask[xa], la); sb_red_or(&S.tbits[xa >> 5], 1u << (xa & 31u)); }
+      if (!(xa & kRemote)) sb_red_or(&S.tbits[xa >> 5], 1u << (xa & 31u));
       else sb_red_or(&S.odirty[(xa & kIdMask) >> 5], 1u << ((xa & kIdMask) & 31u));
     }
     if (lb) {
-      if (!(xb & kRemote)) { sb_red_or(&S.tmask[xb], lb); sb_red_or(&S.tbits[xb >> 5], 1u << (xb & 31u)); }
+      if (!(xb & kRemote)) sb_red_or(&S.tbits[xb >> 5], 1u << (xb & 31u));
       else sb_red_or(&S.odirty[(xb & kIdMask) >> 5], 1u << ((xb & kIdMask) & 31u));
     }
   }
@@ -253,10 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant_
         #pragma unroll
         for (int l = 0; l < kSbLanes; ++l) fin |= (mv.d[l] != kInf ? 1u : 0u) << l;
         const uint32_t low = relax_row(Q.dist + (size_t)u * kSbLanes, mv.d, fin, 0u, ovf);
-        if (low) {
-          sb_red_or(&Q.tmask[u], low);
-          sb_red_or(&Q.tbits[u >> 5], 1u << (u & 31u));
-        }
+        if (low) sb_red_or(&Q.tbits[u >> 5], 1u << (u & 31u));
       }
     }
   }
@@ -284,15 +279,13 @@ __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ 
       const int b = __ffs(bits) - 1;
       bits &= bits - 1;
       x = word * 32 + b;
-      const uint32_t tm = S.tmask[x];
-      S.tmask[x] = 0;
       const Row d = load_row(S.dist + (size_t)x * kSbLanes);
       uint32_t* sp = S.snap + (size_t)x * kSbLanes;
       const Row q = load_row(sp);
       uint32_t am = 0;
       #pragma unroll
       for (int l = 0; l < kSbLanes; ++l) {
-        if (((tm >> l) & 1u) && d.d[l] < q.d[l]) {
+        if (d.d[l] < q.d[l]) {
           sp[l] = d.d[l];
           am |= 1u << l;
         }
@@ -320,13 +313,17 @@ __global__ void k_sb_init(const __grid_constant__ SbArgs A, const uint32_t* g2l,
   const uint32_t v = gl & kIdMask;
   const SbSide& S = A.side[p];
   S.dist[(size_t)v * kSbLanes + l] = 0;
-  atomicOr(&S.tmask[v], 1u << l);
   atomicOr(&S.tbits[v >> 5], 1u << (v & 31u));
 }
 
-// Lane l's distances into out + l * n (global order), and each lane's reached degree sum.
+// Output rows of the collect: lane l's distances go to rows.p[l] (n uint32, global order).
+struct OutRows {
+  uint32_t* p[kSbLanes];
+};
+
+// Lane l's distances into rows.p[l], and each lane's reached degree sum.
 __global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uint32_t n,
-                             uint32_t k, uint32_t* out, SbCounters* ctr) {
+                             uint32_t k, const __grid_constant__ OutRows rows, SbCounters* ctr) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long d[kSbLanes] = {0};
   if (i < n) {
@@ -336,22 +333,23 @@ __global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uin
     const Row r = load_row(S.dist + (size_t)v * kSbLanes);
     const uint32_t gid = S.P.l2g[v];
     const unsigned long long deg = (unsigned long long)(S.P.off[v + 1] - S.P.off[v]);
-    for (uint32_t l = 0; l < k; ++l) {
-      out[(size_t)l * n + gid] = r.d[l];
+    #pragma unroll
+    for (int l = 0; l < kSbLanes; ++l) {
+      if ((uint32_t)l >= k) break;
+      rows.p[l][gid] = r.d[l];
       if (r.d[l] != kInf) d[l] = deg;
       if (r.d[l] == kInf - 1) atomicOr(&ctr->clamped, 1u);
     }
   }
-  for (uint32_t l = 0; l < k; ++l) {
+  #pragma unroll
+  for (int l = 0; l < kSbLanes; ++l) {
+    if ((uint32_t)l >= k) break;
     const unsigned long long s = warp_sum(d[l]);
     if (lane_id() == 0 && s) atomicAdd(&ctr->reached_degree[l], s);
   }
 }
 
-graph_status alloc_ws(graph* g) {
-  if (g->sb) return GRAPH_OK;
-  SbWs* w = new SbWs();
-  g->sb = w;
+graph_status alloc_ws_into(graph* g, SbWs* w) {
   for (int p = 0; p < 2; ++p) {
     const Part& P = g->part[p];
     // bitmap words rounded to whole warps (the filter assigns one lane per word)
@@ -359,7 +357,6 @@ graph_status alloc_ws(graph* g) {
     w->owords[p] = ((P.nout + 31) / 32 + 31) & ~(size_t)31;
     GG_TRY(dalloc(g, w->dist[p], 4ull * kSbLanes * P.nv));
     GG_TRY(dalloc(g, w->snap[p], 4ull * kSbLanes * P.nv));
-    GG_TRY(dalloc(g, w->tmask[p], 4ull * P.nv));
     GG_TRY(dalloc(g, w->tbits[p], 4 * w->words[p]));
     GG_TRY(dalloc(g, w->amask[p], 4ull * P.nv));
     GG_TRY(dalloc(g, w->queue[p][0], 4ull * P.nv));
@@ -369,6 +366,23 @@ graph_status alloc_ws(graph* g) {
     GG_TRY(dalloc(g, w->omsg[p], 4ull * kSbLanes * P.nout));
     GG_TRY(dalloc(g, w->odirty[p], 4 * w->owords[p]));
   }
+  return GRAPH_OK;
+}
+
+void free_ws_buffers(graph* g, SbWs* w) {
+  for (int p = 0; p < 2; ++p) {
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->tbits[p],    &w->amask[p],
+                     &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1],
+                     &w->omsg[p],     &w->odirty[p]};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+}
+
+graph_status alloc_ws(graph* g) {
+  if (g->sb) return GRAPH_OK;
+  SbWs* w = new SbWs();
+  g->sb = w;
+  GG_TRY(alloc_ws_into(g, w));
   if (g->counters.bytes < sizeof(SbCounters) || !g->counters.p) {
     dfree(g, g->counters);
     GG_TRY(dalloc(g, g->counters, 1024));
@@ -391,7 +405,6 @@ SbArgs make_args(graph* g, SbWs* w, SbCounters* ctr, int cur) {
     S.P = g->part[p].view();
     S.dist = (uint32_t*)w->dist[p].p;
     S.snap = (uint32_t*)w->snap[p].p;
-    S.tmask = (uint32_t*)w->tmask[p].p;
     S.tbits = (uint32_t*)w->tbits[p].p;
     S.amask = (uint32_t*)w->amask[p].p;
     S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
@@ -410,7 +423,217 @@ uint64_t active_count(const SbCounters& c) {
   return a;
 }
 
+// Resets a workspace, puts each source at distance 0 in its lane and queues the sources
+// (round 0's active set) into queues 0.
+graph_status launch_start(graph* g, SbWs* w, SbCounters* ctr, const uint32_t* sources,
+                          uint32_t k, cudaStream_t st) {
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->tbits[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * kSbLanes * P.nout, st));
+    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
+  }
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
+  SbSources src;
+  memset(&src, 0, sizeof(src));
+  for (uint32_t l = 0; l < k; ++l) src.id[l] = sources[l];
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  const SbArgs A = make_args(g, w, ctr, 1);  // the filter appends into queues 0
+  k_sb_init<<<1, 32, 0, st>>>(A, (const uint32_t*)g->g2l.p, src, k);
+  GG_CUDA(cudaGetLastError());
+  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  GG_CUDA(cudaGetLastError());
+  return GRAPH_OK;
+}
+
+// One round: relax the active set c describes (queues `cur`), apply the outbox, filter.
+graph_status launch_round(graph* g, SbWs* w, SbCounters* ctr, const SbCounters& c, int cur,
+                          cudaStream_t st, PhaseTimer* timer, int64_t* launches) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
+  const SbArgs A = make_args(g, w, ctr, cur);
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
+               gsh[b], b);
+  }
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
+  if (timer) timer->mark(2);
+  if (pl.nblocks) k_sb_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(0);
+  if (owords) k_sb_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(1);
+  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  GG_CUDA(cudaGetLastError());
+  if (timer) timer->mark(0);
+  *launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+  return GRAPH_OK;
+}
+
+graph_status launch_collect(graph* g, SbWs* w, SbCounters* ctr, int cur, const OutRows& rows,
+                            uint32_t k, cudaStream_t st) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
+  const SbArgs A = make_args(g, w, ctr, cur);
+  k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, rows, ctr);
+  GG_CUDA(cudaGetLastError());
+  return GRAPH_OK;
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Stepwise batched SSSP jobs for the query server: the rounds of sssp_batch issued one at
+// a time on the job's own stream and advanced when the round's event has completed.
+// ---------------------------------------------------------------------------------------
+struct SbJob {
+  SbWs ws;
+  DevBuf ctr;                  // SbCounters (device)
+  SbCounters* hc = nullptr;    // pinned mirror
+  DevBuf stage;                // result staging for host destinations (kSbLanes rows)
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint32_t* dst[kSbLanes] = {};
+  uint32_t k = 0;
+  int dst_mem = 0;
+  int cur = 0;
+  int phase = 0;               // 0 idle, 1 round in flight, 2 collect in flight
+  int64_t rounds = 0;
+  bool overflow = false;
+};
+
+uint32_t sb_job_lanes() { return (uint32_t)kSbLanes; }
+
+size_t sb_job_bytes(const graph* g) {
+  size_t b = 1024 + 4ull * kSbLanes * g->n;
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    const size_t words = ((P.nv + 31) / 32 + 31) & ~(size_t)31;
+    const size_t owords = ((P.nout + 31) / 32 + 31) & ~(size_t)31;
+    b += (8ull * kSbLanes + 12) * P.nv + 4 * words + 8ull * P.nchunk +
+         4ull * kSbLanes * P.nout + 4 * owords;
+  }
+  return b;
+}
+
+void sb_job_destroy(graph* g, SbJob* j) {
+  if (!j) return;
+  if (j->st) cudaStreamSynchronize(j->st);
+  free_ws_buffers(g, &j->ws);
+  dfree(g, j->ctr);
+  dfree(g, j->stage);
+  if (j->hc) cudaFreeHost(j->hc);
+  if (j->ev) cudaEventDestroy(j->ev);
+  if (j->st) cudaStreamDestroy(j->st);
+  delete j;
+}
+
+static graph_status sb_job_alloc(graph* g, SbJob* j) {
+  GG_TRY(alloc_ws_into(g, &j->ws));
+  GG_TRY(dalloc(g, j->ctr, 1024));
+  GG_TRY(dalloc(g, j->stage, 4ull * kSbLanes * g->n));
+  GG_CUDA(cudaMallocHost(&j->hc, sizeof(SbCounters)));
+  GG_CUDA(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
+  GG_CUDA(cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming));
+  return GRAPH_OK;
+}
+
+graph_status sb_job_create(graph* g, SbJob** out) {
+  SbJob* j = new SbJob();
+  const graph_status s = sb_job_alloc(g, j);
+  if (s != GRAPH_OK) {
+    sb_job_destroy(g, j);
+    return s;
+  }
+  *out = j;
+  return GRAPH_OK;
+}
+
+graph_status sb_job_start(graph* g, SbJob* j, const uint32_t* sources, uint32_t k,
+                          uint32_t* const* dst, int dst_mem) {
+  if (k < 1 || k > (uint32_t)kSbLanes) {
+    set_error("a batched SSSP job takes 1..%d searches", kSbLanes);
+    return GRAPH_EINVAL;
+  }
+  j->k = k;
+  for (uint32_t l = 0; l < k; ++l) j->dst[l] = dst[l];
+  j->dst_mem = dst_mem;
+  j->cur = 0;
+  j->rounds = 0;
+  j->overflow = false;
+  SbCounters* dc = (SbCounters*)j->ctr.p;
+  GG_TRY(launch_start(g, &j->ws, dc, sources, k, j->st));
+  GG_CUDA(cudaMemcpyAsync(j->hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, j->st));
+  GG_CUDA(cudaEventRecord(j->ev, j->st));
+  j->phase = 1;
+  return GRAPH_OK;
+}
+
+static int sb_job_fail(SbJob* j, graph_status s) {
+  j->phase = 0;
+  return s;
+}
+
+int sb_job_poll(graph* g, SbJob* j, int* rounds) {
+  if (j->phase == 0) return 0;
+  const cudaError_t q = cudaEventQuery(j->ev);
+  if (q == cudaErrorNotReady) return 0;
+  if (q != cudaSuccess) return sb_job_fail(j, cuda_fail(q, "sssp batch job event", __FILE__, __LINE__));
+  if (rounds) *rounds = (int)j->rounds;
+  SbCounters* dc = (SbCounters*)j->ctr.p;
+  if (j->phase == 2) {
+    j->phase = 0;
+    if (j->overflow && j->hc->clamped) {
+      set_error("a shortest distance reached 2^32 - 1");
+      return GRAPH_ERANGE;
+    }
+    return 1;
+  }
+  const SbCounters c = *j->hc;
+  j->overflow |= c.overflow != 0;
+  if (active_count(c) == 0) {
+    OutRows rows;
+    memset(&rows, 0, sizeof(rows));
+    for (uint32_t l = 0; l < j->k; ++l)
+      rows.p[l] = j->dst_mem == GRAPH_MEM_DEVICE ? j->dst[l]
+                                                 : (uint32_t*)j->stage.p + (size_t)l * g->n;
+    graph_status s = launch_collect(g, &j->ws, dc, j->cur, rows, j->k, j->st);
+    if (s != GRAPH_OK) return sb_job_fail(j, s);
+    cudaError_t e = cudaSuccess;
+    if (j->dst_mem != GRAPH_MEM_DEVICE)
+      for (uint32_t l = 0; l < j->k && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync(j->dst[l], rows.p[l], 4ull * g->n, cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(j->hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+    if (e != cudaSuccess)
+      return sb_job_fail(j, cuda_fail(e, "sssp batch job collect", __FILE__, __LINE__));
+    j->phase = 2;
+    return 0;
+  }
+  if (j->rounds >= (int64_t)g->n + 1) {
+    set_error("sssp batch job reached the superstep cap");
+    return sb_job_fail(j, GRAPH_ETIMEOUT);
+  }
+  int64_t launches = 0;
+  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches);
+  if (s != GRAPH_OK) return sb_job_fail(j, s);
+  cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, j->st);
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+  if (e != cudaSuccess) return sb_job_fail(j, cuda_fail(e, "sssp batch job round", __FILE__, __LINE__));
+  j->cur = 1 - j->cur;
+  j->rounds++;
+  return 0;
+}
+
 }  // namespace gg
 
 using namespace gg;
@@ -458,36 +681,13 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
-  for (int p = 0; p < 2; ++p) {
-    const Part& P = g->part[p];
-    GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
-    GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * kSbLanes * P.nv, st));
-    GG_CUDA(cudaMemsetAsync(w->tmask[p].p, 0, 4ull * P.nv, st));
-    GG_CUDA(cudaMemsetAsync(w->tbits[p].p, 0, 4 * w->words[p], st));
-    GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * kSbLanes * P.nout, st));
-    GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
-  }
-  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
-  SbSources src;
-  memset(&src, 0, sizeof(src));
-  for (uint32_t l = 0; l < k; ++l) src.id[l] = sources[l];
-  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
-  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
-  int cur = 0;
-  {
-    // round 0's active set: the sources, queued by the filter into queues `cur`
-    const SbArgs A = make_args(g, w, dc, 1);
-    k_sb_init<<<1, 32, 0, st>>>(A, (const uint32_t*)g->g2l.p, src, k);
-    GG_CUDA(cudaGetLastError());
-    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
-    GG_CUDA(cudaGetLastError());
-  }
+  GG_TRY(launch_start(g, w, dc, sources, k, st));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
   GG_CUDA(cudaStreamSynchronize(st));
   timer.mark(2);
   int64_t inspected = 0, messages = 0, launches = 2, rounds = 0;
   bool overflow = false;
-  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  int cur = 0;
   for (;; ++rounds) {
     const SbCounters c = *hc;
     if (active_count(c) == 0) break;
@@ -496,28 +696,7 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
       timer.finish(nullptr);
       return GRAPH_ETIMEOUT;
     }
-    GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
-    const SbArgs A = make_args(g, w, dc, cur);
-    Plan pl;
-    memset(&pl, 0, sizeof(pl));
-    for (int p = 0; p < 2; ++p) {
-      const PartView V = g->part[p].view();
-      plan_add(pl, (const uint32_t*)w->hubq[p][cur].p, 0, c.tail[p][0], p, 8, 0);
-      for (int b = 1; b < kNBucket; ++b)
-        plan_add(pl, (const uint32_t*)w->queue[p][cur].p + V.bstart[b], 0, c.tail[p][b], p,
-                 gsh[b], b);
-    }
-    timer.mark(2);
-    if (pl.nblocks) k_sb_relax<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(0);
-    if (owords) k_sb_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(1);
-    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
-    GG_CUDA(cudaGetLastError());
-    timer.mark(0);
-    launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches));
     GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;
@@ -530,13 +709,11 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
     GG_TRY(ensure_stage(g, 4ull * k * g->n + 64));
     dd = (uint32_t*)g->stage.p;
   }
-  GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SbCounters), st));
-  {
-    const SbArgs A = make_args(g, w, dc, cur);
-    k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, dd, dc);
-    GG_CUDA(cudaGetLastError());
-    launches++;
-  }
+  OutRows rows;
+  memset(&rows, 0, sizeof(rows));
+  for (uint32_t l = 0; l < k; ++l) rows.p[l] = dd + (size_t)l * g->n;
+  GG_TRY(launch_collect(g, w, dc, cur, rows, k, st));
+  launches++;
   if (at.out_mem == GRAPH_MEM_HOST)
     GG_TRY(deliver(g, dist, dd, 4ull * k * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));

@@ -91,6 +91,30 @@ def test_server_near_far_sssp_matches_oracle(gpu):
     H.free()
 
 
+def test_server_batched_sssp_matches_oracle(gpu):
+    """A burst of SSSP-heavy queries with batched SSSP jobs enabled: queries that wait
+    together share sssp_batch searches, and every result still equals the oracle's."""
+    g = rmat_graph(14)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=64)
+    qs = [("sssp" if i % 3 else "bfs", s) for i, (_, s) in enumerate(mixed_queries(g, 120, 12))]
+    done, info = run_mix(gpu, H, g, qs, sssp_batch=True, max_sssp=2)
+    assert info["sssp_batch_slots"] > 0
+    assert info["sssp_batched"] > 0, "no query ran on a batched job"
+    H.free()
+
+
+def test_server_batched_sssp_host_outputs_and_partitions(gpu):
+    g = rmat_graph(13, seed=5, wmax=255, wseed=7)
+    for p in (PARTITIONS[0], PARTITIONS[4], PARTITIONS[6]):
+        H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+        apply_partition(gpu, H, g, p)
+        qs = [("sssp", s) for _, s in mixed_queries(g, 40, 13)]
+        done, info = run_mix(gpu, H, g, qs, out="host", sssp_batch=True, max_sssp=1)
+        assert info["sssp_batched"] > 0
+        H.free()
+
+
 def test_server_lanes_join_while_others_run(gpu):
     """Staggered arrivals: some BFS query is admitted while another is still in flight, and
     both results are exact."""
