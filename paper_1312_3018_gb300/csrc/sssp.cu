@@ -126,24 +126,37 @@ template <bool CC>
 __device__ __forceinline__ void relax_edges(const SsspSide& S, uint32_t dv, const uint32_t* Ep,
                                             const uint32_t* Wp, int first, int deg, int stride,
                                             unsigned long long& insp, bool& ovf) {
+  // Four edges per step: their ids and weights, then their targets' distances, are all
+  // loaded before any comparison, so each lane keeps several loads in flight.
   const uint64_t pol = l2_evict_first_policy();
-  #pragma unroll 2
-  for (int i = first; i < deg; i += stride) {
-    insp++;
-    const uint32_t x = ld_stream(Ep + i, pol);
-    bool o = false;
-    const uint32_t nd = CC ? dv : sat_add(dv, ld_stream(Wp + i, pol), o);
-    if (!(x & kRemote)) {
-      if (nd < S.dist[x]) {
-        ovf |= o;
-        red_min(&S.dist[x], nd);
-        red_or(&S.touched[x >> 5], 1u << (x & 31u));
+  for (int i = first; i < deg; i += 4 * stride) {
+    uint32_t x[4], nd[4], cur[4];
+    bool o[4];
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ii = i + j * stride;
+      o[j] = false;
+      x[j] = ii < deg ? ld_stream(Ep + ii, pol) : kInf;
+      nd[j] = CC ? dv : sat_add(dv, ii < deg ? ld_stream(Wp + ii, pol) : 0u, o[j]);
+    }
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cur[j] = 0;
+      if (x[j] != kInf) {
+        insp++;
+        cur[j] = (x[j] & kRemote) ? S.omsg[x[j] & kIdMask] : S.dist[x[j]];
       }
-    } else {
-      const uint32_t idx = x & kIdMask;
-      if (nd < S.omsg[idx]) {
-        ovf |= o;
-        red_min(&S.omsg[idx], nd);
+    }
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (x[j] == kInf || !(nd[j] < cur[j])) continue;
+      ovf |= o[j];
+      if (!(x[j] & kRemote)) {
+        red_min(&S.dist[x[j]], nd[j]);
+        red_or(&S.touched[x[j] >> 5], 1u << (x[j] & 31u));
+      } else {
+        const uint32_t idx = x[j] & kIdMask;
+        red_min(&S.omsg[idx], nd[j]);
         red_or(&S.odirty[idx >> 5], 1u << (idx & 31u));
       }
     }
@@ -443,8 +456,10 @@ graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCoun
   const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
   if (timer) timer->mark(2);
   if (pl.nblocks) {
-    if (cc) k_sssp_relax<true><<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
-    else k_sssp_relax<false><<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+    // one CTA per plan block: short-lived CTAs overlap their load phases better than a
+    // fixed grid walking the blocks
+    if (cc) k_sssp_relax<true><<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+    else k_sssp_relax<false><<<pl.nblocks, kThreads, 0, st>>>(pl, A);
   }
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(0);
