@@ -250,8 +250,9 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
  * attr: out_mem, max_supersteps and timing as for sssp; delta must be 0.
  * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator;
  * edges_inspected counts edge entries read (once per pass, whatever the number of lanes).
- * Device workspace: 76 bytes per vertex and 36 per outbox slot, kept with the graph until
- * it is re-partitioned or freed. Errors: EINVAL, ESTATE, ETIMEOUT, ERANGE, ENOMEM, ECUDA.
+ * Device workspace: about 76 bytes per vertex (distance and queued rows, lane mask, queues)
+ * and 32 per outbox slot, kept with the graph until it is re-partitioned or freed.
+ * Errors: EINVAL, ESTATE, ETIMEOUT, ERANGE, ENOMEM, ECUDA.
  * ------------------------------------------------------------------------------------- */
 #define GRAPH_SSSP_BATCH_MAX 8u
 
