@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     ap.add_argument("--no-sssp-batch", action="store_true",
                     help="serving: SSSP queries on single-query jobs only")
+    ap.add_argument("--serve-max-sssp", type=int, default=0,
+                    help="serving: single-query SSSP slots (0: the library's default)")
     ap.add_argument("--sssp-delta", type=int, default=64,
                     help="near-far bucket width of the step's SSSP (0: plain active-set rounds)")
     return ap.parse_args()
@@ -166,7 +168,8 @@ def serving_bench(G, a, torch):
     nbuf = 400
     bufs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(nbuf)]
     points = []
-    with G.Server(H, out="device", sssp_delta=delta, sssp_batch=not a.no_sssp_batch) as srv:
+    with G.Server(H, out="device", sssp_delta=delta, sssp_batch=not a.no_sssp_batch,
+                  max_sssp=a.serve_max_sssp) as srv:
         info0 = srv.info()
         for i in range(64):  # warm-up
             srv.submit("bfs" if i % 3 else "sssp", int(srcs[i]), bufs[i])

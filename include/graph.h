@@ -391,7 +391,7 @@ typedef struct graph_server graph_server_t;
 typedef struct {
   uint64_t mem_budget; /* bytes for per-query state; 0: half of the free device memory */
   uint32_t bfs_lanes;  /* BFS lanes, 1..64 (0: 64) */
-  uint32_t max_sssp;   /* upper bound on single-query SSSP slots (0: 64, or 4 next to
+  uint32_t max_sssp;   /* upper bound on single-query SSSP slots (0: 64, or 16 next to
                           batched jobs); the budget may allow fewer */
   int out_mem;         /* GRAPH_MEM_HOST (pinned recommended) or _DEVICE for outputs */
   uint32_t sssp_delta; /* SSSP queries: near-far bucket width (0: plain rounds), as sssp() */
