@@ -15,22 +15,23 @@
 //
 // Work items (one CTA each): hub chunks (kHubChunk edges of a vertex of degree >= 2048;
 // each warp's partial sum of the chunk goes to hubsum[item][warp], and k_pr_hubs then adds
-// each hub's partials in chunk and warp order and updates the hub), class tiles (kLeafEdges >> (c-1) vertices of
-// degree class c, so at most kTileE edges; 2^(c-3) threads per vertex, one round) and
-// tiles of degree-zero vertices. Items are resolved once per workspace into a table of
-// 32-byte records (edge range, vertex range, kind), read with an L2 keep-resident hint, so
-// a CTA issues its bulk copies after one L2 hit. A CTA stages its item's edge ids, offsets
-// and previous ranks into shared memory with bulk copies (TMA engine) completing on an
-// mbarrier, issues all of its gathers before consuming any, then reduces per vertex from
-// shared memory. Nothing in a CTA waits for another CTA: short-lived CTAs keep 8 per SM
-// resident, and the number of gathers in flight per SM is what sets the speed (the
-// kernel is bound by gather latency, not by bandwidth).
+// each hub's partials in chunk and warp order and updates the hub), class tiles (at most
+// kPrTileV vertices of degree class c, so at most kTileE edges) and tiles of degree-zero
+// vertices. Items are resolved once per workspace into a table of 32-byte records (edge
+// range, vertex range, kind), read with an L2 keep-resident hint, so a CTA issues its bulk
+// copies after one L2 hit. A CTA stages its item's edge ids, offsets and previous ranks
+// into shared memory with bulk copies (TMA engine) completing on an mbarrier. In a class
+// tile the 2^(c-3) threads of a vertex gather its edges at that stride (at most 8 each,
+// all issued before any is used) and add them in registers. Nothing in a CTA waits for
+// another CTA: short-lived CTAs keep 8 per SM resident (the freed shared memory goes to
+// L1), and the number of gathers in flight per SM is what sets the speed (the kernel is
+// bound by gather latency and the load pipes, not by DRAM bandwidth).
 //
 // Degree-zero vertices: their neighbour sum is empty, so each of them holds exactly the
 // iteration's constant term. Their share of the dangling mass D and of the residual is
 // therefore (count x constant) and (count x |change of the constant|), formed in FP64 by
-// the last block; no per-vertex FP64 work is done (this GPU's FP64 rate is far below its
-// FP32 rate).
+// the finalize kernel; no per-vertex FP64 work is done (this GPU's FP64 rate is far below
+// its FP32 rate).
 //
 // Precision variants: FP32 contributions and sums; FP64 throughout; FP16 contributions
 // scaled by n (x = n r/deg keeps them away from FP16's subnormal range) with FP32 sums.
