@@ -237,7 +237,7 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
 
 /* ---------------------------------------------------------------------------------------
  * sssp_batch -- k <= GRAPH_SSSP_BATCH_MAX shortest-path searches in one sequence of
- * Bellman-Ford supersteps (Section 7.3, Figure 20, in plain rounds). The paper runs one
+ * Bellman-Ford supersteps (Section 7.3, Figure 20). The paper runs one
  * search per call; here every vertex carries a row of 8 distances (one 32-byte sector,
  * lane s belonging to search s), a vertex is queued for the searches whose distance
  * improved, and one relaxation pass reads each of its edge ids and weights once for all of
@@ -247,7 +247,12 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
  *   k        1 <= k <= GRAPH_SSSP_BATCH_MAX (other values: EINVAL)
  *   dist     k * n uint32, row s (dist + s * n) = the distances sssp returns for
  *            sources[s], global order, INF unreachable. Host or device per attr->out_mem.
- * attr: out_mem, max_supersteps and timing as for sssp; delta must be 0.
+ * attr: out_mem, max_supersteps and timing as for sssp; delta > 0 runs the near-far order
+ * with one threshold for all k searches (a lane is queued while its distance is below
+ * it; when nothing is queued it moves to the smallest waiting distance + delta). The
+ * threshold staggers the lanes, so a vertex reads its edges once per group of lanes
+ * activated together instead of once: on RMAT it relaxes more edges than plain rounds
+ * (delta = 0), which is the faster choice for batches.
  * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator;
  * edges_inspected counts edge entries read (once per pass, whatever the number of lanes).
  * Device workspace: about 76 bytes per vertex (distance and queued rows, lane mask, queues)
@@ -374,7 +379,8 @@ graph_status pagerank_multi(graph_t* g, uint32_t ngraphs, const uint32_t* vbase,
  *  - SSSP queries each run on an SSSP job with its own workspace and stream; up to
  *    sssp_slots jobs run at once, their supersteps overlapping on the device. With
  *    attr.sssp_batch, batched jobs are added: queries that wait together are started as
- *    one sssp_batch search of up to GRAPH_SSSP_BATCH_MAX lanes (shared edge reads).
+ *    one sssp_batch search of up to GRAPH_SSSP_BATCH_MAX lanes (shared edge reads, plain
+ *    rounds); single-query jobs use attr.sssp_delta.
  *  - Admission is by device memory: at creation the server sizes the lanes and the job
  *    slots to mem_budget (per-query state: bfs_lanes_bytes once, sssp_job_bytes per
  *    slot) and allocates them; a query waits in FIFO order until a lane or a slot is free.
@@ -394,11 +400,11 @@ typedef struct {
   uint32_t max_sssp;   /* upper bound on single-query SSSP slots (0: 64, or 16 next to
                           batched jobs); the budget may allow fewer */
   int out_mem;         /* GRAPH_MEM_HOST (pinned recommended) or _DEVICE for outputs */
-  uint32_t sssp_delta; /* SSSP queries: near-far bucket width (0: plain rounds), as sssp() */
+  uint32_t sssp_delta; /* single-query SSSP jobs: near-far bucket width (0: plain rounds) */
   uint32_t sssp_batch; /* 0: SSSP queries run one per job; 1: also on batched jobs, where up
                           to GRAPH_SSSP_BATCH_MAX queries waiting together share one
-                          sssp_batch search (plain rounds), taken when no single-query slot
-                          is free or at least half a batch waits */
+                          sssp_batch search, taken when no single-query slot is free or at
+                          least half a batch waits */
 } graph_server_attr;
 
 typedef struct {

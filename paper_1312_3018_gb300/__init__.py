@@ -241,9 +241,10 @@ def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_superstep
 
 
 def sssp_batch(g: Graph, sources, dist=None, *, out: str = "device", max_supersteps: int = 0,
-               timing: bool = False):
+               timing: bool = False, delta: int = 0):
     """k = len(sources) <= SSSP_BATCH_MAX shortest-path searches in one pass of Bellman-Ford
-    supersteps; distances [k, n] uint32 (row s for sources[s], INF unreachable) and stats."""
+    supersteps (delta > 0: near-far order with one threshold for all searches); distances
+    [k, n] uint32 (row s for sources[s], INF unreachable) and stats."""
     torch = _torch()
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64))
     if src.ndim != 1 or np.any(src < 0) or np.any(src >= 2**32):
@@ -254,7 +255,7 @@ def sssp_batch(g: Graph, sources, dist=None, *, out: str = "device", max_superst
         dist = (torch.empty((k, g.n), dtype=torch.int32, device="cuda") if out == "device"
                 else np.empty((k, g.n), dtype=np.uint32))
     pd, mem = _ptr(dist)
-    attr = _lib.sssp_attr(mem, max_supersteps, int(timing), 0)
+    attr = _lib.sssp_attr(mem, max_supersteps, int(timing), int(delta))
     stats = _lib.graph_stats()
     st = _lib.load().sssp_batch(g.handle, src.ctypes.data, k, pd, C.byref(attr),
                                 C.byref(stats))

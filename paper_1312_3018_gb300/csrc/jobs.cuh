@@ -29,9 +29,10 @@ uint32_t sb_job_lanes();
 size_t sb_job_bytes(const graph* g);  // device bytes one batched job holds
 graph_status sb_job_create(graph* g, SbJob** out);
 void sb_job_destroy(graph* g, SbJob* j);
-// Starts k searches (plain rounds); search l's distances go to dst[l] when the job ends.
+// Starts k searches; search l's distances go to dst[l] when the job ends. delta: near-far
+// bucket width shared by the lanes (0: plain rounds).
 graph_status sb_job_start(graph* g, SbJob* j, const uint32_t* sources, uint32_t k,
-                          uint32_t* const* dst, int dst_mem);
+                          uint32_t* const* dst, int dst_mem, uint32_t delta);
 // As sssp_job_poll, for all k searches at once.
 int sb_job_poll(graph* g, SbJob* j, int* rounds);
 

@@ -272,7 +272,9 @@ bool step_jobs(graph_server* s, std::deque<Query>& pend) {
         outs[l] = q.out;
         qs.push_back(q);
       }
-      const graph_status st = sb_job_start(g, s->bjobs[fb], src, (uint32_t)k, outs, s->out_mem);
+      // plain rounds: a shared near-far threshold staggers the lanes, so a vertex would
+      // read its edges again for each lane it waited in, losing the shared reads
+      const graph_status st = sb_job_start(g, s->bjobs[fb], src, (uint32_t)k, outs, s->out_mem, 0);
       if (st != GRAPH_OK) {
         for (const Query& q : qs) emit(s, q, st, s->now());
       } else {

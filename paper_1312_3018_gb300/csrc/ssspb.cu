@@ -15,6 +15,10 @@
 //  - communication: dirty outbox rows are applied to their owners the same way.
 //  - filter and termination: a touched vertex is queued for the lanes whose distance is
 //    below their queued value; the searches end when no vertex is queued.
+//  - optional near-far order (delta > 0), one threshold tau for all lanes: a lane is queued
+//    only while its distance is below tau; a vertex with improved lanes at or above tau
+//    stays touched, and when nothing is queued tau moves to the smallest such distance +
+//    delta (every lane starts at 0, so their frontiers stay at similar distances).
 // Results equal those of k separate sssp() calls (plain rounds): shortest distances are
 // unique.
 #include <string.h>
@@ -28,6 +32,8 @@ constexpr int kSbLanes = 8;  // distances per vertex row (one 32-byte sector)
 struct SbCounters {
   uint32_t tail[2][kNBucket];  // next-round work: [0] hub chunks, [1..3] vertices
   uint32_t overflow;
+  uint32_t far;                // (vertex, lane) pairs left waiting at or above the threshold
+  uint32_t far_key;            // max of ~dist over them (zero-initialised counters work)
   uint32_t pad;
   unsigned long long inspected;
   unsigned long long messages;
@@ -258,16 +264,18 @@ __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant_
   sb_flush(0, msgs, ovf, A.ctr);
 }
 
-// Filter: a touched vertex is queued for the lanes whose distance fell below their queued
-// value (which then becomes that distance). One lane per bitmap word; lanes walk their set
-// bits in step so that appends stay warp-aggregated.
+// Filter: a touched vertex is queued for the lanes whose distance is below their queued
+// value (which then becomes that distance) and below tau; lanes at or above tau keep the
+// vertex touched and are counted with their smallest distance. One lane per bitmap word;
+// lanes walk their set bits in step so that appends stay warp-aggregated.
 __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ SbArgs A,
-                                                        uint32_t words0, uint32_t words) {
+                                                        uint32_t words0, uint32_t words,
+                                                        uint32_t tau) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
   const SbSide& S = A.side[p];
-  uint32_t bits = 0;
+  uint32_t bits = 0, keep = 0, nfar = 0, key = 0;
   if (i < words) {
     bits = S.tbits[word];
     if (bits) S.tbits[word] = 0;
@@ -283,13 +291,20 @@ __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ 
       uint32_t* sp = S.snap + (size_t)x * kSbLanes;
       const Row q = load_row(sp);
       uint32_t am = 0;
+      bool wait = false;
       #pragma unroll
       for (int l = 0; l < kSbLanes; ++l) {
-        if (d.d[l] < q.d[l]) {
+        if (!(d.d[l] < q.d[l])) continue;
+        if (d.d[l] < tau) {
           sp[l] = d.d[l];
           am |= 1u << l;
+        } else {
+          wait = true;
+          nfar++;
+          key = max(key, ~d.d[l]);
         }
       }
+      if (wait) keep |= 1u << b;
       if (am) {
         S.amask[x] = am;
         act = true;
@@ -297,6 +312,13 @@ __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ 
     }
     warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
                          S.nhubq);
+  }
+  if (keep) S.tbits[word] = keep;
+  nfar = warp_sum(nfar);
+  key = __reduce_max_sync(kFull, key);
+  if (lane_id() == 0 && nfar) {
+    atomicAdd(&A.ctr->far, nfar);
+    atomicMax(&A.ctr->far_key, key);
   }
 }
 
@@ -443,14 +465,15 @@ graph_status launch_start(graph* g, SbWs* w, SbCounters* ctr, const uint32_t* so
   const SbArgs A = make_args(g, w, ctr, 1);  // the filter appends into queues 0
   k_sb_init<<<1, 32, 0, st>>>(A, (const uint32_t*)g->g2l.p, src, k);
   GG_CUDA(cudaGetLastError());
-  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, kInf);
   GG_CUDA(cudaGetLastError());
   return GRAPH_OK;
 }
 
 // One round: relax the active set c describes (queues `cur`), apply the outbox, filter.
 graph_status launch_round(graph* g, SbWs* w, SbCounters* ctr, const SbCounters& c, int cur,
-                          cudaStream_t st, PhaseTimer* timer, int64_t* launches) {
+                          cudaStream_t st, PhaseTimer* timer, int64_t* launches,
+                          uint32_t tau) {
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
   const SbArgs A = make_args(g, w, ctr, cur);
   Plan pl;
@@ -472,10 +495,29 @@ graph_status launch_round(graph* g, SbWs* w, SbCounters* ctr, const SbCounters& 
   if (owords) k_sb_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(1);
-  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words);
+  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(0);
   *launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
+  return GRAPH_OK;
+}
+
+// Near-far: nothing is queued but lanes wait at or above the threshold. The next threshold
+// is their smallest distance + delta; the filter alone then queues what lies below it for
+// the round that reads queues `cur`.
+uint32_t next_threshold(const SbCounters& c, uint32_t delta) {
+  const uint64_t t = (uint64_t)(~c.far_key) + delta;
+  return t >= kInf ? kInf : (uint32_t)t;
+}
+
+graph_status launch_refilter(graph* g, SbWs* w, SbCounters* ctr, int cur, uint32_t tau,
+                             cudaStream_t st, int64_t* launches) {
+  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
+  const SbArgs A = make_args(g, w, ctr, 1 - cur);  // appends into queues `cur`
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
+  GG_CUDA(cudaGetLastError());
+  *launches += 1;
   return GRAPH_OK;
 }
 
@@ -508,6 +550,8 @@ struct SbJob {
   int phase = 0;               // 0 idle, 1 round in flight, 2 collect in flight
   int64_t rounds = 0;
   bool overflow = false;
+  uint32_t delta = 0;          // near-far bucket width (0: plain rounds)
+  uint32_t tau = kInf;         // current near-far threshold
 };
 
 uint32_t sb_job_lanes() { return (uint32_t)kSbLanes; }
@@ -558,12 +602,14 @@ graph_status sb_job_create(graph* g, SbJob** out) {
 }
 
 graph_status sb_job_start(graph* g, SbJob* j, const uint32_t* sources, uint32_t k,
-                          uint32_t* const* dst, int dst_mem) {
+                          uint32_t* const* dst, int dst_mem, uint32_t delta) {
   if (k < 1 || k > (uint32_t)kSbLanes) {
     set_error("a batched SSSP job takes 1..%d searches", kSbLanes);
     return GRAPH_EINVAL;
   }
   j->k = k;
+  j->delta = delta;
+  j->tau = delta ? delta : kInf;
   for (uint32_t l = 0; l < k; ++l) j->dst[l] = dst[l];
   j->dst_mem = dst_mem;
   j->cur = 0;
@@ -599,6 +645,18 @@ int sb_job_poll(graph* g, SbJob* j, int* rounds) {
   }
   const SbCounters c = *j->hc;
   j->overflow |= c.overflow != 0;
+  if (active_count(c) == 0 && c.far != 0) {
+    // near-far: raise the threshold and queue the waiting lanes below it
+    int64_t launches = 0;
+    j->tau = next_threshold(c, j->delta);
+    graph_status s = launch_refilter(g, &j->ws, dc, j->cur, j->tau, j->st, &launches);
+    if (s != GRAPH_OK) return sb_job_fail(j, s);
+    cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, j->st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
+    if (e != cudaSuccess)
+      return sb_job_fail(j, cuda_fail(e, "sssp batch job refilter", __FILE__, __LINE__));
+    return 0;
+  }
   if (active_count(c) == 0) {
     OutRows rows;
     memset(&rows, 0, sizeof(rows));
@@ -619,12 +677,12 @@ int sb_job_poll(graph* g, SbJob* j, int* rounds) {
     j->phase = 2;
     return 0;
   }
-  if (j->rounds >= (int64_t)g->n + 1) {
+  if (j->rounds >= ((int64_t)g->n + 1) * (j->delta ? j->k : 1)) {
     set_error("sssp batch job reached the superstep cap");
     return sb_job_fail(j, GRAPH_ETIMEOUT);
   }
   int64_t launches = 0;
-  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches);
+  graph_status s = launch_round(g, &j->ws, dc, c, j->cur, j->st, nullptr, &launches, j->tau);
   if (s != GRAPH_OK) return sb_job_fail(j, s);
   cudaError_t e = cudaMemcpyAsync(j->hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, j->st);
   if (e == cudaSuccess) e = cudaEventRecord(j->ev, j->st);
@@ -668,11 +726,10 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
     set_error("bad out_mem");
     return GRAPH_EINVAL;
   }
-  if (at.delta != 0) {
-    set_error("sssp_batch runs plain rounds: delta must be 0");
-    return GRAPH_EINVAL;
-  }
-  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  // Plain rounds end within n + 1 rounds (Bellman-Ford); with one near-far threshold a
+  // round can advance some lanes while others wait, so up to k (n + 1).
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps
+                                            : ((int64_t)g->n + 1) * (at.delta ? k : 1);
   GG_TRY(ensure_ws(g));
   SbWs* w = g->sb;
   cudaStream_t st = g->stream;
@@ -688,15 +745,24 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
   int64_t inspected = 0, messages = 0, launches = 2, rounds = 0;
   bool overflow = false;
   int cur = 0;
+  uint32_t tau = at.delta ? at.delta : kInf;  // the sources have distance 0 < delta
   for (;; ++rounds) {
-    const SbCounters c = *hc;
+    SbCounters c = *hc;
+    while (active_count(c) == 0 && c.far != 0) {
+      // near-far: nothing below the threshold; move it up to the waiting lanes
+      tau = next_threshold(c, at.delta);
+      GG_TRY(launch_refilter(g, w, dc, cur, tau, st, &launches));
+      GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+      c = *hc;
+    }
     if (active_count(c) == 0) break;
     if (rounds >= cap) {
       set_error("sssp_batch reached the superstep cap (%lld)", (long long)cap);
       timer.finish(nullptr);
       return GRAPH_ETIMEOUT;
     }
-    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches));
+    GG_TRY(launch_round(g, w, dc, c, cur, st, &timer, &launches, tau));
     GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     inspected += (int64_t)hc->inspected;

@@ -92,6 +92,8 @@ def test_rmat22_sssp_batch_eight_sources(gpu, rmat22, loaded22):
         assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d[row]) == 0
         total += oracle.traversed(g.n, g.offsets, d[row])
     assert st["edges_traversed"] == total
+    d2, _ = gpu.sssp_batch(loaded22, srcs, out="host", delta=NEAR_FAR_DELTA)
+    assert np.array_equal(d2, d)
 
 
 def test_rmat22_pagerank_to_residual_1e9(gpu, rmat22, loaded22):

@@ -49,6 +49,42 @@ def test_sssp_batch_widths_duplicates_and_isolated(gpu):
     H.free()
 
 
+@pytest.mark.parametrize("p", PARTITIONS[:5], ids=part_id)
+def test_sssp_batch_near_far_rmat14(gpu, p):
+    """Near-far order with one threshold for all lanes: every row still equals the
+    oracle's, for widths from one distance value per bucket to beyond every distance."""
+    g = rmat_graph(14)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    apply_partition(gpu, H, g, p)
+    srcs = [int(s) for s in synth.sources(g, 8, seed=2)]
+    refs = [oracle.sssp(g.n, g.offsets, g.cols, g.weights, s) for s in srcs]
+    for delta in (1, 16, 64, 1 << 30):
+        d, st = gpu.sssp_batch(H, srcs, out="host", delta=delta)
+        for row in range(len(srcs)):
+            assert np.array_equal(d[row], refs[row]), f"delta {delta} row {row}"
+    H.free()
+
+
+def test_sssp_batch_near_far_hub_path_and_duplicates(gpu):
+    g = star_plus(20000, extra_seed=6)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=3)
+    srcs = [0, 5, 5, 19999, 20016]
+    d, _ = gpu.sssp_batch(H, srcs, out="host", delta=8)
+    for row, s in enumerate(srcs):
+        assert np.array_equal(d[row], oracle.sssp(g.n, g.offsets, g.cols, g.weights, s))
+    H.free()
+    n = 3000
+    w = np.random.default_rng(2).integers(1, 256, n - 1)
+    g = synth.from_edges(n, [(i, i + 1) for i in range(n - 1)], w=w)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(n, 0.5, 3))
+    d, _ = gpu.sssp_batch(H, [0, n - 1, 1500], out="host", delta=100)
+    assert np.array_equal(d[0], np.concatenate([[0], np.cumsum(w)]).astype(np.uint32))
+    assert np.array_equal(d[1], np.concatenate([np.cumsum(w[::-1])[::-1], [0]]).astype(np.uint32))
+    H.free()
+
+
 def test_sssp_batch_reads_each_edge_once_per_pass(gpu):
     """Eight copies of one source run the passes of one search: the edge entries read stay
     those of a single search (up to the timing-dependent same-round activations, which
