@@ -5,7 +5,9 @@ symmetrised, deduplicated, vertex ids permuted; uint32 weights uniform in [1, 25
 degree split at a threshold T chosen by timing the step's algorithms at T = 256 ... 32768
 (hub / leaf partitions with outbox/inbox; `--threshold T` fixes it). One step is the whole
 hot path on the resident graph: BFS from one seeded source (levels and parents), SSSP
-from the same source, and 20 iterations of FP32 PageRank (damping 0.85). The graph load
+from the same source (near-far order, width 64; `--sssp-delta 0` runs the plain rounds of
+Figure 20, which are also reported beside it), and 20 iterations of FP32 PageRank (damping
+0.85). The graph load
 and partition are preprocessing (Section 5: only algorithm time is measured) and are
 reported separately.
 
@@ -14,10 +16,13 @@ as in Section 5: BFS and SSSP the degree sum of the reached vertices, PageRank m
 iteration. Per-algorithm rates, the FP64 / FP16 PageRank variants, the roofline of the
 dominant kernel, the CPU oracle baseline and the end-to-end number (host result buffers,
 device-to-host copies inside the timed region) are added to the same JSON line, and so is
-a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one, and
-PageRank of 256 uneven RMAT graphs in one union (pagerank_multi, iterations replayed as a
-CUDA graph) timed against one pagerank() call per graph, and the query server (continuous
-batching of BFS and SSSP queries on a resident RMAT-23 graph) under Poisson arrivals.
+a 64-search batched BFS (bfs_batch) timed against the same 64 searches run one by one, an
+8-search batched SSSP (sssp_batch) against 8 sssp() calls, PageRank of 256 uneven RMAT
+graphs in one union (pagerank_multi, iterations replayed as a CUDA graph) timed against one
+pagerank() call per graph, the query server (continuous batching of BFS and SSSP queries on
+a resident RMAT-23 graph) under Poisson arrivals, betweenness and connected components, and
+the PageRank error of each precision against the oracle's FP64 ranks (computed in the CPU
+baseline leg) and against the GPU's FP64 run.
 
 `--impl reference` times the CPU oracle (the reference arm) on the same
 workload and prints the same kind of line.
@@ -63,7 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
-                    help="skip the PageRank error report against the FP64 oracle")
+                    help="skip the PageRank error report (against the oracle's ranks from the "
+                         "CPU-baseline leg and against the GPU's FP64 run)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the query-server (continuous batching) measurement")
     ap.add_argument("--serve-scale", type=int, default=23)
@@ -109,21 +115,20 @@ def recorded_traffic(profile, source, threshold):
     return None
 
 
-def precision_report(G, H, g, iters_oracle=3, iters_step=20):
-    """PageRank error per precision: L1 and max-abs against the FP64 oracle after
-    iters_oracle iterations (the oracle is single-threaded, so a few iterations bound its
-    time), and after the step's iters_step iterations against the GPU's FP64 run (which the
-    tests hold to 1e-12 of the oracle)."""
-    import oracle
-    t = time.perf_counter()
-    ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=iters_oracle)
-    ts = time.perf_counter() - t
-    rep = {"vs_oracle": {"iterations": iters_oracle, "oracle_s": round(ts, 1)},
-           "vs_gpu_fp64": {"iterations": iters_step}}
-    for prec in ("fp64", "fp32", "fp16"):
-        r, _ = G.pagerank(H, max_iter=iters_oracle, precision=prec, out="host")
-        d = np.abs(r - ref)
-        rep["vs_oracle"][prec] = {"l1": float(d.sum()), "max_abs": float(d.max())}
+def precision_report(G, H, g, ref=None, iters_oracle=3, iters_step=20):
+    """PageRank error per precision: L1 and max-abs against ``ref``, the FP64 oracle's ranks
+    after iters_oracle iterations that the CPU-baseline leg computed (the oracle is
+    single-threaded, so a few iterations bound its time; absent when that leg is off), and
+    after the step's iters_step iterations against the GPU's FP64 run (which the tests hold
+    to 1e-12 of the oracle)."""
+    rep = {}
+    if ref is not None:
+        rep["vs_oracle"] = {"iterations": iters_oracle}
+        for prec in ("fp64", "fp32", "fp16"):
+            r, _ = G.pagerank(H, max_iter=iters_oracle, precision=prec, out="host")
+            d = np.abs(r - ref)
+            rep["vs_oracle"][prec] = {"l1": float(d.sum()), "max_abs": float(d.max())}
+    rep["vs_gpu_fp64"] = {"iterations": iters_step}
     r64, _ = G.pagerank(H, max_iter=iters_step, precision="fp64", out="host")
     for prec in ("fp32", "fp16"):
         r, _ = G.pagerank(H, max_iter=iters_step, precision=prec, out="host")
@@ -344,19 +349,21 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(g, src, budget_s):
+def cpu_baseline(g, src, budget_s, pr_iters=3):
     """Oracle (single-threaded C) on a bounded sample of the step: one BFS from the step's
-    source and one FP64 PageRank iteration; SSSP's Dijkstra is timed only if the sample is
-    still below the budget."""
+    source and pr_iters FP64 PageRank iterations; SSSP's Dijkstra is timed only if the
+    sample is still below the budget. Returns the baseline and the oracle's ranks after
+    pr_iters iterations, against which the GPU's PageRank precisions are reported."""
     import oracle
     t = time.perf_counter()
     lv, _ = oracle.bfs(g.n, g.offsets, g.cols, int(src))
     tb = time.perf_counter() - t
     eb = oracle.traversed(g.n, g.offsets, lv)
     t = time.perf_counter()
-    oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=1)
+    ranks, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=pr_iters)
     tp = time.perf_counter() - t
-    edges, secs, parts = eb + g.m, tb + tp, "BFS (1 source) + 1 FP64 PageRank iteration"
+    edges, secs = eb + pr_iters * g.m, tb + tp
+    parts = f"BFS (1 source) + {pr_iters} FP64 PageRank iterations"
     # Dijkstra costs roughly 6x a BFS on these graphs; include it when it fits the budget.
     if secs + 6 * tb < budget_s:
         t = time.perf_counter()
@@ -366,7 +373,7 @@ def cpu_baseline(g, src, budget_s):
         secs += ts
         parts += " + SSSP (Dijkstra, 1 source)"
     return {"value": edges / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{parts} on the full graph, {secs:.1f} s single-threaded"}
+            "sample": f"{parts} on the full graph, {secs:.1f} s single-threaded"}, ranks
 
 
 def main():
@@ -752,10 +759,11 @@ def main():
 
     if rank != 0:
         return
-    precision = None if a.no_precision else precision_report(G, H, g, iters_step=a.pr_iters)
-    cpu = None
+    cpu, ref = None, None
     if not a.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(g, srcs[0], a.cpu_budget_s)
+        cpu, ref = cpu_baseline(g, srcs[0], a.cpu_budget_s)
+    precision = None if a.no_precision else precision_report(G, H, g, ref,
+                                                             iters_step=a.pr_iters)
     nproc = os.cpu_count()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
