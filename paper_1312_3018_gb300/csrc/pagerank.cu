@@ -620,11 +620,7 @@ __global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t nv0, uin
 // Threads per vertex (log2) of a class-c tile: kLeafEdges >> (c-1) vertices share the
 // CTA's kThreads threads, so every vertex gets 2^(c-3) of them (one round, 4 to 8 edges
 // per thread); classes 1-3 take one thread per vertex.
-#ifndef PR_GS_OLD
 inline int leaf_gshift(int c) { return std::max(0, c - 3); }
-#else
-inline int leaf_gshift(int c) { return std::min(c - 1, 5); }
-#endif
 
 PrPlan make_plan(graph* g) {
   PrPlan pl;
@@ -669,11 +665,9 @@ graph_status prepare_kernel() {
     auto fn = k_pr_compute<PR, MULTI>;
     const int smem = (int)smem_bytes<PR>();
     GG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-#ifndef PR_NO_CARVEOUT
     const int pct = (int)((100.0 * 8 * (smem + 1024) + 228.0 * 1024 - 1) / (228.0 * 1024));
     GG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  std::min(100, pct)));
-#endif
     done = true;
   }
   return GRAPH_OK;
