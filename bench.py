@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched BFS and many-graph PageRank measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="skip the hybrid (host + GPU) PageRank measurement")
     ap.add_argument("--no-sssp-batch", action="store_true",
                     help="serving: SSSP queries on single-query jobs only")
     ap.add_argument("--serve-max-sssp", type=int, default=0,
@@ -347,6 +349,50 @@ def run_reference(a):
         "budget_s_per_step": per_step_budget,
     }
     print(json.dumps(line), flush=True)
+
+
+def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5):
+    """PageRank with the paper's hybrid placement (pagerank_hybrid: partition 0 on the
+    host's cores, partition 1 on the GPU, message arrays crossing every superstep) next to
+    the GPU-only call on the same partition, for HIGH splits that give the host a share of
+    the edge entries. FP32, device ranks; wall-clock time of each call (host and device
+    work overlap), after one warm-up call that also makes the host copies."""
+    out = {"iters": iters, "cpu_threads": os.cpu_count(), "points": []}
+    rr = torch.empty(H.n, dtype=torch.float64, device="cuda")
+    rg = torch.empty(H.n, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3 / iters, st
+
+    for share in shares:
+        info = G.graph_partition(H, "degree", edge_share=share)
+        G.pagerank(H, max_iter=2, precision="fp32", ranks=rg, out="device")
+        gms, _ = timed(lambda: G.pagerank(H, max_iter=iters, precision="fp32", ranks=rg,
+                                          out="device"))
+        G.pagerank_hybrid(H, max_iter=1, precision="fp32", ranks=rr, out="device")
+        hms, st = timed(lambda: G.pagerank_hybrid(H, max_iter=iters, precision="fp32",
+                                                  ranks=rr, out="device", timing=True))
+        h = st["hybrid"]
+        out["points"].append({
+            "edge_share": share, "T": info["threshold"],
+            "cpu_vertices": h["cpu_vertices"], "cpu_edges": h["cpu_edges"],
+            "cpu_edge_share": round(h["cpu_edges"] / m, 4),
+            "hybrid_ms_per_iter": round(hms, 3),
+            "hybrid_gedges_per_s_iter": round(m / (hms / 1e3) / 1e9, 2),
+            "gpu_only_ms_per_iter": round(gms, 3),
+            "cpu_compute_ms_per_iter": round(h["ms_cpu_compute"] / iters, 3),
+            "gpu_compute_ms_per_iter": round(h["ms_gpu_compute"] / iters, 3),
+            "exchange_ms_per_iter": round(h["ms_exchange"] / iters, 3),
+            "messages_per_iter": st["messages"] // max(st["supersteps"], 1),
+            "l1_vs_gpu_only": float((rr - rg).abs().sum())})
+    out["note"] = ("pagerank_hybrid vs pagerank on the same HIGH partition (edge_share: the "
+                   "host's share of edge entries); the graph fits in HBM here, so the host "
+                   "side is the slower processor")
+    return out
 
 
 def cpu_baseline(g, src, budget_s, pr_iters=3):
@@ -764,6 +810,8 @@ def main():
         cpu, ref = cpu_baseline(g, srcs[0], a.cpu_budget_s)
     precision = None if a.no_precision else precision_report(G, H, g, ref,
                                                              iters_step=a.pr_iters)
+    # Last, because it re-partitions the graph.
+    hybrid = None if a.no_hybrid else hybrid_report(G, H, m, torch)
     nproc = os.cpu_count()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -805,6 +853,7 @@ def main():
         "serving": serving,
         "bc_cc": more,
         "pagerank_precision": precision,
+        "hybrid_pagerank": hybrid,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),

@@ -343,6 +343,46 @@ graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* ranks,
                       graph_stats* stats);
 
 /* ---------------------------------------------------------------------------------------
+ * pagerank_hybrid -- PageRank with the paper's hybrid placement (Section 4.1, Figure 6;
+ * Section 6.2, HIGH): partition 0 (with the DEGREE strategy, the vertices of degree >= T,
+ * or of the edge share chosen by edge_share) is updated by cpu_threads host threads from
+ * host copies of its arrays, partition 1 by the GPU, at the same time. Each iteration is one
+ * superstep: the communication phase copies only message arrays across the host/device
+ * boundary (Section 4.3.2): partition 0's ghost slots (contributions of its partition-1
+ * neighbours) go from device to host, and partition 1's ghost slots, gathered on the host,
+ * go from host to device. Then both processors compute their partition, and the residual
+ * is the FP64 sum of both parts. The result is the PageRank of pagerank() (same
+ * attributes and readings) up to the order of the FP32 / FP64 neighbour sums.
+ *   attr         as for pagerank; precision GRAPH_PR_FP32 or GRAPH_PR_FP64 (FP16: EINVAL)
+ *   cpu_threads  host threads, 1 ... GRAPH_HYBRID_MAX_THREADS; <= 0: the host's hardware
+ *                threads (capped at GRAPH_HYBRID_MAX_THREADS)
+ *   ranks        n doubles in global order (host or device per attr->out_mem)
+ *   info         per-processor sizes and times, or NULL
+ * The first call after graph_partition copies partition 0's offsets and edge ids and
+ * partition 1's outbox to host memory (kept with the PageRank workspace until re-partition,
+ * a change of precision or graph_free) and allocates pinned message buffers. Host times
+ * are wall-clock; GPU compute times are CUDA-event times on the handle's stream. Errors:
+ * EINVAL, ESTATE (not partitioned), ENOMEM (host or device), ECUDA, ETIMEOUT.
+ * ------------------------------------------------------------------------------------- */
+#define GRAPH_HYBRID_MAX_THREADS 1024
+
+typedef struct {
+  int cpu_threads;         /* host threads used */
+  uint32_t cpu_vertices;   /* vertices of partition 0 (host) */
+  uint32_t gpu_vertices;   /* vertices of partition 1 (GPU) */
+  int64_t cpu_edges;       /* edge entries of partition 0 */
+  int64_t gpu_edges;       /* edge entries of partition 1 */
+  double ms_cpu_compute;   /* host partition updates, summed over iterations (wall clock) */
+  double ms_gpu_compute;   /* GPU partition kernels, summed over iterations (CUDA events) */
+  double ms_exchange;      /* communication phase on the stream: publication, device-to-host
+                              and host-to-device copies (includes the host's gather when
+                              the stream waits for it), summed over iterations */
+} pagerank_hybrid_info;
+
+graph_status pagerank_hybrid(graph_t* g, const pagerank_attr* attr, int cpu_threads,
+                             double* ranks, graph_stats* stats, pagerank_hybrid_info* info);
+
+/* ---------------------------------------------------------------------------------------
  * pagerank_multi -- PageRank of many independent graphs in one pass of supersteps. The
  * paper ranks one graph per run (Section 7.1, Figure 14); here the loaded graph is the
  * disjoint union of ngraphs components, component c owning global vertex ids

@@ -19,9 +19,10 @@ from ._lib import (GRAPH_BFS_AUTO, GRAPH_BFS_BOTTOMUP, GRAPH_BFS_TOPDOWN, GRAPH_
                    GRAPH_PART_NONE, GRAPH_PR_FP16, GRAPH_PR_FP32, GRAPH_PR_FP64, GraphError)
 
 __all__ = ["graph_load_csr", "graph_partition", "graph_get_partition_info",
-           "graph_export_partition", "bfs", "bfs_batch", "sssp", "sssp_batch", "betweenness", "connected_components", "pagerank", "pagerank_multi", "bfs_csr_noalloc", "Server",
-           "graph_free", "Graph",
-           "GraphError", "INF", "library_path"]
+           "graph_export_partition", "bfs", "bfs_batch", "sssp", "sssp_batch", "betweenness",
+           "connected_components", "pagerank", "pagerank_hybrid", "pagerank_multi",
+           "bfs_csr_noalloc", "Server", "graph_free", "Graph", "GraphError", "INF",
+           "library_path"]
 
 INF = GRAPH_INF
 _PREC = {"fp32": GRAPH_PR_FP32, "fp64": GRAPH_PR_FP64, "fp16": GRAPH_PR_FP16}
@@ -310,6 +311,30 @@ def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float 
     st = _lib.load().pagerank(g.handle, C.byref(attr), pr_, C.byref(stats))
     _lib.check(st, "pagerank")
     return ranks, stats.as_dict()
+
+
+def pagerank_hybrid(g: Graph, *, cpu_threads: int = 0, damping: float = 0.85,
+                    max_iter: int = 20, tol: float = 0.0, precision: str = "fp32",
+                    dangling: bool = True, ranks=None, out: str = "device",
+                    timing: bool = False):
+    """PageRank with partition 0 updated on cpu_threads host threads and partition 1 on
+    the GPU (the paper's hybrid placement). Returns (FP64 ranks in global order, stats);
+    stats["hybrid"] holds the per-processor sizes and times."""
+    torch = _torch()
+    if ranks is None:
+        ranks = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"
+                 else np.empty(g.n, dtype=np.float64))
+    pr_, mem = _ptr(ranks)
+    attr = _lib.pagerank_attr(float(damping), int(max_iter), float(tol), _PREC[precision],
+                              int(bool(dangling)), mem, int(timing))
+    stats = _lib.graph_stats()
+    info = _lib.pagerank_hybrid_info()
+    st = _lib.load().pagerank_hybrid(g.handle, C.byref(attr), int(cpu_threads), pr_,
+                                     C.byref(stats), C.byref(info))
+    _lib.check(st, "pagerank_hybrid")
+    d = stats.as_dict()
+    d["hybrid"] = info.as_dict()
+    return ranks, d
 
 
 def pagerank_multi(g: Graph, vbase, *, damping: float = 0.85, max_iter: int = 30,

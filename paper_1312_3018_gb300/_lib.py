@@ -116,6 +116,18 @@ class pagerank_attr(C.Structure):
                 ("timing", C.c_int)]
 
 
+class pagerank_hybrid_info(C.Structure):
+    _fields_ = [("cpu_threads", C.c_int), ("cpu_vertices", C.c_uint32),
+                ("gpu_vertices", C.c_uint32), ("cpu_edges", C.c_int64),
+                ("gpu_edges", C.c_int64), ("ms_cpu_compute", C.c_double),
+                ("ms_gpu_compute", C.c_double), ("ms_exchange", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+GRAPH_HYBRID_MAX_THREADS = 1024
+
 # Every symbol include/graph.h declares, with (restype, argtypes).
 _vp, _u32, _i64, _int = C.c_void_p, C.c_uint32, C.c_int64, C.c_int
 SIGNATURES = {
@@ -133,6 +145,8 @@ SIGNATURES = {
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
     "pagerank_multi": (_int, [_vp, _u32, _vp, C.POINTER(pagerank_attr), _vp, _vp,
                               C.POINTER(graph_stats)]),
+    "pagerank_hybrid": (_int, [_vp, C.POINTER(pagerank_attr), _int, _vp, C.POINTER(graph_stats),
+                               C.POINTER(pagerank_hybrid_info)]),
     "bfs_csr_noalloc": (_int, [_u32, _i64, _vp, _vp, _u32, _vp, _vp, _vp]),
     "graph_server_create": (_int, [_vp, C.POINTER(graph_server_attr), C.POINTER(_vp)]),
     "graph_server_submit": (_int, [_vp, _int, _u32, _vp, C.POINTER(C.c_uint64)]),

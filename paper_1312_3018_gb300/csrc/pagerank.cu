@@ -38,6 +38,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -58,6 +60,9 @@ struct MultiWs {
   int dangling = -1;
 };
 
+struct HybWs;
+void free_hyb(struct PrWs* w);
+
 struct PrWs {
   int prec = -1;
   size_t esize = 0;  // bytes per stored contribution
@@ -66,8 +71,10 @@ struct PrWs {
   DevBuf slots, scal, resid;
   DevBuf items, hubsum;      // resolved work items and hub-chunk partial sums
   uint32_t items_n = 0;      // items resolved for the current partition (0: not yet)
+  int items_parts = 0;       // partitions (bit p) the resolved items cover
   int max_iter = 0;
   MultiWs* multi = nullptr;
+  HybWs* hyb = nullptr;      // host side of pagerank_hybrid
 };
 
 void free_multi(graph* g, PrWs* w) {
@@ -86,6 +93,7 @@ void free_pr(graph* g) {
   if (!g->pr) return;
   PrWs* w = g->pr;
   free_multi(g, w);
+  free_hyb(w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->r[p], &w->x[p][0], &w->x[p][1], &w->ghost[p]};
     for (DevBuf* b : all) dfree(g, *b);
@@ -114,7 +122,9 @@ struct PrSide {
 // Device scalars (doubles): [0] constant term of this iteration, (1-d)/n + d D/n;
 // [1] D; [2] last residual; [3] rank of degree-zero vertices before this iteration;
 // [4] the constant term rounded to FP32 (stored as a float in the first half).
-constexpr uint32_t kSlots = 1024;  // FP64 residual slots (block b adds to slot b % kSlots)
+constexpr uint32_t kSlots = 1024;  // FP64 residual slots (block b adds to slot b % kSlots);
+                                   // slot kSlots holds the residual of a partition that the
+                                   // host's cores update (pagerank_hybrid), else zero
 constexpr int kHubParts = kThreads / 32;  // partial sums per hub chunk (one per warp)
 
 struct PrItem;
@@ -124,7 +134,7 @@ struct PrArgs {
   const PrItem* items;  // [nitems] resolved work items
   void* hubsum;         // [nitems] partial sum of each hub-chunk item (accumulation type)
   double* scal;
-  double* slots;      // [kSlots] residual partial sums, zero between iterations
+  double* slots;      // [kSlots + 1] residual partial sums, zero between iterations
   double* resid;      // residual history
   double damping, n;
   float damping_f, n_f, d_over_n_f;
@@ -558,6 +568,8 @@ __global__ void __launch_bounds__(kThreads) k_pr_finalize(const __grid_constant_
   }
   a = block_sum<double>(a, rd);
   if (threadIdx.x == 0) {
+    a += A.slots[kSlots];
+    A.slots[kSlots] = 0.0;
     const double zr = A.scal[0];  // rank every degree-zero vertex now holds
     a += A.nzero * fabs(zr - A.scal[3]);
     const double D = dangling ? A.nzero * zr : 0.0;
@@ -622,7 +634,8 @@ __global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t nv0, uin
 // per thread); classes 1-3 take one thread per vertex.
 inline int leaf_gshift(int c) { return std::max(0, c - 3); }
 
-PrPlan make_plan(graph* g) {
+// Work items of the partitions in `parts` (bit p: partition p).
+PrPlan make_plan(graph* g, int parts = 3) {
   PrPlan pl;
   memset(&pl, 0, sizeof(pl));
   auto add = [&](uint32_t count_items, uint32_t first, uint32_t end, uint32_t per, int kind,
@@ -639,6 +652,7 @@ PrPlan make_plan(graph* g) {
     pl.nitems += count_items;
   };
   for (int p = 0; p < 2; ++p) {
+    if (!(parts & (1 << p))) continue;
     const Part& P = g->part[p];
     pl.hub_item0[p] = pl.nitems;
     add(P.nchunk, 0, P.nchunk, 1, kItemHub, p, 8);
@@ -691,7 +705,7 @@ graph_status alloc_ws(graph* g, int prec, int max_iter) {
     GG_TRY(dalloc(g, w->x[p][1], es * P.nv));
     GG_TRY(dalloc(g, w->ghost[p], es * P.nout));
   }
-  GG_TRY(dalloc(g, w->slots, sizeof(double) * kSlots));
+  GG_TRY(dalloc(g, w->slots, sizeof(double) * (kSlots + 1)));
   GG_TRY(dalloc(g, w->scal, 8 * sizeof(double)));
   GG_TRY(dalloc(g, w->resid, sizeof(double) * (size_t)(max_iter + 1)));
   return GRAPH_OK;
@@ -709,11 +723,12 @@ PrArgs make_args(graph* g, int cur, double damping);
 // Resolves the plan's work items once per workspace (the partition and the plan do not
 // change while the workspace lives).
 template <class PR>
-graph_status prepare_items(graph* g, PrWs* w, const PrPlan& pl) {
-  if (w->items_n == pl.nitems || pl.nitems == 0) return GRAPH_OK;
+graph_status prepare_items(graph* g, PrWs* w, const PrPlan& pl, int parts = 3) {
+  if ((w->items_n == pl.nitems && w->items_parts == parts) || pl.nitems == 0) return GRAPH_OK;
   dfree(g, w->items);
   dfree(g, w->hubsum);
   w->items_n = 0;
+  w->items_parts = parts;
   GG_TRY(dalloc(g, w->items, sizeof(PrItem) * (size_t)pl.nitems));
   GG_TRY(dalloc(g, w->hubsum, sizeof(typename PR::AT) * kHubParts * (size_t)pl.nitems));
   k_pr_items<<<grid_for(pl.nitems, 256), 256, 0, g->stream>>>(pl, make_args(g, 0, 0.85),
@@ -766,7 +781,7 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   timer.mark(2);
   const uint32_t nv0 = g->part[0].nv;
   int cur = 0;
-  GG_CUDA(cudaMemsetAsync(w->slots.p, 0, sizeof(double) * kSlots, st));
+  GG_CUDA(cudaMemsetAsync(w->slots.p, 0, sizeof(double) * (kSlots + 1), st));
   {
     PrArgs A = make_args(g, cur, at.damping);
     k_pr_init<PR, false><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, MultiArgs{});
@@ -1077,6 +1092,367 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// pagerank_hybrid: the paper's hybrid placement (Section 4.1, Figure 6; Section 6.2, HIGH).
+// Partition 0 (the high-degree vertices) is updated by host threads from host copies of
+// its arrays while the GPU updates partition 1 with the kernels above. Every superstep
+// moves only the message arrays across the host/device boundary (Section 4.3.2):
+// partition 0's ghost slots come down from the device, partition 1's go up.
+// ---------------------------------------------------------------------------------------
+struct HybWs {
+  std::vector<int64_t> off0;      // partition 0: offsets and edge ids (host copies)
+  std::vector<uint32_t> E0;
+  std::vector<uint32_t> outbox1;  // partition 1's outbox: partition-0 local ids it pulls
+  std::vector<uint32_t> cut;      // host threads' vertex ranges, balanced by edge count
+  size_t vsize = 0;               // bytes of one rank / contribution
+  std::vector<unsigned char> r0, x0[2];
+  void* ghost0 = nullptr;         // pinned [nout0]: partition 0's ghost slots
+  void* ghost1 = nullptr;         // pinned [nout1]: partition 1's ghost slots
+  double* io = nullptr;           // pinned [2]: host residual out, device residual in
+  cudaEvent_t ev[5] = {};         // ghost0 landed, compute start / end, exchange start / end
+};
+
+void free_hyb(PrWs* w) {
+  HybWs* h = w->hyb;
+  if (!h) return;
+  if (h->ghost0) cudaFreeHost(h->ghost0);
+  if (h->ghost1) cudaFreeHost(h->ghost1);
+  if (h->io) cudaFreeHost(h->io);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+  w->hyb = nullptr;
+}
+
+namespace {
+
+// Runs f(k, begin, end) on nt host threads over [0, n) split evenly, or over the ranges
+// [cut[k], cut[k+1]) when cut is given. A thread that cannot be started runs its range on
+// the calling thread, so no exception leaves while other threads are running.
+template <class F>
+void host_parallel(int nt, uint32_t n, const std::vector<uint32_t>* cut, F&& f) {
+  if (n == 0 || nt < 1) return;
+  auto lo = [&](int k) {
+    return cut ? (*cut)[k] : (uint32_t)((uint64_t)n * (uint64_t)k / (uint64_t)nt);
+  };
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int k = 1; k < nt; ++k) {
+    try {
+      th.emplace_back(f, k, lo(k), lo(k + 1));
+    } catch (...) {
+      f(k, lo(k), lo(k + 1));
+    }
+  }
+  f(0, lo(0), lo(1));
+  for (auto& t : th) t.join();
+}
+
+// Host copies of partition 0's CSR and of partition 1's outbox (once per partition), the
+// per-precision host arrays and pinned message buffers, and the threads' vertex ranges.
+template <class T>
+graph_status ensure_hyb(graph* g, PrWs* w, int nt) {
+  const Part& P0 = g->part[0];
+  const Part& P1 = g->part[1];
+  cudaStream_t st = g->stream;
+  if (!w->hyb) {
+    HybWs* h = new HybWs();
+    w->hyb = h;
+    h->off0.resize((size_t)P0.nv + 1);
+    h->E0.resize((size_t)P0.ne);
+    h->outbox1.resize(P1.nout);
+    GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1),
+                            cudaMemcpyDeviceToHost, st));
+    if (P0.ne)
+      GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+    if (P1.nout)
+      GG_CUDA(cudaMemcpyAsync(h->outbox1.data(), P1.outbox.p, 4ull * P1.nout,
+                              cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    for (cudaEvent_t& e : h->ev) GG_CUDA(cudaEventCreate(&e));
+    if (cudaHostAlloc((void**)&h->io, 2 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+      h->io = nullptr;
+      set_error("pinned host allocation failed");
+      return GRAPH_ENOMEM;
+    }
+  }
+  HybWs* h = w->hyb;
+  if (h->vsize != sizeof(T)) {
+    if (h->ghost0) cudaFreeHost(h->ghost0);
+    if (h->ghost1) cudaFreeHost(h->ghost1);
+    h->ghost0 = h->ghost1 = nullptr;
+    h->vsize = 0;
+    const size_t b0 = sizeof(T) * std::max<size_t>(1, P0.nout);
+    const size_t b1 = sizeof(T) * std::max<size_t>(1, P1.nout);
+    if (cudaHostAlloc(&h->ghost0, b0, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(&h->ghost1, b1, cudaHostAllocDefault) != cudaSuccess) {
+      set_error("pinned host allocation of the message arrays failed");
+      return GRAPH_ENOMEM;
+    }
+    h->r0.assign(sizeof(T) * (size_t)P0.nv, 0);
+    for (auto& x : h->x0) x.assign(sizeof(T) * (size_t)P0.nv, 0);
+    h->vsize = sizeof(T);
+  }
+  if ((int)h->cut.size() != nt + 1) {
+    // Thread k takes the vertices whose first edge lies in [k ne / nt, (k+1) ne / nt).
+    h->cut.assign(nt + 1, P0.nv);
+    h->cut[0] = 0;
+    for (int k = 1; k < nt; ++k) {
+      const int64_t e = P0.ne * (int64_t)k / nt;
+      h->cut[k] = (uint32_t)(std::lower_bound(h->off0.begin(), h->off0.begin() + P0.nv, e) -
+                             h->off0.begin());
+    }
+    for (int k = 1; k <= nt; ++k) h->cut[k] = std::max(h->cut[k], h->cut[k - 1]);
+  }
+  return GRAPH_OK;
+}
+
+// One superstep of partition 0 on the host: the vertex update of update_vertex in the
+// same precision (T = float: FP32 constant term, damping and sums; T = double: FP64).
+// The neighbour sum is pairwise over blocks of kHostBlock edges in CSR order: a block is
+// summed as four interleaved partial sums (four independent chains of loads), and the
+// block sums are merged like a binary counter, so a hub with many edges sees a rounding
+// chain of about log2(blocks) additions, not one per edge. (A sequential FP32 sum over
+// 20,000 edges is off by ~1e-6 relative in each iteration, as the GPU's chunked tree is
+// not.) Degree-zero vertices take the constant term (their residual is the closed form
+// k_pr_finalize adds). Returns sum |r' - r| over the vertices with edges.
+constexpr int kHostBlock = 32;
+
+template <class T>
+double host_update(const HybWs& h, uint32_t v0, uint32_t v1, const T* x, const T* ghost,
+                   T* r, T* xn, T base, T d) {
+  auto val = [&](uint32_t id) { return (id & kRemote) ? ghost[id & kIdMask] : x[id]; };
+  const uint32_t* E = h.E0.data();
+  auto chunk_sum = [&](int64_t e, int64_t e1) {
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (; e + 4 <= e1; e += 4) {
+      s0 += val(E[e]);
+      s1 += val(E[e + 1]);
+      s2 += val(E[e + 2]);
+      s3 += val(E[e + 3]);
+    }
+    if (e < e1) s0 += val(E[e]);
+    if (e + 1 < e1) s1 += val(E[e + 1]);
+    if (e + 2 < e1) s2 += val(E[e + 2]);
+    return (s0 + s1) + (s2 + s3);
+  };
+  double res = 0;
+  for (uint32_t v = v0; v < v1; ++v) {
+    const int64_t e0 = h.off0[v], e1 = h.off0[v + 1];
+    if (e0 == e1) {
+      r[v] = base;
+      xn[v] = (T)0;
+      continue;
+    }
+    T sum;
+    if (e1 - e0 <= kHostBlock) {
+      sum = chunk_sum(e0, e1);
+    } else {
+      T level[48];  // level[k]: sum of 2^k consecutive blocks still waiting for a partner
+      uint64_t nb = 0;
+      for (int64_t b = e0; b < e1; b += kHostBlock) {
+        T t = chunk_sum(b, std::min(b + kHostBlock, e1));
+        int k = 0;
+        for (uint64_t c = nb; c & 1; c >>= 1, ++k) t = level[k] + t;
+        level[k] = t;
+        ++nb;
+      }
+      sum = 0;
+      for (int k = 0; (nb >> k) != 0; ++k)
+        if ((nb >> k) & 1) sum = level[k] + sum;
+    }
+    const T rn = base + d * sum;
+    const T ro = r[v];
+    r[v] = rn;
+    xn[v] = rn / (T)(e1 - e0);
+    res += (double)(rn > ro ? rn - ro : ro - rn);
+  }
+  return res;
+}
+
+template <class PR>
+graph_status run_hybrid(graph* g, const pagerank_attr& at, int nt, double* ranks,
+                        graph_stats* stats, pagerank_hybrid_info* info) {
+  using T = typename PR::AT;
+  using Clock = std::chrono::steady_clock;
+  auto ms_since = [](Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  const auto t_start = Clock::now();
+  cudaStream_t st = g->stream;
+  const PrPlan pl = make_plan(g, 2);  // the GPU's share: partition 1
+  GG_TRY((prepare_kernel<PR, false>()));
+  GG_TRY(ensure_ws(g, at.precision, at.max_iter));
+  PrWs* w = g->pr;
+  GG_TRY(prepare_items<PR>(g, w, pl, 2));
+  {
+    graph_status s = GRAPH_OK;
+    try {
+      s = ensure_hyb<T>(g, w, nt);
+    } catch (const std::bad_alloc&) {
+      set_error("host allocation for the host partition failed");
+      s = GRAPH_ENOMEM;
+    }
+    if (s != GRAPH_OK) {
+      free_hyb(w);
+      return s;
+    }
+  }
+  HybWs* h = w->hyb;
+  const uint32_t nv0 = g->part[0].nv, nout0 = g->part[0].nout, nout1 = g->part[1].nout;
+  const uint32_t nhubs1 = g->part[1].nhub;
+  const size_t vs = sizeof(T), smem = smem_bytes<PR>();
+  const double n = (double)g->n, d = at.damping;
+  int cur = 0;
+  int64_t launches = 1;
+  GG_CUDA(cudaMemsetAsync(w->slots.p, 0, sizeof(double) * (kSlots + 1), st));
+  PrArgs A = make_args(g, cur, at.damping);
+  k_pr_init<PR, false><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, MultiArgs{});
+  GG_CUDA(cudaGetLastError());
+  // The constant term follows the scalar recurrence k_pr_finalize evaluates (D_0 =
+  // nzero / n; after an iteration with constant c, D = nzero c), so the host keeps its own
+  // bit-identical copy instead of reading it back.
+  double D = at.dangling ? A.nzero / n : 0.0;
+  double base = (1.0 - d) / n + d * D / n;
+  {
+    double hs[5] = {base, D, 0.0, 1.0 / n, 0.0};
+    const float bf = (float)base;
+    memcpy(&hs[4], &bf, sizeof(float));
+    GG_CUDA(cudaMemcpyAsync(w->scal.p, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  }
+  T* r0 = (T*)h->r0.data();
+  {
+    const T rinit = (T)(1.0 / n);
+    T* x = (T*)h->x0[cur].data();
+    host_parallel(nt, nv0, nullptr, [&](int, uint32_t a, uint32_t b) {
+      for (uint32_t v = a; v < b; ++v) {
+        const int64_t deg = h->off0[v + 1] - h->off0[v];
+        r0[v] = rinit;
+        x[v] = deg > 0 ? rinit / (T)deg : (T)0;
+      }
+    });
+  }
+  GG_CUDA(cudaStreamSynchronize(st));
+  double ms_cpu = 0, ms_gpu = 0, ms_xchg = 0, ms_comp = 0, last_res = 0;
+  std::vector<double> part(nt);
+  int it = 0;
+  while (it < at.max_iter) {
+    A = make_args(g, cur, at.damping);
+    A.side[0].P.bstart[1] = 0;   // partition 0's hubs are updated on the host
+    PrArgs Apub = A;
+    Apub.side[1].P.nout = 0;     // the device fills only partition 0's ghost slots
+    const T* xh = (const T*)h->x0[cur].data();
+    T* xhn = (T*)h->x0[1 - cur].data();
+    // Communication phase: partition 0's ghost slots down, partition 1's up.
+    GG_CUDA(cudaEventRecord(h->ev[3], st));
+    if (nout0) {
+      k_pr_publish<T><<<grid_for(nout0, 256), 256, 0, st>>>(Apub);
+      GG_CUDA(cudaMemcpyAsync(h->ghost0, w->ghost[0].p, vs * nout0, cudaMemcpyDeviceToHost,
+                              st));
+      ++launches;
+    }
+    GG_CUDA(cudaEventRecord(h->ev[0], st));
+    if (nout1) {
+      T* g1 = (T*)h->ghost1;
+      host_parallel(nt, nout1, nullptr, [&](int, uint32_t a, uint32_t b) {
+        for (uint32_t j = a; j < b; ++j) g1[j] = xh[h->outbox1[j]];
+      });
+      GG_CUDA(cudaMemcpyAsync(w->ghost[1].p, g1, vs * nout1, cudaMemcpyHostToDevice, st));
+    }
+    GG_CUDA(cudaEventRecord(h->ev[4], st));
+    // Compute phase: the GPU's partition is queued, then the host updates its own.
+    GG_CUDA(cudaEventRecord(h->ev[1], st));
+    if (pl.nitems) {
+      k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
+                                                                 MultiArgs{});
+      ++launches;
+      if (nhubs1) {
+        k_pr_hubs<PR, false><<<grid_for(nhubs1, kThreads / 32), kThreads, 0, st>>>(
+            pl, A, it, MultiArgs{});
+        ++launches;
+      }
+    }
+    GG_CUDA(cudaEventRecord(h->ev[2], st));
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaEventSynchronize(h->ev[0]));
+    const auto tc0 = Clock::now();
+    const T* g0 = (const T*)h->ghost0;
+    const T bT = (T)base, dT = (T)d;
+    host_parallel(nt, nv0, &h->cut, [&](int k, uint32_t a, uint32_t b) {
+      part[k] = host_update<T>(*h, a, b, xh, g0, r0, xhn, bT, dT);
+    });
+    double cres = 0;
+    for (int k = 0; k < nt; ++k) cres += part[k];
+    const auto tc1 = Clock::now();
+    h->io[0] = cres;
+    GG_CUDA(cudaMemcpyAsync((double*)w->slots.p + kSlots, h->io, sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+    k_pr_finalize<<<1, kThreads, 0, st>>>(A, it, at.dangling);
+    ++launches;
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaMemcpyAsync(h->io + 1, (double*)w->scal.p + 2, sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    last_res = h->io[1];
+    float gms = 0, xms = 0;
+    GG_CUDA(cudaEventElapsedTime(&gms, h->ev[1], h->ev[2]));
+    GG_CUDA(cudaEventElapsedTime(&xms, h->ev[3], h->ev[4]));
+    const double cms = ms_since(tc0, tc1);
+    ms_cpu += cms;
+    ms_gpu += gms;
+    ms_xchg += xms;
+    ms_comp += std::max(cms, (double)gms);
+    D = at.dangling ? A.nzero * base : 0.0;
+    base = (1.0 - d) / n + d * D / n;
+    cur = 1 - cur;
+    ++it;
+    if (at.tol > 0 && last_res < at.tol) break;
+  }
+  // Collect: the host partition's ranks join the device's, then the usual local -> global
+  // write.
+  if (nv0)
+    GG_CUDA(cudaMemcpyAsync(w->r[0].p, r0, vs * nv0, cudaMemcpyHostToDevice, st));
+  double* out = ranks;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 8ull * g->n));
+    out = (double*)g->stage.p;
+  }
+  A = make_args(g, cur, at.damping);
+  k_pr_collect<T><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, out);
+  GG_CUDA(cudaGetLastError());
+  launches++;
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = it;
+    stats->edges_traversed = g->m * (int64_t)it;
+    stats->edges_inspected = g->m * (int64_t)it;
+    stats->messages = (int64_t)(nout0 + nout1) * it;
+    stats->residual = last_res;
+    stats->launches = launches;
+    if (at.timing) {
+      stats->ms_total = ms_since(t_start, Clock::now());
+      stats->ms_compute = ms_comp;
+      stats->ms_exchange = ms_xchg;
+    }
+  }
+  if (info) {
+    info->cpu_threads = nt;
+    info->cpu_vertices = nv0;
+    info->gpu_vertices = g->part[1].nv;
+    info->cpu_edges = g->part[0].ne;
+    info->gpu_edges = g->part[1].ne;
+    info->ms_cpu_compute = ms_cpu;
+    info->ms_gpu_compute = ms_gpu;
+    info->ms_exchange = ms_xchg;
+  }
+  return s;
+}
+
+}  // namespace
 }  // namespace gg
 
 using namespace gg;
@@ -1104,6 +1480,36 @@ extern "C" graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* 
     case GRAPH_PR_FP16: return run<PrecF16>(g, at, ranks, stats);
     default:
       set_error("bad precision %d", at.precision);
+      return GRAPH_EINVAL;
+  }
+}
+
+extern "C" graph_status pagerank_hybrid(graph_t* g, const pagerank_attr* attr, int cpu_threads,
+                                        double* ranks, graph_stats* stats,
+                                        pagerank_hybrid_info* info) {
+  if (!g || !attr || !ranks) {
+    set_error("graph, attr or ranks is NULL");
+    return GRAPH_EINVAL;
+  }
+  const pagerank_attr at = *attr;
+  if (!(at.damping >= 0.0 && at.damping <= 1.0) || at.max_iter < 1 ||
+      (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) ||
+      (at.dangling != 0 && at.dangling != 1) || cpu_threads > GRAPH_HYBRID_MAX_THREADS) {
+    set_error("bad pagerank_hybrid attributes");
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before pagerank_hybrid");
+    return GRAPH_ESTATE;
+  }
+  int nt = cpu_threads;
+  if (nt <= 0) nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()),
+                                            (unsigned)GRAPH_HYBRID_MAX_THREADS);
+  switch (at.precision) {
+    case GRAPH_PR_FP32: return run_hybrid<PrecF32>(g, at, nt, ranks, stats, info);
+    case GRAPH_PR_FP64: return run_hybrid<PrecF64>(g, at, nt, ranks, stats, info);
+    default:
+      set_error("pagerank_hybrid runs FP32 or FP64 (precision %d)", at.precision);
       return GRAPH_EINVAL;
   }
 }
