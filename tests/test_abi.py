@@ -93,6 +93,8 @@ def test_algorithms_reject_null_handles(lib):
                          None) == _lib.GRAPH_EINVAL
     attr = _lib.pagerank_attr(0.85, 10, 0.0, 0, 1, 0, 0)
     assert lib.pagerank(None, ctypes.byref(attr), None, None) == _lib.GRAPH_EINVAL
+    assert lib.pagerank_hybrid(None, ctypes.byref(attr), 1, None, None,
+                               None) == _lib.GRAPH_EINVAL
     assert lib.graph_partition(None, None) == _lib.GRAPH_EINVAL
     lib.graph_free(None)
 
@@ -101,7 +103,7 @@ def test_binding_constants_match_the_header():
     from paper_1312_3018_gb300 import _lib
     src = open(HEADER).read()
     for name in ("GRAPH_BATCH_MAX", "GRAPH_NOALLOC_MAX_VERTICES", "GRAPH_INF", "GRAPH_MEM_HOST",
-                 "GRAPH_MEM_DEVICE"):
+                 "GRAPH_MEM_DEVICE", "GRAPH_HYBRID_MAX_THREADS"):
         m = re.search(r"#define\s+%s\s+\(?([0-9xXa-fA-F]+)u?(?:\s*<<\s*(\d+))?" % name, src)
         assert m, name
         val = int(m.group(1), 0) << (int(m.group(2)) if m.group(2) else 0)
