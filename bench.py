@@ -382,7 +382,7 @@ def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5):
             "cpu_vertices": h["cpu_vertices"], "cpu_edges": h["cpu_edges"],
             "cpu_edge_share": round(h["cpu_edges"] / m, 4),
             "hybrid_ms_per_iter": round(hms, 3),
-            "hybrid_gedges_per_s_iter": round(m / (hms / 1e3) / 1e9, 2),
+            "hybrid_gedges_per_s_iter": round(m / (max(hms, 1e-6) / 1e3) / 1e9, 2),
             "gpu_only_ms_per_iter": round(gms, 3),
             "cpu_compute_ms_per_iter": round(h["ms_cpu_compute"] / iters, 3),
             "gpu_compute_ms_per_iter": round(h["ms_gpu_compute"] / iters, 3),

@@ -58,3 +58,105 @@ def test_gpu_arm_fails_loudly_without_gpu():
     r = run_bench(SMALL + ["--no-serve", "--no-batch", "--no-cpu-baseline"])
     assert r.returncode != 0
     assert json_lines(r.stdout) == []
+
+
+def _bench_module():
+    import importlib
+    import sys
+    sys.path.insert(0, ROOT)
+    return importlib.import_module("bench")
+
+
+def test_cpu_baseline_leg_returns_the_oracle_ranks_for_the_precision_report():
+    """The oracle runs only in the CPU-baseline leg: that leg returns the FP64 ranks after
+    its PageRank iterations, and the precision report compares against exactly those."""
+    import numpy as np
+    import oracle
+    import synth
+    bench = _bench_module()
+    g = synth.rmat(10, seed=1)
+    synth.weights(g, 255, seed=3)
+    cpu, ranks = bench.cpu_baseline(g, int(synth.sources(g, 1, seed=2)[0]), 25.0, pr_iters=3)
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] > 0
+    assert "3 FP64 PageRank iterations" in cpu["sample"]
+    ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=3)
+    assert np.array_equal(ranks, ref)
+
+    class FakeLib:
+        """Stands in for the GPU library: returns the oracle's ranks rounded to the
+        requested precision, so the report's arithmetic can be checked on the host."""
+        def pagerank(self, H, max_iter, precision, out):
+            r, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=max_iter)
+            dt = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16}[precision]
+            return r.astype(dt).astype(np.float64), {}
+
+    rep = bench.precision_report(FakeLib(), None, g, ranks, iters_oracle=3, iters_step=5)
+    assert list(rep) == ["vs_oracle", "vs_gpu_fp64", "target"]
+    assert rep["vs_oracle"]["fp64"]["l1"] == 0.0
+    l1_32 = float(np.abs(ref.astype(np.float32).astype(np.float64) - ref).sum())
+    assert rep["vs_oracle"]["fp32"]["l1"] == l1_32
+    assert rep["vs_oracle"]["fp16"]["l1"] > rep["vs_oracle"]["fp32"]["l1"]
+    rep = bench.precision_report(FakeLib(), None, g, None, iters_step=5)
+    assert "vs_oracle" not in rep and rep["vs_gpu_fp64"]["iterations"] == 5
+
+
+def test_hybrid_report_fields():
+    """The hybrid object: one point per host edge share, with the per-processor times of
+    the library's info turned into per-iteration figures."""
+    bench = _bench_module()
+
+    class FakeTensor:
+        def __init__(self, v):
+            self.v = v
+
+        def __sub__(self, o):
+            return FakeTensor(self.v - o.v)
+
+        def abs(self):
+            return FakeTensor(abs(self.v))
+
+        def sum(self):
+            return self.v
+
+        def __float__(self):
+            return float(self.v)
+
+    class FakeTorch:
+        float64 = "f64"
+
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+        @staticmethod
+        def empty(n, dtype, device):
+            return FakeTensor(0.0)
+
+    class FakeLib:
+        def graph_partition(self, H, strategy, edge_share):
+            return {"threshold": int(1000 * (1 - edge_share))}
+
+        def pagerank(self, H, max_iter, precision, ranks, out):
+            ranks.v = 1.0
+            return ranks, {}
+
+        def pagerank_hybrid(self, H, max_iter, precision, ranks, out, timing=False):
+            ranks.v = 1.0 + 1e-9
+            info = {"cpu_vertices": 10, "cpu_edges": 250, "ms_cpu_compute": 5.0 * max_iter,
+                    "ms_gpu_compute": 1.0 * max_iter, "ms_exchange": 0.5 * max_iter}
+            return ranks, {"hybrid": info, "messages": 70 * max_iter, "supersteps": max_iter}
+
+    class FakeGraph:
+        n = 100
+
+    rep = bench.hybrid_report(FakeLib(), FakeGraph(), 1000, FakeTorch, shares=(0.05, 0.25),
+                              iters=5)
+    assert rep["iters"] == 5 and len(rep["points"]) == 2
+    p = rep["points"][1]
+    assert p["edge_share"] == 0.25 and p["T"] == 750
+    assert p["cpu_edge_share"] == 0.25
+    assert p["cpu_compute_ms_per_iter"] == 5.0 and p["gpu_compute_ms_per_iter"] == 1.0
+    assert p["exchange_ms_per_iter"] == 0.5 and p["messages_per_iter"] == 70
+    assert abs(p["l1_vs_gpu_only"] - 1e-9) < 1e-15
+    assert p["hybrid_ms_per_iter"] >= 0 and p["gpu_only_ms_per_iter"] >= 0
