@@ -495,7 +495,8 @@ graph_status graph_server_destroy(graph_server_t* s);
  * or could deadlock, allocators frozen after start-up, services with a fixed device-memory
  * budget). It allocates nothing: no cudaMalloc, cudaFree or allocating library call. Its
  * scratch (visited bitmap, two frontier queues, counters) lives in one fixed device array
- * of about 16.3 MB that every GPU loading this library holds until the process exits.
+ * of (2^21/32 + 2 * 2^21 + 64) * 4 = 17,039,616 bytes (17.0 MB, 16.25 MiB) that every GPU
+ * loading this library holds until the process exits.
  *   n        number of vertices, 1 <= n <= GRAPH_NOALLOC_MAX_VERTICES (larger n: EINVAL)
  *   m        number of edge entries
  *   offsets  DEVICE int64[n+1], cols DEVICE uint32[m]: the caller's CSR, read in place
@@ -503,8 +504,9 @@ graph_status graph_server_destroy(graph_server_t* s);
  *   source   start vertex (< n)
  *   levels   DEVICE uint32[n]: hop distance, GRAPH_INF if unreached (required)
  *   parents  DEVICE uint32[n]: a BFS tree (parents[source] = source), or NULL
- *   stream   cudaStream_t for all work (NULL = legacy default stream); the call returns
- *            after the results are complete
+ *   stream   cudaStream_t for all work (NULL = legacy default stream); the call blocks:
+ *            it synchronises the stream with the host after the CSR check and after every
+ *            level, and returns after the results are complete
  * Search is level-synchronous and top-down on the unpartitioned graph; levels equal those
  * of bfs(). The first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current, so make the first call before any

@@ -430,22 +430,52 @@ def bfs_csr_noalloc(offsets, cols, source: int, levels=None, parents=None, *, st
                     want_parents: bool = True):
     """Allocation-free BFS on a CSR already in device memory (torch CUDA tensors: int64
     offsets[n+1], 32-bit cols[m]). For callers that cannot allocate device memory when they
-    search: the library keeps its scratch in one fixed device array of about 16.3 MB and
-    allocates nothing; pass preallocated `levels`/`parents` (int32 CUDA tensors of length n)
-    to keep this wrapper allocation-free as well. n is limited to 2^21 vertices. Calls share
-    the scratch array and must not overlap on the GPU; the first call on a device should come
-    before any stream capture."""
+    search: the library keeps its scratch in one fixed device array of 17.0 MB (16.25 MiB)
+    and allocates nothing; pass preallocated `levels`/`parents` (32-bit CUDA tensors of
+    length n) to keep this wrapper allocation-free as well. n is limited to 2^21 vertices.
+    Calls share the scratch array and must not overlap on the GPU; the first call on a
+    device should come before any stream capture. The call waits for the device after the
+    CSR check and after every level, so it returns with the search complete.
+
+    Raises ValueError before any device work unless offsets is a contiguous int64 tensor,
+    cols, levels and parents contiguous 32-bit integer tensors of the right lengths, and all
+    of them on one CUDA device; the call then runs with that device current."""
     torch = _torch()
+    i32 = (torch.int32, getattr(torch, "uint32", torch.int32))
+
+    def need(t, name, dtypes, length):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor (got {t.device})")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} has dtype {t.dtype}; expected one of {dtypes}")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D tensor")
+        if length is not None and t.numel() != length:
+            raise ValueError(f"{name} has {t.numel()} elements; expected {length}")
+        if t.device != offsets.device:
+            raise ValueError(f"{name} is on {t.device}, offsets on {offsets.device}")
+
+    need(offsets, "offsets", (torch.int64,), None)
     n = offsets.numel() - 1
+    if n < 1:
+        raise ValueError("offsets must hold n + 1 >= 2 entries")
+    need(cols, "cols", i32, None)
     m = cols.numel()
-    if levels is None:
-        levels = torch.empty(n, dtype=torch.int32, device=offsets.device)
-    if want_parents and parents is None:
-        parents = torch.empty(n, dtype=torch.int32, device=offsets.device)
-    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
-    st = _lib.load().bfs_csr_noalloc(n, m, offsets.data_ptr(), cols.data_ptr(), int(source),
-                                     levels.data_ptr(),
-                                     parents.data_ptr() if want_parents else None, s)
+    with torch.cuda.device(offsets.device):
+        if levels is None:
+            levels = torch.empty(n, dtype=torch.int32, device=offsets.device)
+        if want_parents and parents is None:
+            parents = torch.empty(n, dtype=torch.int32, device=offsets.device)
+        need(levels, "levels", i32, n)
+        if want_parents:
+            need(parents, "parents", i32, n)
+        s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+        st = _lib.load().bfs_csr_noalloc(n, m, offsets.data_ptr(),
+                                         cols.data_ptr() if m > 0 else None, int(source),
+                                         levels.data_ptr(),
+                                         parents.data_ptr() if want_parents else None, s)
     _lib.check(st, "bfs_csr_noalloc")
     return levels, (parents if want_parents else None)
 

@@ -10,12 +10,14 @@
 // library routine.
 //
 // The scratch array is a file-scope __device__ array: every GPU that loads this library
-// holds it (about 16.3 MB) until the process exits. Host code cannot use the array's name as
-// a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current and caches it; that first call should
-// therefore come before any stream capture. All calls share the one array, which keeps the
-// last call's contents: each call clears what must start at zero, and calls that overlap on
-// the GPU (two streams, two threads) race on it.
+// holds it ((2^21/32 + 2 * 2^21 + 64) words = 17,039,616 bytes: 17.0 MB, 16.25 MiB) until
+// the process exits. Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress while that
+// device is current and caches it; that first call should therefore come before any stream
+// capture. All calls share the one array, which keeps the last call's contents: each call
+// clears what must start at zero, and calls that overlap on the GPU (two streams, two
+// threads) race on it. The call blocks the host: it synchronises its stream after the CSR
+// check and after every level (the level loop reads the next frontier's size).
 #include <mutex>
 
 #include "common.cuh"

@@ -1,15 +1,19 @@
-"""Parity at the full workload sizes, in the launch configuration the benchmark times
-(degree split at T = 2048, RMAT with the Table 2 parameters, weights uniform in [1, 255]).
+"""Parity at the full workload sizes (RMAT with the Table 2 parameters, weights uniform in
+[1, 255]), at the degree split the benchmark times and at T = 2048.
 
-RMAT scale 22 (4.19M vertices, ~128M edge entries): BFS levels and SSSP distances compared
-with the oracle element by element for sampled sources, PageRank to an L1 residual below
-1e-9 (the oracle's iteration count K*) in FP32 / FP16 against FP64.
+The benchmark's threshold is read through the same autotuner call and threshold cache the
+benchmark uses (bench_threshold below), so the two cannot drift apart.
 
-RMAT scale 25 (33.5M vertices, ~1.05B edge entries): BFS levels against the oracle for one
-source and its parents validated; SSSP distances checked with the optimality certificate
-(every edge satisfies dist[v] <= dist[u] + w and every reached vertex has a tight
-predecessor, which fixes the distances exactly), and the near-far order equal to them;
-PageRank after 3 iterations against the FP64 oracle.
+RMAT scale 22 (4.19M vertices, ~128M edge entries, T = 2048): BFS levels and SSSP distances
+compared with the oracle element by element for sampled sources, PageRank to an L1 residual
+below 1e-9 (the oracle's iteration count K*) in FP32 / FP16 against FP64.
+
+RMAT scale 25 (33.5M vertices, ~1.05B edge entries), at the benchmark's threshold and at
+T = 2048: BFS levels against the oracle element by element and parents validated; SSSP
+distances against the oracle's Dijkstra element by element and through the optimality
+certificate (every edge satisfies dist[v] <= dist[u] + w and every reached vertex has a
+tight predecessor), in plain rounds and in the benchmark's near-far order; FP32 PageRank
+after 3 iterations against the FP64 oracle (L1 and per-vertex bounds), FP16 by L1.
 """
 import numpy as np
 import pytest
@@ -21,6 +25,18 @@ pytestmark = pytest.mark.gpu
 INF = oracle.INF
 T = 2048
 NEAR_FAR_DELTA = 128
+BENCH_DELTA = 64        # near-far width of the benchmark step's SSSP
+
+
+def bench_threshold(G, H, g):
+    """The degree threshold the benchmark runs at: the autotuner called exactly as bench.py
+    calls it (same source, same cache file, no retuning). Leaves H partitioned at it."""
+    import os
+    from paper_1312_3018_gb300 import autotune
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = os.path.join(root, "paper_1312_3018_gb300", "tuned_thresholds.json")
+    src = int(synth.sources(g, 64, seed=2)[0])
+    return int(autotune.autotune_threshold(G, H, src, weighted=True, cache=cache)["T"])
 
 
 @pytest.fixture(scope="module")
@@ -47,10 +63,16 @@ def loaded22(gpu, rmat22):
 
 @pytest.fixture(scope="module")
 def loaded25(gpu, rmat25):
+    """The RMAT-25 handle and the thresholds to check: the benchmark's and 2048."""
     H = gpu.graph_load_csr(rmat25.offsets, rmat25.cols, rmat25.weights)
-    gpu.graph_partition(H, "degree", degree_threshold=T)
-    yield H
+    tb = bench_threshold(gpu, H, rmat25)
+    yield H, sorted({tb, T})
     H.free()
+
+
+@pytest.fixture(scope="module")
+def source25(rmat25):
+    return int(synth.sources(rmat25, 1, seed=2)[0])
 
 
 def test_rmat22_bfs_sixty_four_sources(gpu, rmat22, loaded22):
@@ -109,33 +131,56 @@ def test_rmat22_pagerank_to_residual_1e9(gpu, rmat22, loaded22):
     assert np.abs(r16 - ref).sum() <= 1e-3
 
 
-def test_rmat25_bfs(gpu, rmat25, loaded25):
-    g = rmat25
-    s = int(synth.sources(g, 1, seed=2)[0])
-    lv, pa, st = gpu.bfs(loaded25, s, out="host")
+def test_rmat25_bfs(gpu, rmat25, loaded25, source25):
+    g, s = rmat25, source25
+    H, thresholds = loaded25
     ref, _ = oracle.bfs(g.n, g.offsets, g.cols, s, want_parents=False)
-    assert np.array_equal(lv, ref)
-    assert oracle.check_bfs(g.n, g.offsets, g.cols, s, lv, pa) == 0
-    assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, ref)
+    trav = oracle.traversed(g.n, g.offsets, ref)
+    for t in thresholds:
+        gpu.graph_partition(H, "degree", degree_threshold=t)
+        lv, pa, st = gpu.bfs(H, s, out="host")
+        assert np.array_equal(lv, ref), f"T={t}"
+        assert oracle.check_bfs(g.n, g.offsets, g.cols, s, lv, pa) == 0, f"T={t}"
+        assert st["edges_traversed"] == trav
 
 
-def test_rmat25_sssp_certificate(gpu, rmat25, loaded25):
-    g = rmat25
-    s = int(synth.sources(g, 1, seed=2)[0])
-    d, st = gpu.sssp(loaded25, s, out="host")
-    assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d) == 0
-    assert st["edges_traversed"] == oracle.traversed(g.n, g.offsets, d)
-    d2, _ = gpu.sssp(loaded25, s, out="host", delta=NEAR_FAR_DELTA)
-    assert np.array_equal(d2, d)
+def test_rmat25_sssp(gpu, rmat25, loaded25, source25):
+    g, s = rmat25, source25
+    H, thresholds = loaded25
+    ref = oracle.sssp(g.n, g.offsets, g.cols, g.weights, s)
+    trav = oracle.traversed(g.n, g.offsets, ref)
+    for t in thresholds:
+        gpu.graph_partition(H, "degree", degree_threshold=t)
+        for delta in (0, BENCH_DELTA):   # Figure 20's plain rounds, the benchmark's order
+            d, st = gpu.sssp(H, s, out="host", delta=delta)
+            assert np.array_equal(d, ref), f"T={t} delta={delta}"
+            assert st["edges_traversed"] == trav
+        assert oracle.check_sssp(g.n, g.offsets, g.cols, g.weights, s, d) == 0
+
+
+# Per-vertex bounds of FP32 PageRank after 3 iterations against FP64. Every rank is at
+# least (1-d)/n, a neighbour sum of k positive FP32 terms added in any order is within
+# (k-1) ulp-relative error of the exact sum, and the deepest sum here (a hub's partials)
+# has a few thousand terms, so 3 iterations stay within a few 1e-5 relative even in the
+# worst case; the bound below (1e-4 relative, 1e-8 absolute) leaves room for that and
+# still fails on any dropped or doubled neighbour of a vertex of degree < 1e4.
+PR_MAX_REL = 1e-4
+PR_MAX_ABS = 1e-8
 
 
 def test_rmat25_pagerank_three_iterations(gpu, rmat25, loaded25):
     g = rmat25
+    H, thresholds = loaded25
     ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=3)
-    r32, _ = gpu.pagerank(loaded25, max_iter=3, precision="fp32", out="host")
-    assert np.abs(r32 - ref).sum() <= 1e-6
-    r16, _ = gpu.pagerank(loaded25, max_iter=3, precision="fp16", out="host")
-    assert np.abs(r16 - ref).sum() <= 1e-3
+    for t in thresholds:
+        gpu.graph_partition(H, "degree", degree_threshold=t)
+        r32, _ = gpu.pagerank(H, max_iter=3, precision="fp32", out="host")
+        d = np.abs(r32 - ref)
+        assert d.sum() <= 1e-6, f"T={t} L1 {d.sum():.3e}"
+        assert d.max() <= PR_MAX_ABS, f"T={t} max-abs {d.max():.3e}"
+        assert (d / ref).max() <= PR_MAX_REL, f"T={t} max-rel {(d / ref).max():.3e}"
+        r16, _ = gpu.pagerank(H, max_iter=3, precision="fp16", out="host")
+        assert np.abs(r16 - ref).sum() <= 1e-3, f"T={t}"
 
 
 def test_rmat22_bfs_batch_sixty_four_sources(gpu, rmat22, loaded22):
@@ -165,8 +210,10 @@ def test_rmat22_bfs_batch_sixty_four_sources(gpu, rmat22, loaded22):
 
 def test_rmat25_bfs_batch(gpu, rmat25, loaded25):
     g = rmat25
+    H, thresholds = loaded25
+    gpu.graph_partition(H, "degree", degree_threshold=thresholds[0])
     srcs = synth.sources(g, 64, seed=2)
-    lv, st = gpu.bfs_batch(loaded25, srcs, out="device")
+    lv, st = gpu.bfs_batch(H, srcs, out="device")
     for row in (0, 41):
         ref, _ = oracle.bfs(g.n, g.offsets, g.cols, int(srcs[row]), want_parents=False)
         assert np.array_equal(gpu.as_numpy_u32(lv[row]), ref), f"row {row}"
@@ -206,6 +253,6 @@ def test_rmat22_betweenness_four_sources(gpu, rmat22, loaded22):
 
 
 def test_rmat22_and_rmat25_connected_components(gpu, rmat22, loaded22, rmat25, loaded25):
-    for g, H in ((rmat22, loaded22), (rmat25, loaded25)):
+    for g, H in ((rmat22, loaded22), (rmat25, loaded25[0])):
         lab, _ = gpu.connected_components(H, out="host")
         assert np.array_equal(lab, oracle.cc(g.n, g.offsets, g.cols))
