@@ -322,22 +322,65 @@ graph_status connected_components(graph_t* g, uint32_t* labels, const cc_attr* a
  *   GRAPH_PR_FP16  x stored as FP16 scaled by n (n*r/deg), FP32 accumulation, FP32 ranks
  *   ranks   n doubles: the ranks after the last iteration
  * Runs max_iter iterations, or stops after the first iteration whose residual < tol
- * (tol <= 0: never). Errors: EINVAL (damping outside [0,1], max_iter < 1, NULL ranks, bad
- * precision), ESTATE, ENOMEM, ECUDA.
+ * (tol <= 0: never).
+ * How the neighbour sum is formed (method; the result is the same sum up to FP32 rounding
+ * order):
+ *   GRAPH_PR_AUTO       SEGMENTED for FP32 and FP16 when the graph fits its limits, else
+ *                       GATHER
+ *   GRAPH_PR_GATHER     every edge entry gathers its neighbour's contribution from global
+ *                       memory (per-vertex work items by degree class)
+ *   GRAPH_PR_SEGMENTED  FP32 / FP16 only: the source ids of each partition are cut into
+ *                       segments of 2^seg_log2 whose contributions fit in shared memory; a
+ *                       first pass sums every destination's entries of one segment from
+ *                       shared memory into a partial sum, a second pass adds each
+ *                       destination's partial sums and updates the vertex. The layout (the
+ *                       plan: 2 bytes per edge entry, about 6 bytes per partial sum) is
+ *                       built on the device by the first call after graph_partition and kept
+ *                       until the next partition, graph_free or a call with other seg_*
+ *                       values. Limits: at most 4,095 partial sums per vertex and fewer than
+ *                       2^31 edge entries per partition; GRAPH_PR_SEGMENTED on a graph beyond
+ *                       them returns EINVAL.
+ *   seg_log2   6 ... 15 (0: 15), seg_chunk 64 ... 8176 entries per first-pass chunk (0:
+ *              8176), seg_bin 64 ... 28672 partial sums per second-pass bin (0: 28672);
+ *              ignored by GATHER. pagerank_hybrid and pagerank_multi always gather.
+ * Errors: EINVAL (damping outside [0,1], max_iter < 1, NULL ranks, bad precision, method
+ * or seg_* value), ESTATE, ENOMEM, ECUDA, ETIMEOUT.
  * ------------------------------------------------------------------------------------- */
 #define GRAPH_PR_FP32 0
 #define GRAPH_PR_FP64 1
 #define GRAPH_PR_FP16 2
 
+#define GRAPH_PR_AUTO 0
+#define GRAPH_PR_GATHER 1
+#define GRAPH_PR_SEGMENTED 2
+
 typedef struct {
   double damping; /* d, e.g. 0.85 */
   int max_iter;
   double tol;
-  int precision;  /* GRAPH_PR_* */
+  int precision;  /* GRAPH_PR_FP32 / FP64 / FP16 */
   int dangling;   /* 1 = spread degree-zero rank uniformly, 0 = drop it */
   int out_mem;
   int timing;
+  int method;     /* GRAPH_PR_AUTO / GATHER / SEGMENTED */
+  int seg_log2;   /* SEGMENTED layout parameters, 0 = default (see above) */
+  int seg_chunk;
+  int seg_bin;
 } pagerank_attr;
+
+/* Layout of the segmented plan that pagerank() last built for g's current partition
+ * (inspection; all zero before the first segmented call). */
+typedef struct {
+  int built;           /* 1 after a segmented call on the current partition */
+  int usable;          /* 0: the graph exceeded a limit; calls gather instead */
+  int seg_log2, seg_chunk, seg_bin;
+  uint64_t partials;   /* partial sums per iteration (rows of the first pass) */
+  uint32_t chunks;     /* first-pass chunks */
+  uint32_t bins;       /* second-pass bins */
+  double build_ms;     /* wall-clock time of the plan build */
+} pagerank_plan_info;
+
+graph_status pagerank_plan_get(const graph_t* g, pagerank_plan_info* info);
 
 graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* ranks,
                       graph_stats* stats);

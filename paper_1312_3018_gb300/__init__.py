@@ -296,21 +296,35 @@ def connected_components(g: Graph, labels=None, *, out: str = "device", max_supe
     return labels, stats.as_dict()
 
 
+_METHOD = {"auto": 0, "gather": 1, "segmented": 2}
+
+
 def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float = 0.0,
              precision: str = "fp32", dangling: bool = True, ranks=None, out: str = "device",
-             timing: bool = False):
-    """FP64 ranks in global vertex order, and stats (residual = last L1 change)."""
+             timing: bool = False, method: str = "auto", seg_log2: int = 0,
+             seg_chunk: int = 0, seg_bin: int = 0):
+    """FP64 ranks in global vertex order, and stats (residual = last L1 change).
+    method: 'auto' (segmented for FP32 / FP16 when the graph fits), 'gather' or
+    'segmented'; seg_* are the segmented layout's parameters (0 = default)."""
     torch = _torch()
     if ranks is None:
         ranks = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"
                  else np.empty(g.n, dtype=np.float64))
     pr_, mem = _ptr(ranks)
     attr = _lib.pagerank_attr(float(damping), int(max_iter), float(tol), _PREC[precision],
-                              int(bool(dangling)), mem, int(timing))
+                              int(bool(dangling)), mem, int(timing), _METHOD[method],
+                              int(seg_log2), int(seg_chunk), int(seg_bin))
     stats = _lib.graph_stats()
     st = _lib.load().pagerank(g.handle, C.byref(attr), pr_, C.byref(stats))
     _lib.check(st, "pagerank")
     return ranks, stats.as_dict()
+
+
+def pagerank_plan(g: Graph) -> dict:
+    """Layout of the segmented plan of g's current partition (all zero before one is built)."""
+    info = _lib.pagerank_plan_info()
+    _lib.check(_lib.load().pagerank_plan_get(g.handle, C.byref(info)), "pagerank_plan_get")
+    return info.as_dict()
 
 
 def pagerank_hybrid(g: Graph, *, cpu_threads: int = 0, damping: float = 0.85,

@@ -113,7 +113,20 @@ class sssp_attr(C.Structure):
 class pagerank_attr(C.Structure):
     _fields_ = [("damping", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("precision", C.c_int), ("dangling", C.c_int), ("out_mem", C.c_int),
-                ("timing", C.c_int)]
+                ("timing", C.c_int), ("method", C.c_int), ("seg_log2", C.c_int),
+                ("seg_chunk", C.c_int), ("seg_bin", C.c_int)]
+
+
+GRAPH_PR_AUTO, GRAPH_PR_GATHER, GRAPH_PR_SEGMENTED = 0, 1, 2
+
+
+class pagerank_plan_info(C.Structure):
+    _fields_ = [("built", C.c_int), ("usable", C.c_int), ("seg_log2", C.c_int),
+                ("seg_chunk", C.c_int), ("seg_bin", C.c_int), ("partials", C.c_uint64),
+                ("chunks", C.c_uint32), ("bins", C.c_uint32), ("build_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class pagerank_hybrid_info(C.Structure):
@@ -143,6 +156,7 @@ SIGNATURES = {
     "betweenness": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bc_attr), C.POINTER(graph_stats)]),
     "connected_components": (_int, [_vp, _vp, C.POINTER(cc_attr), C.POINTER(graph_stats)]),
     "pagerank": (_int, [_vp, C.POINTER(pagerank_attr), _vp, C.POINTER(graph_stats)]),
+    "pagerank_plan_get": (_int, [_vp, C.POINTER(pagerank_plan_info)]),
     "pagerank_multi": (_int, [_vp, _u32, _vp, C.POINTER(pagerank_attr), _vp, _vp,
                               C.POINTER(graph_stats)]),
     "pagerank_hybrid": (_int, [_vp, C.POINTER(pagerank_attr), _int, _vp, C.POINTER(graph_stats),

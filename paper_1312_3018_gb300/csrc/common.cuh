@@ -299,6 +299,7 @@ struct PrWs;
 struct MsWs;
 struct BcWs;
 struct SbWs;
+struct SegWs;
 
 }  // namespace gg
 
@@ -325,6 +326,7 @@ struct graph {
   gg::MsWs* ms = nullptr;     // batched BFS workspace
   gg::BcWs* bc = nullptr;     // betweenness workspace
   gg::SbWs* sb = nullptr;     // batched SSSP workspace
+  gg::SegWs* seg = nullptr;   // segmented PageRank plan of the current partition
 };
 
 namespace gg {
@@ -368,6 +370,7 @@ void free_pr(graph* g);
 void free_msbfs(graph* g);
 void free_bc(graph* g);
 void free_ssspb(graph* g);
+void free_seg(graph* g);
 
 inline unsigned grid_for(uint64_t work, unsigned per_block) {
   uint64_t b = (work + per_block - 1) / per_block;

@@ -694,6 +694,7 @@ graph_status build_partition(graph* g, int mode, uint32_t T, const uint8_t* expl
   free_msbfs(g);
   free_bc(g);
   free_ssspb(g);
+  free_seg(g);
   free_part(g, g->part[0]);
   free_part(g, g->part[1]);
   g->part[0] = NP[0];
@@ -926,6 +927,7 @@ void graph_free(graph_t* g) {
   free_msbfs(g);
   free_bc(g);
   free_ssspb(g);
+  free_seg(g);
   free_part(g, g->part[0]);
   free_part(g, g->part[1]);
   dfree(g, g->off);

@@ -43,6 +43,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "pr_seg.cuh"
 
 namespace gg {
 
@@ -771,11 +772,27 @@ PrArgs make_args(graph* g, int cur, double damping) {
 template <class PR>
 graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* stats) {
   cudaStream_t st = g->stream;
+  // Segmented neighbour sums (pr_seg.cu) for FP32 and FP16 when the graph fits the layout;
+  // the per-edge gather kernel otherwise.
+  constexpr bool kSegCapable = sizeof(typename PR::AT) == 4;
+  bool seg = false;
+  if (at.method == GRAPH_PR_SEGMENTED && !kSegCapable) {
+    set_error("the segmented method needs FP32 or FP16 precision");
+    return GRAPH_EINVAL;
+  }
+  if (kSegCapable && at.method != GRAPH_PR_GATHER) {
+    const SegParams prm{at.seg_log2, at.seg_chunk, at.seg_bin};
+    GG_TRY(seg_prepare(g, prm, &seg));
+    if (!seg && at.method == GRAPH_PR_SEGMENTED) {
+      set_error("the graph exceeds a limit of the segmented layout");
+      return GRAPH_EINVAL;
+    }
+  }
   const PrPlan pl = make_plan(g);
-  GG_TRY((prepare_kernel<PR, false>()));
+  if (!seg) GG_TRY((prepare_kernel<PR, false>()));
   GG_TRY(ensure_ws(g, at.precision, at.max_iter));
   PrWs* w = g->pr;
-  GG_TRY(prepare_items<PR>(g, w, pl));
+  if (!seg) GG_TRY(prepare_items<PR>(g, w, pl));
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
@@ -798,6 +815,7 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
   const uint32_t nout = g->part[0].nout + g->part[1].nout;
   const uint32_t nhubs = g->part[0].nhub + g->part[1].nhub;
   const size_t smem = smem_bytes<PR>();
+  const int seg_launches = seg ? seg_launches_per_iter(g) : 0;
   int it = 0;
   int64_t launches = 1;
   double last_res = 0;
@@ -806,16 +824,36 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
     timer.mark(2);
     if (nout) k_pr_publish<typename PR::XT><<<grid_for(nout, 256), 256, 0, st>>>(A);
     timer.mark(1);
-    if (pl.nitems) {
-      k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
-                                                                 MultiArgs{});
-      if (nhubs)
-        k_pr_hubs<PR, false><<<grid_for(nhubs, kThreads / 32), kThreads, 0, st>>>(pl, A, it,
-                                                                                   MultiArgs{});
+    if (seg) {
+      SegIter si;
+      for (int p = 0; p < 2; ++p) {
+        si.x[p] = A.side[p].x;
+        si.ghost[p] = A.side[p].ghost;
+        si.xn[p] = A.side[p].xn;
+        si.r[p] = A.side[p].r;
+      }
+      si.scal = A.scal;
+      si.slots = A.slots;
+      si.nslots = kSlots;
+      si.d = A.damping_f;
+      si.d_over_n = A.d_over_n_f;
+      si.n = A.n_f;
+      si.fp16 = PR::SCALED;
+      GG_TRY(seg_launch(g, si));
       k_pr_finalize<<<1, kThreads, 0, st>>>(A, it, at.dangling);
+      launches += (nout ? 1 : 0) + seg_launches + 1;
+    } else {
+      if (pl.nitems) {
+        k_pr_compute<PR, false><<<pl.nitems, kThreads, smem, st>>>(pl, A, it, at.dangling,
+                                                                   MultiArgs{});
+        if (nhubs)
+          k_pr_hubs<PR, false><<<grid_for(nhubs, kThreads / 32), kThreads, 0, st>>>(pl, A, it,
+                                                                                     MultiArgs{});
+        k_pr_finalize<<<1, kThreads, 0, st>>>(A, it, at.dangling);
+      }
+      launches += (nout ? 1 : 0) + (pl.nitems ? 2 : 0) + (pl.nitems && nhubs ? 1 : 0);
     }
     timer.mark(0);
-    launches += (nout ? 1 : 0) + (pl.nitems ? 2 : 0) + (pl.nitems && nhubs ? 1 : 0);
     GG_CUDA(cudaGetLastError());
     cur = 1 - cur;
     ++it;
@@ -1466,7 +1504,8 @@ extern "C" graph_status pagerank(graph_t* g, const pagerank_attr* attr, double* 
   const pagerank_attr at = *attr;
   if (!(at.damping >= 0.0 && at.damping <= 1.0) || at.max_iter < 1 ||
       (at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) ||
-      (at.dangling != 0 && at.dangling != 1)) {
+      (at.dangling != 0 && at.dangling != 1) || at.method < GRAPH_PR_AUTO ||
+      at.method > GRAPH_PR_SEGMENTED) {
     set_error("bad pagerank attributes");
     return GRAPH_EINVAL;
   }

@@ -1,0 +1,1144 @@
+// Segmented pull PageRank (Section 7.1, Figure 14) for FP32 and FP16-stored contributions.
+//
+// The neighbour sum of Figure 14 gathers one contribution x[u] per edge entry. Done as a
+// scattered 4-byte global load per entry, those gathers run at about one element per SM
+// clock on this GPU, far below the HBM rate. This file reorganises each partition's edges
+// once (the plan, built on the device by the first pagerank() call after a partition) so
+// that every gather reads shared memory instead (CSR segmenting, Zhang et al., "Making
+// Caches Work for Graph Analytics", IEEE BigData 2017):
+//  - a partition's source space (its own vertices, then its ghost slots) is cut into
+//    segments of 2^log2 consecutive ids, small enough that one segment's contributions fit
+//    in a CTA's shared memory;
+//  - the partition's edge entries are stably sorted by the segment of their source; inside
+//    a segment the entries of one destination vertex form a row (rows follow destination
+//    order). An entry is 2 bytes: a 15-bit source offset within the segment and a
+//    row-start bit;
+//  - phase 1 (k_pr_seg): one persistent CTA per SM walks a contiguous range of chunks of
+//    rows. It holds the current segment's contributions in shared memory (one bulk copy
+//    per segment change), stages each chunk's entries by bulk copy while the previous chunk
+//    is summed, and writes one partial sum per row;
+//  - phase 2 (k_pr_merge): destination vertices are grouped into bins of about `bin`
+//    partial sums. A CTA bulk-copies its bin's partial sums (one contiguous run per
+//    segment) into a shared-memory window and adds each vertex's partials in segment order,
+//    reading a 15-bit window position per partial, then applies Figure 14's update.
+// Each destination therefore reads 2 bytes per edge entry plus about 10 bytes per partial
+// sum, and gathers nothing from global memory. On RMAT graphs most entries point at the
+// few high-degree vertices, so a destination's entries fall into few segments: about 0.12
+// partial sums per entry at scale 22, which is what makes the layout pay.
+//
+// Both phases add with one deterministic segmented sum (fixed per-thread runs and a fixed
+// scan over the CTA's threads), so ranks repeat bit for bit from run to run. The summation
+// order differs from a sequential neighbour sum; the FP32 result stays within the same
+// bound against FP64.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "pr_seg.cuh"
+
+namespace gg {
+
+namespace {
+
+constexpr int kSegThreads = 512;                       // phase-1 CTA
+constexpr int kSegK = 16;                              // entries per thread per chunk
+constexpr int kFrame = kSegThreads * kSegK;            // 8192 staged entries per chunk
+constexpr int kSegChunkMax = kFrame - 16;              // entries per chunk (frame slack)
+constexpr int kMergeThreads = 512;                     // phase-2 CTA
+constexpr int kMergeK = 16;
+constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 8192 staged positions per pass
+constexpr int kMergePass = kMergeFrame - 16;           // positions per pass
+constexpr uint32_t kWinMax = 32768;                    // window slots (15-bit positions)
+constexpr uint32_t kMergeVerts = 4096;                 // destination vertices per bin (max)
+constexpr uint32_t kMaxPartials = 4095;                // partial sums of one destination
+constexpr uint16_t kRowStart = 0x8000;
+constexpr uint16_t kOffMask = 0x7FFF;
+constexpr int kSortTile = 16384;                       // entries per warp in the stable sort
+constexpr int kDefLog2 = 15, kDefChunk = 8176, kDefBin = 28672;
+
+struct SegChunk {   // 32 bytes
+  int64_t e0;       // first entry in the partition's entry array
+  uint32_t nent;    // entries (<= kSegChunkMax)
+  uint32_t row0;    // first row (index into the partition's partial sums)
+  uint32_t src0;    // first source id of the segment (in its space)
+  uint32_t srclen;  // sources in the segment
+  uint32_t key;     // segment id over both partitions (changes when the slice must reload)
+  uint8_t part, ghost;
+  uint16_t pad;
+};
+static_assert(sizeof(SegChunk) == 32, "SegChunk is 32 bytes");
+
+struct SegBin {     // 32 bytes
+  uint32_t v0, v1;      // destination vertices [v0, v1) of partition `part`
+  uint32_t run0, run1;  // runs of partial sums (window copies)
+  uint32_t pos0, npos;  // positions [pos0, pos0 + npos) in the partition's position list
+  uint32_t wgran;       // window size in 16-byte granules
+  uint32_t part;
+};
+static_assert(sizeof(SegBin) == 32, "SegBin is 32 bytes");
+
+struct SegPart {
+  uint32_t S = 0, L = 0, nz = 0, nbin = 0, nchunk = 0;
+  uint32_t P = 0;     // rows (partial sums)
+  uint64_t nruns = 0;
+  DevBuf ent, part, plist, runs;
+};
+
+// Arguments of both phases (one struct, passed by value).
+struct SegArgs {
+  const void* x[2];
+  const void* ghost[2];
+  void* xn[2];
+  void* r[2];
+  const int64_t* off[2];
+  const uint16_t* ent[2];
+  float* part[2];
+  const uint16_t* plist[2];
+  const uint2* runs[2];
+  const SegChunk* chunks;
+  const SegBin* bins;
+  const uint32_t* cta0;   // first chunk of each phase-1 CTA, [grid + 1]
+  uint32_t nz[2], nv[2];
+  const double* scal;
+  double* slots;
+  uint32_t nslots;
+  float d, d_over_n, n;
+  int* err;
+};
+
+}  // namespace
+
+struct SegWs {
+  int log2 = 0, chunk = 0, bin = 0;
+  bool usable = false;
+  double build_ms = 0;
+  SegPart pp[2];
+  DevBuf chunks, bins, cta0;
+  uint32_t nchunk = 0, nbin = 0, grid1 = 0;
+};
+
+void free_seg(graph* g) {
+  SegWs* w = g->seg;
+  if (!w) return;
+  for (int p = 0; p < 2; ++p) {
+    SegPart& P = w->pp[p];
+    DevBuf* all[] = {&P.ent, &P.part, &P.plist, &P.runs};
+    for (DevBuf* b : all) dfree(g, *b);
+  }
+  dfree(g, w->chunks);
+  dfree(g, w->bins);
+  dfree(g, w->cta0);
+  delete w;
+  g->seg = nullptr;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Plan construction (device kernels; one partition at a time)
+// ---------------------------------------------------------------------------------------
+
+// Segment of an edge entry: local sources in segments [0, L), ghost slots in [L, S).
+__device__ __forceinline__ uint32_t seg_of(uint32_t e, int log2, uint32_t L) {
+  return (e & kRemote) ? L + ((e & kIdMask) >> log2) : (e >> log2);
+}
+
+// vrow[e] = the local vertex owning entry e (one warp per vertex, grid stride).
+__global__ void k_sg_vrow(const int64_t* off, uint32_t nv, uint32_t* vrow) {
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = w0; v < nv; v += nw)
+    for (int64_t e = off[v] + lane_id(); e < off[v + 1]; e += 32) vrow[e] = v;
+}
+
+// hist[key * ntiles + tile] += entries of `tile` in segment key (one warp per tile).
+__global__ void k_sg_hist(const uint32_t* E, int64_t ne, int log2, uint32_t L, uint32_t ntiles,
+                          uint32_t* hist) {
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t tile = w0; tile < ntiles; tile += nw) {
+    const int64_t a = (int64_t)tile * kSortTile;
+    const int64_t b = min(a + (int64_t)kSortTile, ne);
+    for (int64_t e0 = a; e0 < b; e0 += 32) {
+      const int64_t e = e0 + lane_id();
+      const bool valid = e < b;
+      const uint32_t key = valid ? seg_of(E[e], log2, L) : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(kFull, key);
+      if (valid && (lanemask_lt() & peers) == 0)
+        atomicAdd(&hist[(uint64_t)key * ntiles + tile], (uint32_t)__popc(peers));
+    }
+  }
+}
+
+// Stable scatter by segment: sorted position = base[key, tile] + rank within the tile.
+__global__ void k_sg_scatter(const uint32_t* E, const uint32_t* vrow, int64_t ne, int log2,
+                             uint32_t L, uint32_t ntiles, uint32_t* base, uint32_t* sv,
+                             uint16_t* sidx) {
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t mask = (1u << log2) - 1;
+  for (uint32_t tile = w0; tile < ntiles; tile += nw) {
+    const int64_t a = (int64_t)tile * kSortTile;
+    const int64_t b = min(a + (int64_t)kSortTile, ne);
+    for (int64_t e0 = a; e0 < b; e0 += 32) {
+      const int64_t e = e0 + lane_id();
+      const bool valid = e < b;
+      const uint32_t x = valid ? E[e] : 0u;
+      const uint32_t key = valid ? seg_of(x, log2, L) : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(kFull, key);
+      const uint32_t rank = __popc(peers & lanemask_lt());
+      uint32_t* slot = valid ? &base[(uint64_t)key * ntiles + tile] : nullptr;
+      const uint32_t at = valid ? *slot : 0u;
+      if (valid) {
+        sv[at + rank] = vrow[e];
+        sidx[at + rank] = (uint16_t)((x & kIdMask) & mask);
+      }
+      __syncwarp();
+      if (valid && rank == 0) *slot = at + (uint32_t)__popc(peers);
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void k_sg_segstart(const uint32_t* base, uint32_t S, uint32_t ntiles, uint32_t ne,
+                              uint32_t* segstart) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < S) segstart[s] = base[(uint64_t)s * ntiles];
+  if (s == S) segstart[s] = ne;
+}
+
+// Row starts: a new destination, or the first entry of a chunk.
+__global__ void k_sg_flags(const uint32_t* sv, uint32_t ne, uint8_t* f) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ne) f[j] = (j == 0 || sv[j] != sv[j - 1]) ? 1 : 0;
+}
+__global__ void k_sg_chunkflag(const uint32_t* ce0, uint32_t nchunk, uint8_t* f) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nchunk) f[ce0[c]] = 1;
+}
+
+// Entry words, and the destination of every row.
+__global__ void k_sg_ent(const uint32_t* sv, const uint16_t* sidx, const uint8_t* f,
+                         const uint32_t* rowid, uint32_t ne, uint16_t* ent, uint32_t* rowv) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ne) return;
+  ent[j] = (uint16_t)(sidx[j] | (f[j] ? kRowStart : 0));
+  if (f[j]) rowv[rowid[j]] = sv[j];
+}
+
+__global__ void k_sg_chunkrow(const uint32_t* ce0, const uint32_t* rowid, uint32_t nchunk,
+                              uint32_t* crow) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nchunk) crow[c] = rowid[ce0[c]];
+}
+
+// rowseg[r] = segment of row r (one thread per chunk: its rows are consecutive).
+__global__ void k_sg_rowseg(const uint32_t* crow, const uint32_t* cseg, uint32_t nchunk,
+                            uint32_t P, uint32_t* rowseg) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunk) return;
+  const uint32_t r1 = c + 1 < nchunk ? crow[c + 1] : P;
+  for (uint32_t r = crow[c]; r < r1; ++r) rowseg[r] = cseg[c];
+}
+
+__global__ void k_sg_pcount(const uint32_t* rowv, uint32_t P, uint32_t* pcount) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < P) atomicAdd(&pcount[rowv[r]], 1u);
+}
+
+__global__ void k_sg_maxp(const uint32_t* pcount, uint32_t nv, uint32_t* out) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t c = v < nv ? pcount[v] : 0u;
+  c = __reduce_max_sync(kFull, c);
+  if (lane_id() == 0 && c) atomicMax(out, c);
+}
+
+// Bin of a destination: a new bin starts every `wb` partial sums and every kMergeVerts
+// vertices (both terms never decrease along v).
+__device__ __forceinline__ uint32_t bin_key(const uint32_t* pstart, uint32_t v, uint32_t wb) {
+  return pstart[v] / wb + v / kMergeVerts;
+}
+
+__global__ void k_sg_binv0(const uint32_t* pstart, uint32_t nz, uint32_t wb, uint32_t* binv0) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nz) return;
+  const uint32_t k = bin_key(pstart, v, wb);
+  const uint32_t kp = v ? bin_key(pstart, v - 1, wb) + 1 : 0u;
+  for (uint32_t b = kp; b <= k; ++b) binv0[b] = v;  // bins skipped over start (empty) here
+}
+
+__global__ void k_sg_mc(const uint32_t* rowv, const uint32_t* rowseg, const uint32_t* pstart,
+                        uint32_t P, uint32_t S, uint32_t wb, uint32_t* mc) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < P) atomicAdd(&mc[(uint64_t)bin_key(pstart, rowv[r], wb) * S + rowseg[r]], 1u);
+}
+
+// rs[k][s]: first row of segment s that falls in bin k (one thread per segment).
+__global__ void k_sg_rs(const uint32_t* mc, const uint32_t* segrow0, uint32_t S, uint32_t nbin,
+                        uint32_t* rs) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  uint32_t acc = segrow0[s];
+  for (uint32_t k = 0; k < nbin; ++k) {
+    rs[(uint64_t)k * S + s] = acc;
+    acc += mc[(uint64_t)k * S + s];
+  }
+}
+
+// Window placement of bin k (one thread per bin): the runs of its segments, in segment
+// order, each copied as whole 16-byte granules to the next free granule of the window.
+// woff[k][s] = window slot of row rs[k][s]. Pass 0 counts runs and granules; pass 1 writes
+// the run records (source granule, window granule | granules << 16).
+__global__ void k_sg_window(const uint32_t* mc, const uint32_t* rs, uint32_t S, uint32_t nbin,
+                            int pass, uint32_t* woff, uint32_t* nruns, uint32_t* wgran,
+                            const uint32_t* runoff, uint2* runs) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nbin) return;
+  uint32_t cur = 0, nr = 0;
+  for (uint32_t s = 0; s < S; ++s) {
+    const uint64_t i = (uint64_t)k * S + s;
+    const uint32_t c = mc[i];
+    if (!c) continue;
+    const uint32_t r0 = rs[i];
+    const uint32_t g0 = r0 >> 2, g1 = (r0 + c + 3) >> 2;
+    if (pass == 0) woff[i] = 4 * cur + (r0 & 3);
+    else runs[runoff[k] + nr] = make_uint2(g0, cur | ((g1 - g0) << 16));
+    cur += g1 - g0;
+    ++nr;
+  }
+  if (pass == 0) {
+    nruns[k] = nr;
+    wgran[k] = cur;
+  }
+}
+
+// Window position of every row, collected per destination (unordered).
+__global__ void k_sg_pos(const uint32_t* rowv, const uint32_t* rowseg, const uint32_t* pstart,
+                         const uint32_t* woff, const uint32_t* rs, uint32_t P, uint32_t S,
+                         uint32_t wb, uint32_t* cur, uint16_t* tmp) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P) return;
+  const uint32_t v = rowv[r];
+  const uint64_t i = (uint64_t)bin_key(pstart, v, wb) * S + rowseg[r];
+  const uint32_t w = woff[i] + (r - rs[i]);
+  tmp[pstart[v] + atomicAdd(&cur[v], 1u)] = (uint16_t)w;
+}
+
+// Each destination's positions in ascending order (= segment order), the first marked
+// (one warp per vertex; rank by counting, positions of one vertex are distinct).
+__global__ void k_sg_plist(const uint32_t* pstart, uint32_t nz, const uint16_t* tmp,
+                           uint16_t* plist) {
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = w0; v < nz; v += nw) {
+    const uint32_t a = pstart[v], L = pstart[v + 1] - a;
+    for (uint32_t i = lane_id(); i < L; i += 32) {
+      const uint16_t wi = tmp[a + i];
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < L; ++j) rank += tmp[a + j] < wi;
+      plist[a + rank] = (uint16_t)(wi | (rank == 0 ? kRowStart : 0));
+    }
+  }
+}
+
+__global__ void k_sg_gather_u32(const uint32_t* src, const uint32_t* idx, uint32_t n,
+                                uint32_t* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[idx[i]];
+}
+
+// Scoped device buffers of the plan build: freed on every exit.
+struct Temps {
+  graph* g;
+  std::vector<DevBuf> bufs;
+  explicit Temps(graph* gg_) : g(gg_) {}
+  ~Temps() {
+    for (DevBuf& b : bufs) dfree(g, b);
+  }
+  graph_status get(size_t bytes, void** p) {
+    bufs.emplace_back();
+    const graph_status s = dalloc(g, bufs.back(), bytes ? bytes : 16);
+    *p = bufs.back().p;
+    return s;
+  }
+};
+
+template <class T>
+graph_status to_host(graph* g, std::vector<T>& h, const void* d, size_t n) {
+  h.resize(n);
+  if (n) GG_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, g->stream));
+  GG_CUDA(cudaStreamSynchronize(g->stream));
+  return GRAPH_OK;
+}
+
+template <class T>
+graph_status to_dev(graph* g, void* d, const std::vector<T>& h) {
+  if (!h.empty())
+    GG_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, g->stream));
+  GG_CUDA(cudaStreamSynchronize(g->stream));
+  return GRAPH_OK;
+}
+
+// Host records of one partition's plan, merged into the unified tables afterwards.
+struct PartHost {
+  std::vector<SegChunk> chunks;
+  std::vector<SegBin> bins;
+};
+
+// Builds partition p's plan. *fits = false (and nothing kept) when a limit of the layout is
+// exceeded.
+graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, SegPart& SP,
+                        PartHost& H, uint32_t key0, bool* fits) {
+  *fits = false;
+  const Part& P = g->part[p];
+  cudaStream_t st = g->stream;
+  const uint32_t nv = P.nv, nout = P.nout;
+  const uint32_t seg = 1u << log2;
+  if (P.ne >= (int64_t)0x7FFFFFF0) return GRAPH_OK;     // 32-bit entry and row indices
+  const uint32_t ne = (uint32_t)P.ne;
+  SP.L = (nv + seg - 1) / seg;
+  SP.S = SP.L + (nout + seg - 1) / seg;
+  SP.nz = P.cls_end[1];
+  const uint32_t S = SP.S;
+  // A bin's window holds fewer than wb + kMaxPartials partial sums plus at most 6 slots of
+  // granule padding per run (one run per segment): keep it within the 15-bit positions.
+  if ((uint64_t)kMaxPartials + 6ull * S + 64 >= kWinMax) return GRAPH_OK;
+  wb = std::min<uint32_t>(wb, kWinMax - kMaxPartials - 6 * S - 1);
+  if (ne == 0) {
+    *fits = true;
+    GG_TRY(dalloc(g, SP.ent, 64));
+    GG_TRY(dalloc(g, SP.part, 64));
+    GG_TRY(dalloc(g, SP.plist, 64));
+    GG_TRY(dalloc(g, SP.runs, 64));
+    return GRAPH_OK;
+  }
+  const uint32_t ntiles = (ne + kSortTile - 1) / kSortTile;
+  if ((uint64_t)S * ntiles >= (1ull << 28)) return GRAPH_OK;
+  Temps T(g);
+  uint32_t *vrow, *hist, *sv, *rowid, *segstart;
+  uint16_t* sidx;
+  uint8_t* f;
+  GG_TRY(T.get(4ull * ne, (void**)&vrow));
+  GG_TRY(T.get(4ull * S * ntiles, (void**)&hist));
+  GG_TRY(T.get(4ull * ne, (void**)&sv));
+  GG_TRY(T.get(2ull * ne, (void**)&sidx));
+  GG_TRY(T.get(4ull * (S + 1), (void**)&segstart));
+  const uint32_t* E = (const uint32_t*)P.E.p;
+  const int64_t* off = (const int64_t*)P.off.p;
+  const unsigned gridw = 152 * 8;
+  k_sg_vrow<<<gridw, 256, 0, st>>>(off, nv, vrow);
+  GG_CUDA(cudaMemsetAsync(hist, 0, 4ull * S * ntiles, st));
+  k_sg_hist<<<gridw, 256, 0, st>>>(E, ne, log2, SP.L, ntiles, hist);
+  GG_CUDA(cudaGetLastError());
+  GG_TRY(exclusive_scan_u32(g, hist, hist, (uint64_t)S * ntiles, nullptr));
+  k_sg_segstart<<<grid_for(S + 1, 256), 256, 0, st>>>(hist, S, ntiles, ne, segstart);
+  k_sg_scatter<<<gridw, 256, 0, st>>>(E, vrow, ne, log2, SP.L, ntiles, hist, sv, sidx);
+  GG_CUDA(cudaGetLastError());
+  std::vector<uint32_t> hseg;
+  GG_TRY(to_host(g, hseg, segstart, S + 1));
+
+  // Chunks: consecutive entries of one segment, at most ce each.
+  std::vector<uint32_t> ce0, cseg;
+  for (uint32_t s = 0; s < S; ++s)
+    for (uint32_t a = hseg[s]; a < hseg[s + 1]; a += ce) {
+      ce0.push_back(a);
+      cseg.push_back(s);
+    }
+  const uint32_t nchunk = (uint32_t)ce0.size();
+  uint32_t *dce0, *dcseg, *dcrow;
+  GG_TRY(T.get(4ull * nchunk, (void**)&dce0));
+  GG_TRY(T.get(4ull * nchunk, (void**)&dcseg));
+  GG_TRY(T.get(4ull * nchunk, (void**)&dcrow));
+  GG_TRY(to_dev(g, dce0, ce0));
+  GG_TRY(to_dev(g, dcseg, cseg));
+
+  GG_TRY(T.get(ne, (void**)&f));
+  GG_TRY(T.get(4ull * ne, (void**)&rowid));
+  k_sg_flags<<<grid_for(ne, 256), 256, 0, st>>>(sv, ne, f);
+  k_sg_chunkflag<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, nchunk, f);
+  GG_CUDA(cudaGetLastError());
+  uint32_t nrow = 0;
+  GG_TRY(exclusive_scan_u8_to_u32(g, f, rowid, ne, &nrow));
+  if (nrow >= 0x7FFFFFF0u) return GRAPH_OK;
+  SP.P = nrow;
+  GG_TRY(dalloc(g, SP.ent, 2ull * ne + 64));
+  uint32_t *rowv, *rowseg;
+  GG_TRY(T.get(4ull * nrow, (void**)&rowv));
+  GG_TRY(T.get(4ull * nrow, (void**)&rowseg));
+  k_sg_ent<<<grid_for(ne, 256), 256, 0, st>>>(sv, sidx, f, rowid, ne, (uint16_t*)SP.ent.p, rowv);
+  GG_CUDA(cudaMemsetAsync((uint16_t*)SP.ent.p + ne, 0, 64, st));
+  k_sg_chunkrow<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, rowid, nchunk, dcrow);
+  k_sg_rowseg<<<grid_for(nchunk, 128), 128, 0, st>>>(dcrow, dcseg, nchunk, nrow, rowseg);
+  GG_CUDA(cudaGetLastError());
+  std::vector<uint32_t> crow;
+  GG_TRY(to_host(g, crow, dcrow, nchunk));
+
+  // Partial sums per destination and the bins of phase 2.
+  uint32_t *pcount, *pstart, *dmax;
+  GG_TRY(T.get(4ull * (nv + 1), (void**)&pcount));
+  GG_TRY(T.get(4ull * (nv + 1), (void**)&pstart));
+  GG_TRY(T.get(4, (void**)&dmax));
+  GG_CUDA(cudaMemsetAsync(pcount, 0, 4ull * (nv + 1), st));
+  GG_CUDA(cudaMemsetAsync(dmax, 0, 4, st));
+  k_sg_pcount<<<grid_for(nrow, 256), 256, 0, st>>>(rowv, nrow, pcount);
+  k_sg_maxp<<<grid_for(nv, 256), 256, 0, st>>>(pcount, nv, dmax);
+  GG_CUDA(cudaGetLastError());
+  uint32_t total = 0;
+  GG_TRY(exclusive_scan_u32(g, pcount, pstart, nv + 1, &total));
+  std::vector<uint32_t> hmax;
+  GG_TRY(to_host(g, hmax, dmax, 1));
+  if (hmax[0] > kMaxPartials || total != nrow) return GRAPH_OK;
+  const uint32_t nz = SP.nz;
+  std::vector<uint32_t> hlast;
+  GG_TRY(to_host(g, hlast, pstart + (nz ? nz - 1 : 0), 1));
+  const uint32_t nbin = nz ? hlast[0] / wb + (nz - 1) / kMergeVerts + 1 : 0;
+  if ((uint64_t)nbin * S >= (1ull << 28)) return GRAPH_OK;
+  SP.nbin = nbin;
+  uint32_t *binv0, *mc, *rs, *woff, *nruns, *wgran, *runoff, *segrow0;
+  GG_TRY(T.get(4ull * (nbin + 1), (void**)&binv0));
+  GG_TRY(T.get(4ull * nbin * S, (void**)&mc));
+  GG_TRY(T.get(4ull * nbin * S, (void**)&rs));
+  GG_TRY(T.get(4ull * nbin * S, (void**)&woff));
+  GG_TRY(T.get(4ull * (nbin + 1), (void**)&nruns));
+  GG_TRY(T.get(4ull * (nbin + 1), (void**)&wgran));
+  GG_TRY(T.get(4ull * (nbin + 1), (void**)&runoff));
+  GG_TRY(T.get(4ull * S, (void**)&segrow0));
+  k_sg_binv0<<<grid_for(nz, 256), 256, 0, st>>>(pstart, nz, wb, binv0);
+  GG_CUDA(cudaMemcpyAsync(binv0 + nbin, &nz, 4, cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemsetAsync(mc, 0, 4ull * nbin * S, st));
+  k_sg_mc<<<grid_for(nrow, 256), 256, 0, st>>>(rowv, rowseg, pstart, nrow, S, wb, mc);
+  GG_CUDA(cudaGetLastError());
+  // first row of every segment (segments without entries: never read)
+  std::vector<uint32_t> hsegrow0(S, 0);
+  for (uint32_t c = 0; c < nchunk; ++c)
+    if (c == 0 || cseg[c] != cseg[c - 1]) hsegrow0[cseg[c]] = crow[c];
+  GG_TRY(to_dev(g, segrow0, hsegrow0));
+  k_sg_rs<<<grid_for(S, 128), 128, 0, st>>>(mc, segrow0, S, nbin, rs);
+  k_sg_window<<<grid_for(nbin, 128), 128, 0, st>>>(mc, rs, S, nbin, 0, woff, nruns, wgran,
+                                                   nullptr, nullptr);
+  GG_CUDA(cudaGetLastError());
+  uint32_t R = 0;
+  GG_TRY(exclusive_scan_u32(g, nruns, runoff, nbin, &R));
+  GG_CUDA(cudaMemcpyAsync(runoff + nbin, &R, 4, cudaMemcpyHostToDevice, st));
+  SP.nruns = R;
+  GG_TRY(dalloc(g, SP.runs, 8ull * R + 16));
+  k_sg_window<<<grid_for(nbin, 128), 128, 0, st>>>(mc, rs, S, nbin, 1, woff, nruns, wgran,
+                                                   runoff, (uint2*)SP.runs.p);
+  GG_CUDA(cudaGetLastError());
+  std::vector<uint32_t> hbinv0, hwgran, hrunoff, hbinpos;
+  GG_TRY(to_host(g, hbinv0, binv0, nbin + 1));
+  GG_TRY(to_host(g, hwgran, wgran, nbin));
+  GG_TRY(to_host(g, hrunoff, runoff, nbin + 1));
+  for (uint32_t k = 0; k < nbin; ++k)
+    if (4ull * hwgran[k] > kWinMax) return GRAPH_OK;
+  {
+    uint32_t* bpos;
+    GG_TRY(T.get(4ull * (nbin + 1), (void**)&bpos));
+    k_sg_gather_u32<<<grid_for(nbin + 1, 256), 256, 0, st>>>(pstart, binv0, nbin + 1, bpos);
+    GG_CUDA(cudaGetLastError());
+    GG_TRY(to_host(g, hbinpos, bpos, nbin + 1));
+  }
+
+  // Position lists.
+  uint32_t* cur;
+  uint16_t* tmp;
+  GG_TRY(T.get(4ull * nv, (void**)&cur));
+  GG_TRY(T.get(2ull * nrow, (void**)&tmp));
+  GG_TRY(dalloc(g, SP.plist, 2ull * nrow + 64));
+  GG_CUDA(cudaMemsetAsync(cur, 0, 4ull * nv, st));
+  k_sg_pos<<<grid_for(nrow, 256), 256, 0, st>>>(rowv, rowseg, pstart, woff, rs, nrow, S, wb,
+                                                cur, tmp);
+  k_sg_plist<<<gridw, 256, 0, st>>>(pstart, nz, tmp, (uint16_t*)SP.plist.p);
+  GG_CUDA(cudaMemsetAsync((uint16_t*)SP.plist.p + nrow, 0, 64, st));
+  GG_CUDA(cudaGetLastError());
+  GG_TRY(dalloc(g, SP.part, 4ull * nrow + 64));
+  GG_CUDA(cudaMemsetAsync(SP.part.p, 0, 4ull * nrow + 64, st));
+
+  // Host records.
+  H.chunks.resize(nchunk);
+  for (uint32_t c = 0; c < nchunk; ++c) {
+    SegChunk& C = H.chunks[c];
+    const uint32_t s = cseg[c];
+    C.e0 = ce0[c];
+    C.nent = std::min(ce, hseg[s + 1] - ce0[c]);
+    C.row0 = crow[c];
+    C.ghost = s >= SP.L;
+    C.src0 = (s >= SP.L ? s - SP.L : s) << log2;
+    const uint32_t lim = C.ghost ? nout : nv;
+    C.srclen = std::min(seg, lim - C.src0);
+    C.key = key0 + s;
+    C.part = (uint8_t)p;
+    C.pad = 0;
+  }
+  H.bins.resize(nbin);
+  for (uint32_t k = 0; k < nbin; ++k) {
+    SegBin& B = H.bins[k];
+    B.v0 = hbinv0[k];
+    B.v1 = hbinv0[k + 1];
+    B.run0 = hrunoff[k];
+    B.run1 = hrunoff[k + 1];
+    B.pos0 = hbinpos[k];
+    B.npos = hbinpos[k + 1] - hbinpos[k];
+    B.wgran = hwgran[k];
+    B.part = (uint32_t)p;
+  }
+  SP.nchunk = nchunk;
+  GG_CUDA(cudaStreamSynchronize(st));
+  *fits = true;
+  return GRAPH_OK;
+}
+
+void free_seg_part(graph* g, SegPart& SP) {
+  DevBuf* all[] = {&SP.ent, &SP.part, &SP.plist, &SP.runs};
+  for (DevBuf* b : all) dfree(g, *b);
+  SP = SegPart();
+}
+
+int sm_count(graph* g) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || n <= 0)
+    n = 152;
+  return n;
+}
+
+// ---------------------------------------------------------------------------------------
+// The deterministic segmented sum shared by both phases.
+// ---------------------------------------------------------------------------------------
+// Each thread owns kK consecutive entries of a frame. A row-start bit begins a new row. The
+// scan over threads combines (any row start in the thread, sum since the thread's last row
+// start or of the whole thread) in fixed order, so every row's value has one fixed
+// summation tree. Returned per thread: the exclusive scan (carry value, whether a row start
+// precedes the thread in the frame, number of row starts before the thread).
+struct Scan {
+  float v;
+  int f;
+  int n;
+};
+
+__device__ __forceinline__ Scan scan_op(const Scan& a, const Scan& b) {
+  Scan c;
+  c.v = b.f ? b.v : a.v + b.v;
+  c.f = a.f | b.f;
+  c.n = a.n + b.n;
+  return c;
+}
+
+template <int NT>
+__device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, Scan* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Scan inc = x;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Scan y;
+    y.v = __shfl_up_sync(kFull, inc.v, o);
+    y.f = __shfl_up_sync(kFull, inc.f, o);
+    y.n = __shfl_up_sync(kFull, inc.n, o);
+    if (lane >= o) inc = scan_op(y, inc);
+  }
+  if (lane == 31) wtot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int NW = NT / 32;
+    Scan t = lane < NW ? wtot[lane] : Scan{0.f, 0, 0};
+    #pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      Scan y;
+      y.v = __shfl_up_sync(kFull, t.v, o);
+      y.f = __shfl_up_sync(kFull, t.f, o);
+      y.n = __shfl_up_sync(kFull, t.n, o);
+      if (lane >= o) t = scan_op(y, t);
+    }
+    if (lane < NW) wtot[lane] = t;
+  }
+  __syncthreads();
+  Scan prev;
+  prev.v = __shfl_up_sync(kFull, inc.v, 1);
+  prev.f = __shfl_up_sync(kFull, inc.f, 1);
+  prev.n = __shfl_up_sync(kFull, inc.n, 1);
+  if (lane == 0) prev = Scan{0.f, 0, 0};
+  Scan excl = prev;
+  if (warp > 0) excl = scan_op(wtot[warp - 1], prev);
+  *total = wtot[NT / 32 - 1];
+  __syncthreads();  // wtot is reused by the next call
+  return excl;
+}
+
+// Loads the thread's kK entries of the staged frame (two 16-byte loads) and the table
+// values they index. Entries outside [lo, hi) of the frame are empty (no row start, 0).
+template <int kK, class TT>
+__device__ __forceinline__ uint32_t load_entries(const uint16_t* frame, int lo, int hi,
+                                                 const TT* table, float* val) {
+  static_assert(kK == 16, "two 16-byte loads per thread");
+  const int j0 = threadIdx.x * kK;
+  uint16_t e[kK];
+  const uint4 a = reinterpret_cast<const uint4*>(frame + j0)[0];
+  const uint4 b = reinterpret_cast<const uint4*>(frame + j0)[1];
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  #pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[2 * i] = (uint16_t)(w[i] & 0xFFFF);
+    e[2 * i + 1] = (uint16_t)(w[i] >> 16);
+  }
+  uint32_t fm = 0;
+  #pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    const bool in = j0 + k >= lo && j0 + k < hi;
+    const uint16_t x = in ? e[k] : (uint16_t)0;
+    if (x & kRowStart) fm |= 1u << k;
+    val[k] = in ? (float)table[x & kOffMask] : 0.f;
+  }
+  return fm;
+}
+
+template <int kK>
+__device__ __forceinline__ Scan thread_summary(const float* val, uint32_t fm) {
+  Scan s;
+  s.f = fm != 0;
+  s.n = __popc(fm);
+  float acc = 0.f;
+  #pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    if (fm & (1u << k)) acc = 0.f;
+    acc += val[k];
+  }
+  s.v = acc;  // sum since the last row start, or of the whole thread
+  return s;
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// ---------------------------------------------------------------------------------------
+// Phase 1: partial sum of every (segment, destination) row.
+// ---------------------------------------------------------------------------------------
+template <class XT>
+__host__ __device__ constexpr size_t seg_slice_bytes(int log2) {
+  return ((sizeof(XT) << log2) + 127) & ~(size_t)127;
+}
+template <class XT>
+__host__ __device__ constexpr size_t seg_smem_bytes(int log2) {
+  return seg_slice_bytes<XT>(log2) + 2 * 2 * (size_t)kFrame;
+}
+
+// Thread 0: bulk copy of chunk c's entries into `frame` (whole 16-byte granules from the
+// granule holding the chunk's first entry).
+__device__ __forceinline__ void seg_issue_chunk(const SegArgs& A, const SegChunk& C,
+                                                uint16_t* frame, uint64_t* bar) {
+  const int64_t a0 = C.e0 & ~(int64_t)7;
+  const uint32_t bytes = (uint32_t)((((C.e0 - a0) + C.nent) * 2 + 15) & ~15ll);
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s_stream(frame, A.ent[C.part] + a0, bytes, bar, l2_evict_first_policy());
+}
+
+template <class XT>
+__global__ void __launch_bounds__(kSegThreads, 1)
+k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  XT* slice = reinterpret_cast<XT*>(smem);
+  uint16_t* frames = reinterpret_cast<uint16_t*>(smem + seg_slice_bytes<XT>(log2));
+  __shared__ uint64_t bar_slice, bar_chunk[2];
+  __shared__ Scan wtot[kSegThreads / 32];
+  const uint32_t c0 = A.cta0[blockIdx.x], c1 = A.cta0[blockIdx.x + 1];
+  if (c0 >= c1) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_slice, 1);
+    mbar_init(&bar_chunk[0], 1);
+    mbar_init(&bar_chunk[1], 1);
+    fence_mbar_init();
+    seg_issue_chunk(A, A.chunks[c0], frames, &bar_chunk[0]);
+  }
+  __syncthreads();
+  uint32_t key = 0xFFFFFFFFu, ph_slice = 0, ph[2] = {0, 0};
+  bool ok = true;
+  bool out_chunk[2] = {true, false}, out_slice = false;  // copies thread 0 has in flight
+  for (uint32_t c = c0, i = 0; c < c1; ++c, ++i) {
+    const SegChunk C = A.chunks[c];
+    if (C.key != key) {
+      // every thread finished the previous chunk (barrier at the end of the loop body)
+      if (threadIdx.x == 0) {
+        const XT* src = reinterpret_cast<const XT*>(C.ghost ? A.ghost[C.part] : A.x[C.part]) + C.src0;
+        const uint32_t bytes = (uint32_t)((C.srclen * sizeof(XT) + 15) & ~(size_t)15);
+        mbar_expect_tx(&bar_slice, bytes);
+        bulk_g2s(slice, src, bytes, &bar_slice);
+        out_slice = true;
+      }
+      ok = mbar_wait_bounded(&bar_slice, ph_slice, A.err);
+      if (ok) {
+        ph_slice ^= 1;
+        out_slice = false;
+      }
+      key = C.key;
+      if (!__syncthreads_and(ok)) break;
+    }
+    const int b = i & 1;
+    if (threadIdx.x == 0 && c + 1 < c1) {
+      seg_issue_chunk(A, A.chunks[c + 1], frames + (1 - b) * kFrame, &bar_chunk[1 - b]);
+      out_chunk[1 - b] = true;
+    }
+    ok = mbar_wait_bounded(&bar_chunk[b], ph[b], A.err);
+    if (ok) {
+      ph[b] ^= 1;
+      out_chunk[b] = false;
+    }
+    if (!__syncthreads_and(ok)) break;
+    const int lo = (int)(C.e0 & 7), hi = lo + (int)C.nent;
+    float val[kSegK];
+    const uint32_t fm = load_entries<kSegK>(frames + b * kFrame, lo, hi, slice, val);
+    Scan total;
+    const Scan ex = block_seg_scan<kSegThreads>(thread_summary<kSegK>(val, fm), wtot, &total);
+    // walk: close the open row at each row start, carry the last one on
+    float* part = A.part[C.part];
+    uint32_t row = C.row0 + (uint32_t)ex.n - 1u;  // open row (wraps when none is open)
+    bool open = ex.n > 0;
+    float acc = ex.v;
+    const int j0 = threadIdx.x * kSegK;
+    #pragma unroll
+    for (int k = 0; k < kSegK; ++k) {
+      if (fm & (1u << k)) {
+        if (open) part[row] = acc;
+        ++row;
+        open = true;
+        acc = 0.f;
+      }
+      acc += val[k];
+    }
+    if (j0 <= hi - 1 && hi - 1 < j0 + kSegK) part[row] = acc;  // the chunk's last row
+    __syncthreads();  // frame b and the slice are free again
+  }
+  if (!ok && threadIdx.x == 0) {
+    // copies may still be in flight into shared memory: wait for them (bounded) first
+    if (out_slice) mbar_wait_bounded(&bar_slice, ph_slice, A.err);
+    for (int b = 0; b < 2; ++b)
+      if (out_chunk[b]) mbar_wait_bounded(&bar_chunk[b], ph[b], A.err);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Phase 2: per bin, add each destination's partial sums and update the vertex.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kMWin = 4ull * kWinMax;
+constexpr size_t kMPos = 2ull * kMergeFrame;                // one position frame
+constexpr size_t kMOff = 8ull * (kMergeVerts + 4);
+constexpr size_t kMRank = 4ull * (kMergeVerts + 8);
+constexpr size_t kMergeSmem = kMWin + 2 * kMPos + kMOff + kMRank;
+
+__device__ __forceinline__ void merge_issue_pos(const uint16_t* plist, uint32_t start,
+                                                uint32_t cnt, uint16_t* frame, uint64_t* bar) {
+  const uint32_t a0 = start & ~7u;
+  const uint32_t bytes = (((start - a0) + cnt) * 2 + 15) & ~15u;
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s_stream(frame, plist + a0, bytes, bar, l2_evict_first_policy());
+}
+
+template <class XT, bool SCALED>
+__global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_constant__ SegArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* win = reinterpret_cast<float*>(smem);
+  uint16_t* pframe = reinterpret_cast<uint16_t*>(smem + kMWin);
+  int64_t* soff = reinterpret_cast<int64_t*>(smem + kMWin + 2 * kMPos);
+  float* sr = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMOff);
+  __shared__ uint64_t bar_w, bar_p[2];
+  __shared__ Scan wtot[kMergeThreads / 32];
+  __shared__ float carry_sh;
+  __shared__ uint32_t rows_sh;
+  __shared__ float red[kMergeThreads / 32];
+  const SegBin B = A.bins[blockIdx.x];
+  if (B.v0 >= B.v1) return;
+  const int p = (int)B.part;
+  const uint32_t o0 = B.v0 & ~1u, q0 = B.v0 & ~3u;
+  const uint32_t npass = (B.npos + kMergePass - 1) / kMergePass;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_w, 1);
+    mbar_init(&bar_p[0], 1);
+    mbar_init(&bar_p[1], 1);
+    fence_mbar_init();
+    const uint32_t obytes = ((B.v1 + 1 - o0) * 8 + 15) & ~15u;
+    const uint32_t rbytes = ((B.v1 - q0) * 4 + 15) & ~15u;
+    mbar_expect_tx(&bar_w, 16u * B.wgran + obytes + rbytes);
+    const uint64_t pol = l2_evict_first_policy();
+    bulk_g2s_stream(soff, A.off[p] + o0, obytes, &bar_w, pol);
+    bulk_g2s_stream(sr, reinterpret_cast<const float*>(A.r[p]) + q0, rbytes, &bar_w, pol);
+    merge_issue_pos(A.plist[p], B.pos0, min(B.npos, (uint32_t)kMergePass), pframe, &bar_p[0]);
+    carry_sh = 0.f;
+    rows_sh = 0;
+  }
+  __syncthreads();
+  {
+    const uint2* runs = A.runs[p];
+    const float* part = A.part[p];
+    const uint64_t pol = l2_evict_first_policy();
+    for (uint32_t i = B.run0 + threadIdx.x; i < B.run1; i += kMergeThreads) {
+      const uint2 R = runs[i];
+      bulk_g2s_stream(win + 4 * (R.y & 0xFFFF), part + 4ull * R.x, 16u * (R.y >> 16), &bar_w, pol);
+    }
+  }
+  const bool okw = mbar_wait_bounded(&bar_w, 0, A.err);
+  bool ok = okw;
+  const float base = reinterpret_cast<const float*>(A.scal + 4)[0];
+  float res = 0.f;
+  uint32_t ph[2] = {0, 0};
+  bool out_p[2] = {true, false};  // position copies thread 0 has in flight
+  for (uint32_t q = 0; q < npass; ++q) {
+    const int b = q & 1;
+    const uint32_t start = B.pos0 + q * kMergePass;
+    const uint32_t cnt = min(B.npos - q * kMergePass, (uint32_t)kMergePass);
+    if (threadIdx.x == 0 && q + 1 < npass) {
+      const uint32_t s1 = start + cnt;
+      merge_issue_pos(A.plist[p], s1, min(B.npos - (q + 1) * kMergePass, (uint32_t)kMergePass),
+                      pframe + (1 - b) * kMergeFrame, &bar_p[1 - b]);
+      out_p[1 - b] = true;
+    }
+    const bool okp = ok && mbar_wait_bounded(&bar_p[b], ph[b], A.err);
+    if (okp) {
+      ph[b] ^= 1;
+      out_p[b] = false;
+    }
+    ok = okp;
+    if (!__syncthreads_and(ok)) break;
+    const int lo = (int)(start & 7u), hi = lo + (int)cnt;
+    float val[kMergeK];
+    const uint32_t fm = load_entries<kMergeK>(pframe + b * kMergeFrame, lo, hi, win, val);
+    Scan total;
+    const Scan ex = block_seg_scan<kMergeThreads>(thread_summary<kMergeK>(val, fm), wtot, &total);
+    const uint32_t rows_before = rows_sh;
+    const float carry = carry_sh;
+    uint32_t row = rows_before + (uint32_t)ex.n - 1u;  // open row of the bin (wraps if none)
+    bool open = rows_before + (uint32_t)ex.n > 0;
+    float acc = ex.f ? ex.v : carry + ex.v;
+    const int j0 = threadIdx.x * kMergeK;
+    const bool last_here = j0 <= hi - 1 && hi - 1 < j0 + kMergeK;
+    auto finish = [&](uint32_t i, float sum) {
+      const uint32_t v = B.v0 + i;
+      const int64_t deg = soff[v + 1 - o0] - soff[v - o0];
+      const float ro = sr[v - q0];
+      const float rn = SCALED ? base + A.d_over_n * sum : base + A.d * sum;
+      reinterpret_cast<float*>(A.r[p])[v] = rn;
+      XT* xn = reinterpret_cast<XT*>(A.xn[p]) + v;
+      if (SCALED) *reinterpret_cast<__half*>(xn) = __float2half_rn((rn * A.n) / (float)deg);
+      else *reinterpret_cast<float*>(xn) = rn / (float)deg;
+      res += fabsf(rn - ro);
+    };
+    #pragma unroll
+    for (int k = 0; k < kMergeK; ++k) {
+      if (fm & (1u << k)) {
+        if (open) finish(row, acc);
+        ++row;
+        open = true;
+        acc = 0.f;
+      }
+      acc += val[k];
+    }
+    __syncthreads();  // every thread has read rows_sh / carry_sh
+    if (last_here) {
+      if (q + 1 == npass) finish(row, acc);
+      else {
+        carry_sh = acc;
+        rows_sh = rows_before + (uint32_t)total.n;
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    // copies may still be in flight into shared memory: wait for them (bounded) first
+    if (threadIdx.x == 0) {
+      if (!okw) mbar_wait_bounded(&bar_w, 0, A.err);
+      for (int b = 0; b < 2; ++b)
+        if (out_p[b]) mbar_wait_bounded(&bar_p[b], ph[b], A.err);
+    }
+    return;
+  }
+  res = warp_sum(res);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = res;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < kMergeThreads / 32 ? red[threadIdx.x] : 0.f;
+    t = warp_sum(t);
+    if (threadIdx.x == 0 && t != 0.f)
+      atomicAdd(A.slots + (blockIdx.x % A.nslots), (double)t);
+  }
+}
+
+// Degree-zero vertices: the rank is the constant term, the contribution zero.
+template <class XT>
+__global__ void k_pr_seg_zero(const __grid_constant__ SegArgs A) {
+  const float base = reinterpret_cast<const float*>(A.scal + 4)[0];
+  const uint32_t z0 = A.nv[0] - A.nz[0];
+  const uint32_t total = z0 + (A.nv[1] - A.nz[1]);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += gridDim.x * blockDim.x) {
+    const int p = i < z0 ? 0 : 1;
+    const uint32_t v = A.nz[p] + (p ? i - z0 : i);
+    reinterpret_cast<float*>(A.r[p])[v] = base;
+    reinterpret_cast<XT*>(A.xn[p])[v] = XT(0.f);
+  }
+}
+
+template <class F>
+graph_status set_smem(F fn, size_t bytes) {
+  GG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return GRAPH_OK;
+}
+
+}  // namespace
+
+graph_status seg_prepare(graph* g, const SegParams& prm, bool* usable) {
+  *usable = false;
+  const int log2 = prm.log2 ? prm.log2 : kDefLog2;
+  const int ce = prm.chunk ? prm.chunk : kDefChunk;
+  const int wb = prm.bin ? prm.bin : kDefBin;
+  if (log2 < 6 || log2 > 15 || ce < 64 || ce > kSegChunkMax || wb < 64 || wb > kDefBin) {
+    set_error("segmented PageRank parameters out of range (log2 %d, chunk %d, bin %d)", log2,
+              ce, wb);
+    return GRAPH_EINVAL;
+  }
+  if (g->seg && g->seg->log2 == log2 && g->seg->chunk == ce && g->seg->bin == wb) {
+    *usable = g->seg->usable;
+    return GRAPH_OK;
+  }
+  free_seg(g);
+  const auto t0 = std::chrono::steady_clock::now();
+  SegWs* w = new SegWs();
+  g->seg = w;
+  w->log2 = log2;
+  w->chunk = ce;
+  w->bin = wb;
+  PartHost H[2];
+  bool fits[2] = {false, false};
+  for (int p = 0; p < 2 && (p == 0 || fits[0]); ++p) {
+    const graph_status s = build_part(g, p, log2, (uint32_t)ce, (uint32_t)wb, w->pp[p], H[p],
+                                      p ? w->pp[0].S : 0u, &fits[p]);
+    if (s != GRAPH_OK) {
+      free_seg(g);
+      return s;
+    }
+  }
+  if (!fits[0] || !fits[1]) {  // keep the decision, drop the partial plan
+    for (int p = 0; p < 2; ++p) free_seg_part(g, w->pp[p]);
+    w->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return GRAPH_OK;
+  }
+  std::vector<SegChunk> chunks(H[0].chunks);
+  chunks.insert(chunks.end(), H[1].chunks.begin(), H[1].chunks.end());
+  std::vector<SegBin> bins(H[0].bins);
+  bins.insert(bins.end(), H[1].bins.begin(), H[1].bins.end());
+  w->nchunk = (uint32_t)chunks.size();
+  w->nbin = (uint32_t)bins.size();
+  // Phase-1 CTAs: one per SM, each a contiguous run of chunks of about equal work
+  // (entries plus a fixed cost per chunk).
+  const uint32_t grid = (uint32_t)std::max(1, std::min<int>(sm_count(g), (int)std::max<uint32_t>(w->nchunk, 1)));
+  std::vector<uint32_t> cta0(grid + 1, w->nchunk);
+  {
+    double tot = 0;
+    for (const SegChunk& C : chunks) tot += C.nent + 512.0;
+    double acc = 0;
+    uint32_t b = 0;
+    cta0[0] = 0;
+    for (uint32_t c = 0; c < w->nchunk && b + 1 < grid; ++c) {
+      acc += chunks[c].nent + 512.0;
+      while (b + 1 < grid && acc >= tot * (b + 1) / grid) cta0[++b] = c + 1;
+    }
+    while (b + 1 <= grid) cta0[++b] = w->nchunk;
+  }
+  w->grid1 = grid;
+  graph_status s = dalloc(g, w->chunks, sizeof(SegChunk) * std::max<size_t>(chunks.size(), 1));
+  if (s == GRAPH_OK) s = dalloc(g, w->bins, sizeof(SegBin) * std::max<size_t>(bins.size(), 1));
+  if (s == GRAPH_OK) s = dalloc(g, w->cta0, 4 * cta0.size());
+  if (s == GRAPH_OK) s = to_dev(g, w->chunks.p, chunks);
+  if (s == GRAPH_OK) s = to_dev(g, w->bins.p, bins);
+  if (s == GRAPH_OK) s = to_dev(g, w->cta0.p, cta0);
+  if (s == GRAPH_OK) s = set_smem(k_pr_seg<float>, seg_smem_bytes<float>(log2));
+  if (s == GRAPH_OK) s = set_smem(k_pr_seg<__half>, seg_smem_bytes<__half>(log2));
+  if (s == GRAPH_OK) s = set_smem(k_pr_merge<float, false>, kMergeSmem);
+  if (s == GRAPH_OK) s = set_smem(k_pr_merge<__half, true>, kMergeSmem);
+  if (s != GRAPH_OK) {
+    free_seg(g);
+    return s;
+  }
+  w->usable = true;
+  *usable = true;
+  w->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return GRAPH_OK;
+}
+
+graph_status seg_launch(graph* g, const SegIter& it) {
+  SegWs* w = g->seg;
+  SegArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int p = 0; p < 2; ++p) {
+    const Part& P = g->part[p];
+    A.x[p] = it.x[p];
+    A.ghost[p] = it.ghost[p];
+    A.xn[p] = it.xn[p];
+    A.r[p] = it.r[p];
+    A.off[p] = (const int64_t*)P.off.p;
+    A.ent[p] = (const uint16_t*)w->pp[p].ent.p;
+    A.part[p] = (float*)w->pp[p].part.p;
+    A.plist[p] = (const uint16_t*)w->pp[p].plist.p;
+    A.runs[p] = (const uint2*)w->pp[p].runs.p;
+    A.nz[p] = P.cls_end[1];
+    A.nv[p] = P.nv;
+  }
+  A.chunks = (const SegChunk*)w->chunks.p;
+  A.bins = (const SegBin*)w->bins.p;
+  A.cta0 = (const uint32_t*)w->cta0.p;
+  A.scal = it.scal;
+  A.slots = it.slots;
+  A.nslots = it.nslots;
+  A.d = it.d;
+  A.d_over_n = it.d_over_n;
+  A.n = it.n;
+  A.err = (int*)g->err.p;
+  cudaStream_t st = g->stream;
+  if (w->nchunk) {
+    if (it.fp16)
+      k_pr_seg<__half><<<w->grid1, kSegThreads, seg_smem_bytes<__half>(w->log2), st>>>(A, w->log2);
+    else
+      k_pr_seg<float><<<w->grid1, kSegThreads, seg_smem_bytes<float>(w->log2), st>>>(A, w->log2);
+    GG_CUDA(cudaGetLastError());
+  }
+  if (w->nbin) {
+    if (it.fp16) k_pr_merge<__half, true><<<w->nbin, kMergeThreads, kMergeSmem, st>>>(A);
+    else k_pr_merge<float, false><<<w->nbin, kMergeThreads, kMergeSmem, st>>>(A);
+    GG_CUDA(cudaGetLastError());
+  }
+  const uint32_t zeros = (A.nv[0] - A.nz[0]) + (A.nv[1] - A.nz[1]);
+  if (zeros) {
+    if (it.fp16) k_pr_seg_zero<__half><<<std::min(grid_for(zeros, 256), 152u * 8), 256, 0, st>>>(A);
+    else k_pr_seg_zero<float><<<std::min(grid_for(zeros, 256), 152u * 8), 256, 0, st>>>(A);
+    GG_CUDA(cudaGetLastError());
+  }
+  return GRAPH_OK;
+}
+
+int seg_launches_per_iter(const graph* g) {
+  const SegWs* w = g->seg;
+  if (!w) return 0;
+  const uint32_t zeros = (g->part[0].nv - g->part[0].cls_end[1]) + (g->part[1].nv - g->part[1].cls_end[1]);
+  return (w->nchunk ? 1 : 0) + (w->nbin ? 1 : 0) + (zeros ? 1 : 0);
+}
+
+}  // namespace gg
+
+using namespace gg;
+
+extern "C" graph_status pagerank_plan_get(const graph_t* g, pagerank_plan_info* info) {
+  if (!g || !info) {
+    set_error("graph or info is NULL");
+    return GRAPH_EINVAL;
+  }
+  memset(info, 0, sizeof(*info));
+  const SegWs* w = g->seg;
+  if (!w) return GRAPH_OK;
+  info->built = 1;
+  info->usable = w->usable ? 1 : 0;
+  info->seg_log2 = w->log2;
+  info->seg_chunk = w->chunk;
+  info->seg_bin = w->bin;
+  info->partials = (uint64_t)w->pp[0].P + w->pp[1].P;
+  info->chunks = w->nchunk;
+  info->bins = w->nbin;
+  info->build_ms = w->build_ms;
+  return GRAPH_OK;
+}
