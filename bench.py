@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--retune", action="store_true",
                     help="time the threshold candidates even if the cache has this graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-omp", action="store_true",
+                    help="skip the OpenMP CPU baseline (the step on all host cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the PageRank error report (against the oracle's ranks from the "
@@ -420,6 +422,40 @@ def cpu_baseline(g, src, budget_s, pr_iters=3):
         parts += " + SSSP (Dijkstra, 1 source)"
     return {"value": edges / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{parts} on the full graph, {secs:.1f} s single-threaded"}, ranks
+
+
+def omp_baseline(G, H, g, src, pr_iters):
+    """The benchmark step on all host cores: the paper's CPU kernels in OpenMP (top-down
+    bitmap BFS, Bellman-Ford SSSP, FP32 pull PageRank; baseline/omp_graph.cpp) from the
+    step's first source, one whole step (the same work as one GPU step), timed once. The
+    GPU's levels and distances for the same source are compared element by element."""
+    import baseline
+    deg = np.diff(g.offsets)
+    t = time.perf_counter()
+    lv, _ = baseline.bfs(g.n, g.offsets, g.cols, int(src))
+    tb = time.perf_counter() - t
+    t = time.perf_counter()
+    d, rounds = baseline.sssp(g.n, g.offsets, g.cols, g.weights, int(src))
+    ts = time.perf_counter() - t
+    t = time.perf_counter()
+    r, _ = baseline.pagerank(g.n, g.offsets, g.cols, 0.85, pr_iters)
+    tp = time.perf_counter() - t
+    eb = int(deg[lv != 0xFFFFFFFF].sum())
+    es = int(deg[d != 0xFFFFFFFF].sum())
+    secs = tb + ts + tp
+    glv, _, _ = G.bfs(H, int(src), out="host", want_parents=False)
+    gd, _ = G.sssp(H, int(src), out="host")
+    gr, _ = G.pagerank(H, max_iter=pr_iters, precision="fp32", out="host")
+    return {"value": (eb + es + pr_iters * g.m) / secs / 1e9, "unit": UNIT,
+            "cores": baseline.threads(), "kind": "openmp (Figures 11, 14, 20)",
+            "sample": f"one full step (BFS + Bellman-Ford SSSP + {pr_iters} FP32 PageRank "
+                      f"iterations) from the step's first source, {secs:.1f} s",
+            "ms": {"bfs": round(tb * 1e3, 1), "sssp": round(ts * 1e3, 1),
+                   "pagerank_per_iter": round(tp * 1e3 / pr_iters, 2)},
+            "sssp_rounds": rounds,
+            "agrees_with_gpu": {"bfs_levels": bool(np.array_equal(lv, glv)),
+                                "sssp_distances": bool(np.array_equal(d, gd)),
+                                "pagerank_l1": float(np.abs(r - gr).sum())}}
 
 
 def main():
@@ -808,6 +844,10 @@ def main():
     cpu, ref = None, None
     if not a.no_cpu_baseline and world == 1:
         cpu, ref = cpu_baseline(g, srcs[0], a.cpu_budget_s)
+    cpu_omp = None
+    if not a.no_cpu_omp and world == 1:
+        cpu_omp = omp_baseline(G, H, g, srcs[0], a.pr_iters)
+        cpu_omp["vs_gpu_value"] = round(value / cpu_omp["value"], 2)
     precision = None if a.no_precision else precision_report(G, H, g, ref,
                                                              iters_step=a.pr_iters)
     # Last, because it re-partitions the graph.
@@ -846,6 +886,7 @@ def main():
         "roofline": dict(rl[dom], kernel=dom),
         "rooflines": rl,
         "cpu_baseline": cpu,
+        "cpu_omp": cpu_omp,
         "e2e": e2e,
         "batch_bfs": batch,
         "batch_sssp": batch_sssp,

@@ -42,14 +42,7 @@ namespace gg {
 
 namespace {
 
-constexpr int kSegThreads = 512;                       // phase-1 CTA
-constexpr int kSegK = 16;                              // entries per thread per chunk
-constexpr int kFrame = kSegThreads * kSegK;            // 8192 staged entries per chunk
-constexpr int kSegChunkMax = kFrame - 16;              // entries per chunk (frame slack)
-constexpr int kMergeThreads = 512;                     // phase-2 CTA
-constexpr int kMergeK = 16;
-constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 8192 staged positions per pass
-constexpr int kMergePass = kMergeFrame - 16;           // positions per pass
+constexpr int kChunkEntriesMax = 8176;                 // entries per phase-1 chunk
 constexpr uint32_t kWinMax = 32768;                    // window slots (15-bit positions)
 constexpr uint32_t kMergeVerts = 4096;                 // destination vertices per bin (max)
 constexpr uint32_t kMaxPartials = 4095;                // partial sums of one destination
@@ -60,7 +53,7 @@ constexpr int kDefLog2 = 15, kDefChunk = 8176, kDefBin = 28672;
 
 struct SegChunk {   // 32 bytes
   int64_t e0;       // first entry in the partition's entry array
-  uint32_t nent;    // entries (<= kSegChunkMax)
+  uint32_t nent;    // entries (<= kChunkEntriesMax)
   uint32_t row0;    // first row (index into the partition's partial sums)
   uint32_t src0;    // first source id of the segment (in its space)
   uint32_t srclen;  // sources in the segment
@@ -83,7 +76,7 @@ struct SegPart {
   uint32_t S = 0, L = 0, nz = 0, nbin = 0, nchunk = 0;
   uint32_t P = 0;     // rows (partial sums)
   uint64_t nruns = 0;
-  DevBuf ent, part, plist, runs;
+  DevBuf ent, part, plist, runs, deg;
 };
 
 // Arguments of both phases (one struct, passed by value).
@@ -92,7 +85,7 @@ struct SegArgs {
   const void* ghost[2];
   void* xn[2];
   void* r[2];
-  const int64_t* off[2];
+  const uint32_t* deg[2];  // degree of each vertex (plan copy, 32-bit)
   const uint16_t* ent[2];
   float* part[2];
   const uint16_t* plist[2];
@@ -124,7 +117,7 @@ void free_seg(graph* g) {
   if (!w) return;
   for (int p = 0; p < 2; ++p) {
     SegPart& P = w->pp[p];
-    DevBuf* all[] = {&P.ent, &P.part, &P.plist, &P.runs};
+    DevBuf* all[] = {&P.ent, &P.part, &P.plist, &P.runs, &P.deg};
     for (DevBuf* b : all) dfree(g, *b);
   }
   dfree(g, w->chunks);
@@ -343,6 +336,11 @@ __global__ void k_sg_plist(const uint32_t* pstart, uint32_t nz, const uint16_t* 
   }
 }
 
+__global__ void k_sg_deg(const int64_t* off, uint32_t nv, uint32_t* deg) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) deg[v] = (uint32_t)(off[v + 1] - off[v]);
+}
+
 __global__ void k_sg_gather_u32(const uint32_t* src, const uint32_t* idx, uint32_t n,
                                 uint32_t* out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -406,6 +404,11 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   // granule padding per run (one run per segment): keep it within the 15-bit positions.
   if ((uint64_t)kMaxPartials + 6ull * S + 64 >= kWinMax) return GRAPH_OK;
   wb = std::min<uint32_t>(wb, kWinMax - kMaxPartials - 6 * S - 1);
+  GG_TRY(dalloc(g, SP.deg, 4ull * nv + 64));
+  if (nv) {
+    k_sg_deg<<<grid_for(nv, 256), 256, 0, st>>>((const int64_t*)P.off.p, nv, (uint32_t*)SP.deg.p);
+    GG_CUDA(cudaGetLastError());
+  }
   if (ne == 0) {
     *fits = true;
     GG_TRY(dalloc(g, SP.ent, 64));
@@ -591,7 +594,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
 }
 
 void free_seg_part(graph* g, SegPart& SP) {
-  DevBuf* all[] = {&SP.ent, &SP.part, &SP.plist, &SP.runs};
+  DevBuf* all[] = {&SP.ent, &SP.part, &SP.plist, &SP.runs, &SP.deg};
   for (DevBuf* b : all) dfree(g, *b);
   SP = SegPart();
 }
@@ -606,34 +609,33 @@ int sm_count(graph* g) {
 // ---------------------------------------------------------------------------------------
 // The deterministic segmented sum shared by both phases.
 // ---------------------------------------------------------------------------------------
-// Each thread owns kK consecutive entries of a frame. A row-start bit begins a new row. The
-// scan over threads combines (any row start in the thread, sum since the thread's last row
-// start or of the whole thread) in fixed order, so every row's value has one fixed
-// summation tree. Returned per thread: the exclusive scan (carry value, whether a row start
-// precedes the thread in the frame, number of row starts before the thread).
+// A frame of staged 2-byte entries (table offset | row-start bit) is split over the CTA's
+// threads, kK consecutive entries each. A row-start bit begins a new row. Each thread
+// summarises its entries as (sum since its last row start, or of all of them; number of
+// row starts); an exclusive scan of these summaries over the threads, in fixed order, gives
+// every thread the running value of the row open at its first entry. Each row's value
+// therefore has one fixed summation tree, whatever the timing. Completed rows go to a
+// shared-memory row buffer at index pad(row) (one skipped slot every 16 rows, so that
+// threads closing rows 16 apart write different banks).
 struct Scan {
-  float v;
-  int f;
-  int n;
+  float v;  // running sum of the open row
+  int n;    // row starts
 };
 
 __device__ __forceinline__ Scan scan_op(const Scan& a, const Scan& b) {
-  Scan c;
-  c.v = b.f ? b.v : a.v + b.v;
-  c.f = a.f | b.f;
-  c.n = a.n + b.n;
-  return c;
+  return Scan{b.n > 0 ? b.v : a.v + b.v, a.n + b.n};
 }
 
+__device__ __forceinline__ int pad_row(int r) { return r + (r >> 4); }
+
 template <int NT>
-__device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, Scan* total) {
+__device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Scan inc = x;
   #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     Scan y;
     y.v = __shfl_up_sync(kFull, inc.v, o);
-    y.f = __shfl_up_sync(kFull, inc.f, o);
     y.n = __shfl_up_sync(kFull, inc.n, o);
     if (lane >= o) inc = scan_op(y, inc);
   }
@@ -641,12 +643,11 @@ __device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, Scan* total) 
   __syncthreads();
   if (warp == 0) {
     constexpr int NW = NT / 32;
-    Scan t = lane < NW ? wtot[lane] : Scan{0.f, 0, 0};
+    Scan t = lane < NW ? wtot[lane] : Scan{0.f, 0};
     #pragma unroll
     for (int o = 1; o < NW; o <<= 1) {
       Scan y;
       y.v = __shfl_up_sync(kFull, t.v, o);
-      y.f = __shfl_up_sync(kFull, t.f, o);
       y.n = __shfl_up_sync(kFull, t.n, o);
       if (lane >= o) t = scan_op(y, t);
     }
@@ -655,71 +656,91 @@ __device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, Scan* total) 
   __syncthreads();
   Scan prev;
   prev.v = __shfl_up_sync(kFull, inc.v, 1);
-  prev.f = __shfl_up_sync(kFull, inc.f, 1);
   prev.n = __shfl_up_sync(kFull, inc.n, 1);
-  if (lane == 0) prev = Scan{0.f, 0, 0};
+  if (lane == 0) prev = Scan{0.f, 0};
   Scan excl = prev;
   if (warp > 0) excl = scan_op(wtot[warp - 1], prev);
-  *total = wtot[NT / 32 - 1];
+  *total = wtot[NT / 32 - 1].n;
   __syncthreads();  // wtot is reused by the next call
   return excl;
-}
-
-// Loads the thread's kK entries of the staged frame (two 16-byte loads) and the table
-// values they index. Entries outside [lo, hi) of the frame are empty (no row start, 0).
-template <int kK, class TT>
-__device__ __forceinline__ uint32_t load_entries(const uint16_t* frame, int lo, int hi,
-                                                 const TT* table, float* val) {
-  static_assert(kK == 16, "two 16-byte loads per thread");
-  const int j0 = threadIdx.x * kK;
-  uint16_t e[kK];
-  const uint4 a = reinterpret_cast<const uint4*>(frame + j0)[0];
-  const uint4 b = reinterpret_cast<const uint4*>(frame + j0)[1];
-  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-  #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    e[2 * i] = (uint16_t)(w[i] & 0xFFFF);
-    e[2 * i + 1] = (uint16_t)(w[i] >> 16);
-  }
-  uint32_t fm = 0;
-  #pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    const bool in = j0 + k >= lo && j0 + k < hi;
-    const uint16_t x = in ? e[k] : (uint16_t)0;
-    if (x & kRowStart) fm |= 1u << k;
-    val[k] = in ? (float)table[x & kOffMask] : 0.f;
-  }
-  return fm;
-}
-
-template <int kK>
-__device__ __forceinline__ Scan thread_summary(const float* val, uint32_t fm) {
-  Scan s;
-  s.f = fm != 0;
-  s.n = __popc(fm);
-  float acc = 0.f;
-  #pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    if (fm & (1u << k)) acc = 0.f;
-    acc += val[k];
-  }
-  s.v = acc;  // sum since the last row start, or of the whole thread
-  return s;
 }
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
+// Sums frame entries [lo, hi) (frame indices) with table values. Rows are numbered from
+// rb - 1 (the row open before the frame, continued from `carry`; no such row when rb = 0)
+// upward; every row closed inside the frame goes to rowbuf[pad_row(row)]. Returns the
+// number of row starts in the frame; the thread holding entry hi - 1 gets *last = true,
+// with *last_row / *last_acc the row still open at the frame's end and its running sum.
+template <int NT, int K, class TT>
+__device__ __forceinline__ int seg_frame(const uint16_t* frame, int lo, int hi, const TT* table,
+                                         int rb, float carry, float* rowbuf, Scan* wtot,
+                                         bool* last, int* last_row, float* last_acc) {
+  static_assert(K == 8, "one 16-byte load per thread");
+  const int j0 = threadIdx.x * K;
+  const uint4 q = *reinterpret_cast<const uint4*>(frame + j0);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  float val[K];
+  uint32_t fm = 0;
+  if (j0 >= lo && j0 + K <= hi) {
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t e = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+      fm |= (e >> 15) << k;
+      val[k] = to_f(table[e & kOffMask]);
+    }
+  } else {
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool in = j0 + k >= lo && j0 + k < hi;
+      const uint32_t e = in ? ((k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu)) : 0u;
+      fm |= (e >> 15) << k;
+      val[k] = in ? to_f(table[e & kOffMask]) : 0.f;
+    }
+  }
+  Scan mine;
+  mine.n = __popc(fm);
+  float a = 0.f;
+  #pragma unroll
+  for (int k = 0; k < K; ++k) a = ((fm >> k) & 1u) ? val[k] : a + val[k];
+  mine.v = a;
+  int total;
+  const Scan ex = block_seg_scan<NT>(mine, wtot, &total);
+  int row = rb + ex.n - 1;
+  float acc = ex.n > 0 ? ex.v : carry + ex.v;
+  #pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if ((fm >> k) & 1u) {
+      if (row >= 0) rowbuf[pad_row(row)] = acc;
+      ++row;
+      acc = 0.f;
+    }
+    acc += val[k];
+  }
+  *last = j0 <= hi - 1 && hi - 1 < j0 + K;
+  *last_row = row;
+  *last_acc = acc;
+  return total;
+}
+
 // ---------------------------------------------------------------------------------------
 // Phase 1: partial sum of every (segment, destination) row.
 // ---------------------------------------------------------------------------------------
+constexpr int kSegThreads = 1024;                      // phase-1 CTA (one per SM)
+constexpr int kSegK = 8;                               // entries per thread per chunk
+constexpr int kFrame = kSegThreads * kSegK;            // 8192 staged entries
+constexpr int kSegChunkMax = kFrame - 16;              // entries per chunk (frame slack)
+constexpr int kSegStages = 3;                          // chunks staged ahead
+constexpr int kRowBuf1 = kFrame + kFrame / 16 + 32;    // padded row buffer (floats)
+
 template <class XT>
 __host__ __device__ constexpr size_t seg_slice_bytes(int log2) {
   return ((sizeof(XT) << log2) + 127) & ~(size_t)127;
 }
 template <class XT>
 __host__ __device__ constexpr size_t seg_smem_bytes(int log2) {
-  return seg_slice_bytes<XT>(log2) + 2 * 2 * (size_t)kFrame;
+  return seg_slice_bytes<XT>(log2) + kSegStages * 2 * (size_t)kFrame + 4 * (size_t)kRowBuf1;
 }
 
 // Thread 0: bulk copy of chunk c's entries into `frame` (whole 16-byte granules from the
@@ -738,22 +759,29 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
   extern __shared__ __align__(128) unsigned char smem[];
   XT* slice = reinterpret_cast<XT*>(smem);
   uint16_t* frames = reinterpret_cast<uint16_t*>(smem + seg_slice_bytes<XT>(log2));
-  __shared__ uint64_t bar_slice, bar_chunk[2];
+  float* rowbuf = reinterpret_cast<float*>(smem + seg_slice_bytes<XT>(log2) +
+                                           kSegStages * 2 * (size_t)kFrame);
+  __shared__ uint64_t bar_slice, bar_chunk[kSegStages];
   __shared__ Scan wtot[kSegThreads / 32];
   const uint32_t c0 = A.cta0[blockIdx.x], c1 = A.cta0[blockIdx.x + 1];
   if (c0 >= c1) return;
+  uint32_t phases = 0;      // bit s: parity of bar_chunk[s]; bit 4: bar_slice
+  uint32_t outstanding = 0;  // (thread 0) bit s: a copy on bar_chunk[s] not yet waited for;
+                             // bit 4: the slice copy
   if (threadIdx.x == 0) {
     mbar_init(&bar_slice, 1);
-    mbar_init(&bar_chunk[0], 1);
-    mbar_init(&bar_chunk[1], 1);
+    for (int s = 0; s < kSegStages; ++s) mbar_init(&bar_chunk[s], 1);
     fence_mbar_init();
-    seg_issue_chunk(A, A.chunks[c0], frames, &bar_chunk[0]);
+    for (uint32_t k = 0; k < kSegStages - 1 && c0 + k < c1; ++k) {
+      seg_issue_chunk(A, A.chunks[c0 + k], frames + k * kFrame, &bar_chunk[k]);
+      outstanding |= 1u << k;
+    }
   }
   __syncthreads();
-  uint32_t key = 0xFFFFFFFFu, ph_slice = 0, ph[2] = {0, 0};
+  uint32_t key = 0xFFFFFFFFu;
   bool ok = true;
-  bool out_chunk[2] = {true, false}, out_slice = false;  // copies thread 0 has in flight
-  for (uint32_t c = c0, i = 0; c < c1; ++c, ++i) {
+  int stage = 0;
+  for (uint32_t c = c0; c < c1; ++c, stage = stage + 1 == kSegStages ? 0 : stage + 1) {
     const SegChunk C = A.chunks[c];
     if (C.key != key) {
       // every thread finished the previous chunk (barrier at the end of the loop body)
@@ -762,67 +790,60 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
         const uint32_t bytes = (uint32_t)((C.srclen * sizeof(XT) + 15) & ~(size_t)15);
         mbar_expect_tx(&bar_slice, bytes);
         bulk_g2s(slice, src, bytes, &bar_slice);
-        out_slice = true;
+        outstanding |= 16u;
       }
-      ok = mbar_wait_bounded(&bar_slice, ph_slice, A.err);
+      ok = mbar_wait_bounded(&bar_slice, (phases >> 4) & 1u, A.err);
       if (ok) {
-        ph_slice ^= 1;
-        out_slice = false;
+        phases ^= 16u;
+        outstanding &= ~16u;
       }
       key = C.key;
       if (!__syncthreads_and(ok)) break;
     }
-    const int b = i & 1;
-    if (threadIdx.x == 0 && c + 1 < c1) {
-      seg_issue_chunk(A, A.chunks[c + 1], frames + (1 - b) * kFrame, &bar_chunk[1 - b]);
-      out_chunk[1 - b] = true;
+    if (threadIdx.x == 0 && c + kSegStages - 1 < c1) {
+      const int s2 = (stage + kSegStages - 1) % kSegStages;   // freed by chunk c - 1
+      seg_issue_chunk(A, A.chunks[c + kSegStages - 1], frames + s2 * kFrame, &bar_chunk[s2]);
+      outstanding |= 1u << s2;
     }
-    ok = mbar_wait_bounded(&bar_chunk[b], ph[b], A.err);
+    ok = mbar_wait_bounded(&bar_chunk[stage], (phases >> stage) & 1u, A.err);
     if (ok) {
-      ph[b] ^= 1;
-      out_chunk[b] = false;
+      phases ^= 1u << stage;
+      outstanding &= ~(1u << stage);
     }
     if (!__syncthreads_and(ok)) break;
     const int lo = (int)(C.e0 & 7), hi = lo + (int)C.nent;
-    float val[kSegK];
-    const uint32_t fm = load_entries<kSegK>(frames + b * kFrame, lo, hi, slice, val);
-    Scan total;
-    const Scan ex = block_seg_scan<kSegThreads>(thread_summary<kSegK>(val, fm), wtot, &total);
-    // walk: close the open row at each row start, carry the last one on
-    float* part = A.part[C.part];
-    uint32_t row = C.row0 + (uint32_t)ex.n - 1u;  // open row (wraps when none is open)
-    bool open = ex.n > 0;
-    float acc = ex.v;
-    const int j0 = threadIdx.x * kSegK;
-    #pragma unroll
-    for (int k = 0; k < kSegK; ++k) {
-      if (fm & (1u << k)) {
-        if (open) part[row] = acc;
-        ++row;
-        open = true;
-        acc = 0.f;
-      }
-      acc += val[k];
-    }
-    if (j0 <= hi - 1 && hi - 1 < j0 + kSegK) part[row] = acc;  // the chunk's last row
-    __syncthreads();  // frame b and the slice are free again
+    bool last;
+    int lrow;
+    float lacc;
+    const int nrows = seg_frame<kSegThreads, kSegK>(frames + stage * kFrame, lo, hi, slice, 0,
+                                                    0.f, rowbuf, wtot, &last, &lrow, &lacc);
+    if (last) rowbuf[pad_row(lrow)] = lacc;  // the chunk's last row
+    __syncthreads();
+    float* part = A.part[C.part] + C.row0;
+    for (int j = threadIdx.x; j < nrows; j += kSegThreads) part[j] = rowbuf[pad_row(j)];
+    __syncthreads();  // the frame, the row buffer and the slice are free again
   }
   if (!ok && threadIdx.x == 0) {
     // copies may still be in flight into shared memory: wait for them (bounded) first
-    if (out_slice) mbar_wait_bounded(&bar_slice, ph_slice, A.err);
-    for (int b = 0; b < 2; ++b)
-      if (out_chunk[b]) mbar_wait_bounded(&bar_chunk[b], ph[b], A.err);
+    if (outstanding & 16u) mbar_wait_bounded(&bar_slice, (phases >> 4) & 1u, A.err);
+    for (int s = 0; s < kSegStages; ++s)
+      if (outstanding & (1u << s)) mbar_wait_bounded(&bar_chunk[s], (phases >> s) & 1u, A.err);
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // Phase 2: per bin, add each destination's partial sums and update the vertex.
 // ---------------------------------------------------------------------------------------
+constexpr int kMergeThreads = 1024;                    // phase-2 CTA (one per SM)
+constexpr int kMergeK = 8;
+constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 8192 staged positions per pass
+constexpr int kMergePass = kMergeFrame - 16;           // positions per pass
+constexpr int kRowBuf2 = kMergeVerts + kMergeVerts / 16 + 32;
 constexpr size_t kMWin = 4ull * kWinMax;
-constexpr size_t kMPos = 2ull * kMergeFrame;                // one position frame
-constexpr size_t kMOff = 8ull * (kMergeVerts + 4);
+constexpr size_t kMPos = 2ull * kMergeFrame;                 // one position frame
+constexpr size_t kMDeg = 4ull * (kMergeVerts + 8);
 constexpr size_t kMRank = 4ull * (kMergeVerts + 8);
-constexpr size_t kMergeSmem = kMWin + 2 * kMPos + kMOff + kMRank;
+constexpr size_t kMergeSmem = kMWin + 2 * kMPos + kMDeg + kMRank + 4ull * kRowBuf2;
 
 __device__ __forceinline__ void merge_issue_pos(const uint16_t* plist, uint32_t start,
                                                 uint32_t cnt, uint16_t* frame, uint64_t* bar) {
@@ -837,29 +858,29 @@ __global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_cons
   extern __shared__ __align__(128) unsigned char smem[];
   float* win = reinterpret_cast<float*>(smem);
   uint16_t* pframe = reinterpret_cast<uint16_t*>(smem + kMWin);
-  int64_t* soff = reinterpret_cast<int64_t*>(smem + kMWin + 2 * kMPos);
-  float* sr = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMOff);
+  uint32_t* sdeg = reinterpret_cast<uint32_t*>(smem + kMWin + 2 * kMPos);
+  float* sr = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMDeg);
+  float* rowbuf = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMDeg + kMRank);
   __shared__ uint64_t bar_w, bar_p[2];
   __shared__ Scan wtot[kMergeThreads / 32];
   __shared__ float carry_sh;
-  __shared__ uint32_t rows_sh;
+  __shared__ int rows_sh;
   __shared__ float red[kMergeThreads / 32];
   const SegBin B = A.bins[blockIdx.x];
   if (B.v0 >= B.v1) return;
   const int p = (int)B.part;
-  const uint32_t o0 = B.v0 & ~1u, q0 = B.v0 & ~3u;
+  const uint32_t q0 = B.v0 & ~3u;
   const uint32_t npass = (B.npos + kMergePass - 1) / kMergePass;
   if (threadIdx.x == 0) {
     mbar_init(&bar_w, 1);
     mbar_init(&bar_p[0], 1);
     mbar_init(&bar_p[1], 1);
     fence_mbar_init();
-    const uint32_t obytes = ((B.v1 + 1 - o0) * 8 + 15) & ~15u;
-    const uint32_t rbytes = ((B.v1 - q0) * 4 + 15) & ~15u;
-    mbar_expect_tx(&bar_w, 16u * B.wgran + obytes + rbytes);
+    const uint32_t vbytes = ((B.v1 - q0) * 4 + 15) & ~15u;
+    mbar_expect_tx(&bar_w, 16u * B.wgran + 2 * vbytes);
     const uint64_t pol = l2_evict_first_policy();
-    bulk_g2s_stream(soff, A.off[p] + o0, obytes, &bar_w, pol);
-    bulk_g2s_stream(sr, reinterpret_cast<const float*>(A.r[p]) + q0, rbytes, &bar_w, pol);
+    bulk_g2s_stream(sdeg, A.deg[p] + q0, vbytes, &bar_w, pol);
+    bulk_g2s_stream(sr, reinterpret_cast<const float*>(A.r[p]) + q0, vbytes, &bar_w, pol);
     merge_issue_pos(A.plist[p], B.pos0, min(B.npos, (uint32_t)kMergePass), pframe, &bar_p[0]);
     carry_sh = 0.f;
     rows_sh = 0;
@@ -876,66 +897,39 @@ __global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_cons
   }
   const bool okw = mbar_wait_bounded(&bar_w, 0, A.err);
   bool ok = okw;
-  const float base = reinterpret_cast<const float*>(A.scal + 4)[0];
-  float res = 0.f;
-  uint32_t ph[2] = {0, 0};
-  bool out_p[2] = {true, false};  // position copies thread 0 has in flight
+  uint32_t ph = 0;                 // bit b: parity of bar_p[b]
+  uint32_t out_p = 1;              // (thread 0) bit b: a copy on bar_p[b] not yet waited for
   for (uint32_t q = 0; q < npass; ++q) {
     const int b = q & 1;
     const uint32_t start = B.pos0 + q * kMergePass;
     const uint32_t cnt = min(B.npos - q * kMergePass, (uint32_t)kMergePass);
     if (threadIdx.x == 0 && q + 1 < npass) {
-      const uint32_t s1 = start + cnt;
-      merge_issue_pos(A.plist[p], s1, min(B.npos - (q + 1) * kMergePass, (uint32_t)kMergePass),
+      merge_issue_pos(A.plist[p], start + cnt,
+                      min(B.npos - (q + 1) * kMergePass, (uint32_t)kMergePass),
                       pframe + (1 - b) * kMergeFrame, &bar_p[1 - b]);
-      out_p[1 - b] = true;
+      out_p |= 2u >> b;
     }
-    const bool okp = ok && mbar_wait_bounded(&bar_p[b], ph[b], A.err);
+    const bool okp = ok && mbar_wait_bounded(&bar_p[b], (ph >> b) & 1u, A.err);
     if (okp) {
-      ph[b] ^= 1;
-      out_p[b] = false;
+      ph ^= 1u << b;
+      out_p &= ~(1u << b);
     }
     ok = okp;
     if (!__syncthreads_and(ok)) break;
     const int lo = (int)(start & 7u), hi = lo + (int)cnt;
-    float val[kMergeK];
-    const uint32_t fm = load_entries<kMergeK>(pframe + b * kMergeFrame, lo, hi, win, val);
-    Scan total;
-    const Scan ex = block_seg_scan<kMergeThreads>(thread_summary<kMergeK>(val, fm), wtot, &total);
-    const uint32_t rows_before = rows_sh;
-    const float carry = carry_sh;
-    uint32_t row = rows_before + (uint32_t)ex.n - 1u;  // open row of the bin (wraps if none)
-    bool open = rows_before + (uint32_t)ex.n > 0;
-    float acc = ex.f ? ex.v : carry + ex.v;
-    const int j0 = threadIdx.x * kMergeK;
-    const bool last_here = j0 <= hi - 1 && hi - 1 < j0 + kMergeK;
-    auto finish = [&](uint32_t i, float sum) {
-      const uint32_t v = B.v0 + i;
-      const int64_t deg = soff[v + 1 - o0] - soff[v - o0];
-      const float ro = sr[v - q0];
-      const float rn = SCALED ? base + A.d_over_n * sum : base + A.d * sum;
-      reinterpret_cast<float*>(A.r[p])[v] = rn;
-      XT* xn = reinterpret_cast<XT*>(A.xn[p]) + v;
-      if (SCALED) *reinterpret_cast<__half*>(xn) = __float2half_rn((rn * A.n) / (float)deg);
-      else *reinterpret_cast<float*>(xn) = rn / (float)deg;
-      res += fabsf(rn - ro);
-    };
-    #pragma unroll
-    for (int k = 0; k < kMergeK; ++k) {
-      if (fm & (1u << k)) {
-        if (open) finish(row, acc);
-        ++row;
-        open = true;
-        acc = 0.f;
-      }
-      acc += val[k];
-    }
-    __syncthreads();  // every thread has read rows_sh / carry_sh
-    if (last_here) {
-      if (q + 1 == npass) finish(row, acc);
+    const int rb = rows_sh;
+    bool last;
+    int lrow;
+    float lacc;
+    const int nflags = seg_frame<kMergeThreads, kMergeK>(pframe + b * kMergeFrame, lo, hi, win,
+                                                         rb, carry_sh, rowbuf, wtot, &last,
+                                                         &lrow, &lacc);
+    // every thread has read rows_sh and carry_sh (barriers inside seg_frame)
+    if (last) {
+      if (q + 1 == npass) rowbuf[pad_row(lrow)] = lacc;
       else {
-        carry_sh = acc;
-        rows_sh = rows_before + (uint32_t)total.n;
+        carry_sh = lacc;
+        rows_sh = rb + nflags;
       }
     }
     __syncthreads();
@@ -945,15 +939,30 @@ __global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_cons
     if (threadIdx.x == 0) {
       if (!okw) mbar_wait_bounded(&bar_w, 0, A.err);
       for (int b = 0; b < 2; ++b)
-        if (out_p[b]) mbar_wait_bounded(&bar_p[b], ph[b], A.err);
+        if (out_p & (1u << b)) mbar_wait_bounded(&bar_p[b], (ph >> b) & 1u, A.err);
     }
     return;
+  }
+  // Vertex updates (Figure 14), one thread per vertex of the bin.
+  const float base = reinterpret_cast<const float*>(A.scal + 4)[0];
+  float res = 0.f;
+  float* rg = reinterpret_cast<float*>(A.r[p]);
+  for (uint32_t i = threadIdx.x; i < B.v1 - B.v0; i += kMergeThreads) {
+    const uint32_t v = B.v0 + i;
+    const float sum = rowbuf[pad_row((int)i)];
+    const float deg = (float)sdeg[v - q0];
+    const float ro = sr[v - q0];
+    const float rn = SCALED ? base + A.d_over_n * sum : base + A.d * sum;
+    rg[v] = rn;
+    if (SCALED) reinterpret_cast<__half*>(A.xn[p])[v] = __float2half_rn((rn * A.n) / deg);
+    else reinterpret_cast<float*>(A.xn[p])[v] = rn / deg;
+    res += fabsf(rn - ro);
   }
   res = warp_sum(res);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = res;
   __syncthreads();
   if (threadIdx.x < 32) {
-    float t = threadIdx.x < kMergeThreads / 32 ? red[threadIdx.x] : 0.f;
+    float t = red[threadIdx.x];
     t = warp_sum(t);
     if (threadIdx.x == 0 && t != 0.f)
       atomicAdd(A.slots + (blockIdx.x % A.nslots), (double)t);
@@ -988,7 +997,7 @@ graph_status seg_prepare(graph* g, const SegParams& prm, bool* usable) {
   const int log2 = prm.log2 ? prm.log2 : kDefLog2;
   const int ce = prm.chunk ? prm.chunk : kDefChunk;
   const int wb = prm.bin ? prm.bin : kDefBin;
-  if (log2 < 6 || log2 > 15 || ce < 64 || ce > kSegChunkMax || wb < 64 || wb > kDefBin) {
+  if (log2 < 6 || log2 > 15 || ce < 64 || ce > kChunkEntriesMax || wb < 64 || wb > kDefBin) {
     set_error("segmented PageRank parameters out of range (log2 %d, chunk %d, bin %d)", log2,
               ce, wb);
     return GRAPH_EINVAL;
@@ -1072,7 +1081,7 @@ graph_status seg_launch(graph* g, const SegIter& it) {
     A.ghost[p] = it.ghost[p];
     A.xn[p] = it.xn[p];
     A.r[p] = it.r[p];
-    A.off[p] = (const int64_t*)P.off.p;
+    A.deg[p] = (const uint32_t*)w->pp[p].deg.p;
     A.ent[p] = (const uint16_t*)w->pp[p].ent.p;
     A.part[p] = (float*)w->pp[p].part.p;
     A.plist[p] = (const uint16_t*)w->pp[p].plist.p;
