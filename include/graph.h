@@ -337,12 +337,13 @@ graph_status connected_components(graph_t* g, uint32_t* labels, const cc_attr* a
  *                       plan: 2 bytes per edge entry, about 6 bytes per partial sum) is
  *                       built on the device by the first call after graph_partition and kept
  *                       until the next partition, graph_free or a call with other seg_*
- *                       values. Limits: at most 4,095 partial sums per vertex and fewer than
- *                       2^31 edge entries per partition; GRAPH_PR_SEGMENTED on a graph beyond
- *                       them returns EINVAL.
+ *                       values. Limits: at most 2,047 partial sums per vertex, at most 2,378
+ *                       segments per partition and fewer than 2^31 edge entries per
+ *                       partition; GRAPH_PR_SEGMENTED on a graph beyond them returns EINVAL.
  *   seg_log2   6 ... 15 (0: 15), seg_chunk 64 ... 8176 entries per first-pass chunk (0:
- *              8176), seg_bin 64 ... 28672 partial sums per second-pass bin (0: 28672);
- *              ignored by GATHER. pagerank_hybrid and pagerank_multi always gather.
+ *              8176), seg_bin 64 ... 14336 partial sums per second-pass bin (0: 12288, and
+ *              at most 14336 - 6 * segments of the partition); ignored by GATHER.
+ *              pagerank_hybrid and pagerank_multi always gather.
  * Errors: EINVAL (damping outside [0,1], max_iter < 1, NULL ranks, bad precision, method
  * or seg_* value), ESTATE, ENOMEM, ECUDA, ETIMEOUT.
  * ------------------------------------------------------------------------------------- */

@@ -43,21 +43,25 @@ namespace gg {
 namespace {
 
 constexpr int kChunkEntriesMax = 8176;                 // entries per phase-1 chunk
-constexpr uint32_t kWinMax = 32768;                    // window slots (15-bit positions)
-constexpr uint32_t kMergeVerts = 4096;                 // destination vertices per bin (max)
-constexpr uint32_t kMaxPartials = 4095;                // partial sums of one destination
+constexpr uint32_t kMini = 256;                        // entries per phase-1 warp piece
+constexpr uint32_t kMiniPerChunk = 32;                 // mini-chunks per chunk frame
+constexpr uint32_t kWinMax = 16384;                    // window slots (fit 15-bit positions)
+constexpr uint32_t kMergeVerts = 2048;                 // destination vertices per bin (max)
+constexpr uint32_t kMaxPartials = 2047;                // partial sums of one destination
 constexpr uint16_t kRowStart = 0x8000;
 constexpr uint16_t kOffMask = 0x7FFF;
 constexpr int kSortTile = 16384;                       // entries per warp in the stable sort
-constexpr int kDefLog2 = 15, kDefChunk = 8176, kDefBin = 28672;
+constexpr int kDefLog2 = 15, kDefChunk = 8176, kDefBin = 12288;
+constexpr int kMaxBin = (int)(kWinMax - kMaxPartials - 1);   // 14336
 
 struct SegChunk {   // 32 bytes
-  int64_t e0;       // first entry in the partition's entry array
+  uint32_t e0;      // first entry in the partition's entry array
   uint32_t nent;    // entries (<= kChunkEntriesMax)
   uint32_t row0;    // first row (index into the partition's partial sums)
   uint32_t src0;    // first source id of the segment (in its space)
   uint32_t srclen;  // sources in the segment
   uint32_t key;     // segment id over both partitions (changes when the slice must reload)
+  uint32_t cl;      // chunk index within its partition (its mini-chunk row offsets)
   uint8_t part, ghost;
   uint16_t pad;
 };
@@ -76,7 +80,7 @@ struct SegPart {
   uint32_t S = 0, L = 0, nz = 0, nbin = 0, nchunk = 0;
   uint32_t P = 0;     // rows (partial sums)
   uint64_t nruns = 0;
-  DevBuf ent, part, plist, runs, deg;
+  DevBuf ent, part, plist, runs, deg, mrow;
 };
 
 // Arguments of both phases (one struct, passed by value).
@@ -87,6 +91,7 @@ struct SegArgs {
   void* r[2];
   const uint32_t* deg[2];  // degree of each vertex (plan copy, 32-bit)
   const uint16_t* ent[2];
+  const uint16_t* mrow[2];  // [chunk][32] first row of each mini-chunk, relative to row0
   float* part[2];
   const uint16_t* plist[2];
   const uint2* runs[2];
@@ -117,7 +122,7 @@ void free_seg(graph* g) {
   if (!w) return;
   for (int p = 0; p < 2; ++p) {
     SegPart& P = w->pp[p];
-    DevBuf* all[] = {&P.ent, &P.part, &P.plist, &P.runs, &P.deg};
+    DevBuf* all[] = {&P.ent, &P.part, &P.plist, &P.runs, &P.deg, &P.mrow};
     for (DevBuf* b : all) dfree(g, *b);
   }
   dfree(g, w->chunks);
@@ -207,9 +212,30 @@ __global__ void k_sg_flags(const uint32_t* sv, uint32_t ne, uint8_t* f) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < ne) f[j] = (j == 0 || sv[j] != sv[j - 1]) ? 1 : 0;
 }
-__global__ void k_sg_chunkflag(const uint32_t* ce0, uint32_t nchunk, uint8_t* f) {
+// Rows also start at the first entry of every chunk and of every mini-chunk: the 256-entry
+// pieces of the chunk's 16-byte-aligned frame that one warp of phase 1 sums on its own.
+__global__ void k_sg_chunkflag(const uint32_t* ce0, const uint32_t* cn, uint32_t nchunk,
+                               uint8_t* f) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < nchunk) f[ce0[c]] = 1;
+  if (c >= nchunk) return;
+  const uint32_t e0 = ce0[c], e1 = e0 + cn[c], a0 = e0 & ~7u;
+  f[e0] = 1;
+  for (uint32_t pos = a0 + kMini; pos < e1; pos += kMini) f[pos] = 1;
+}
+
+// mrow[c][w]: rows of chunk c before mini-chunk w (rows of the chunk if w is past its end).
+__global__ void k_sg_mrow(const uint32_t* ce0, const uint32_t* cn, const uint32_t* rowid,
+                          uint32_t nchunk, uint32_t ne, uint32_t P, uint16_t* mrow) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunk) return;
+  const uint32_t e0 = ce0[c], e1 = e0 + cn[c], a0 = e0 & ~7u;
+  const uint32_t r0 = rowid[e0];
+  const uint32_t rend = e1 < ne ? rowid[e1] : P;
+  for (uint32_t w = 0; w < kMiniPerChunk; ++w) {
+    const uint32_t pos = a0 + w * kMini;
+    mrow[(size_t)c * kMiniPerChunk + w] =
+        (uint16_t)(w == 0 ? 0u : (pos < e1 ? rowid[pos] - r0 : rend - r0));
+  }
 }
 
 // Entry words, and the destination of every row.
@@ -411,6 +437,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   }
   if (ne == 0) {
     *fits = true;
+    GG_TRY(dalloc(g, SP.mrow, 64));
     GG_TRY(dalloc(g, SP.ent, 64));
     GG_TRY(dalloc(g, SP.part, 64));
     GG_TRY(dalloc(g, SP.plist, 64));
@@ -450,17 +477,21 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
       cseg.push_back(s);
     }
   const uint32_t nchunk = (uint32_t)ce0.size();
-  uint32_t *dce0, *dcseg, *dcrow;
+  std::vector<uint32_t> cn(nchunk);
+  for (uint32_t c = 0; c < nchunk; ++c) cn[c] = std::min(ce, hseg[cseg[c] + 1] - ce0[c]);
+  uint32_t *dce0, *dcseg, *dcrow, *dcn;
   GG_TRY(T.get(4ull * nchunk, (void**)&dce0));
   GG_TRY(T.get(4ull * nchunk, (void**)&dcseg));
   GG_TRY(T.get(4ull * nchunk, (void**)&dcrow));
+  GG_TRY(T.get(4ull * nchunk, (void**)&dcn));
   GG_TRY(to_dev(g, dce0, ce0));
   GG_TRY(to_dev(g, dcseg, cseg));
+  GG_TRY(to_dev(g, dcn, cn));
 
   GG_TRY(T.get(ne, (void**)&f));
   GG_TRY(T.get(4ull * ne, (void**)&rowid));
   k_sg_flags<<<grid_for(ne, 256), 256, 0, st>>>(sv, ne, f);
-  k_sg_chunkflag<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, nchunk, f);
+  k_sg_chunkflag<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, dcn, nchunk, f);
   GG_CUDA(cudaGetLastError());
   uint32_t nrow = 0;
   GG_TRY(exclusive_scan_u8_to_u32(g, f, rowid, ne, &nrow));
@@ -473,6 +504,9 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   k_sg_ent<<<grid_for(ne, 256), 256, 0, st>>>(sv, sidx, f, rowid, ne, (uint16_t*)SP.ent.p, rowv);
   GG_CUDA(cudaMemsetAsync((uint16_t*)SP.ent.p + ne, 0, 64, st));
   k_sg_chunkrow<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, rowid, nchunk, dcrow);
+  GG_TRY(dalloc(g, SP.mrow, 2ull * kMiniPerChunk * nchunk + 64));
+  k_sg_mrow<<<grid_for(nchunk, 128), 128, 0, st>>>(dce0, dcn, rowid, nchunk, ne, nrow,
+                                                   (uint16_t*)SP.mrow.p);
   k_sg_rowseg<<<grid_for(nchunk, 128), 128, 0, st>>>(dcrow, dcseg, nchunk, nrow, rowseg);
   GG_CUDA(cudaGetLastError());
   std::vector<uint32_t> crow;
@@ -565,8 +599,9 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
     SegChunk& C = H.chunks[c];
     const uint32_t s = cseg[c];
     C.e0 = ce0[c];
-    C.nent = std::min(ce, hseg[s + 1] - ce0[c]);
+    C.nent = cn[c];
     C.row0 = crow[c];
+    C.cl = c;
     C.ghost = s >= SP.L;
     C.src0 = (s >= SP.L ? s - SP.L : s) << log2;
     const uint32_t lim = C.ghost ? nout : nv;
@@ -594,7 +629,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
 }
 
 void free_seg_part(graph* g, SegPart& SP) {
-  DevBuf* all[] = {&SP.ent, &SP.part, &SP.plist, &SP.runs, &SP.deg};
+  DevBuf* all[] = {&SP.ent, &SP.part, &SP.plist, &SP.runs, &SP.deg, &SP.mrow};
   for (DevBuf* b : all) dfree(g, *b);
   SP = SegPart();
 }
@@ -727,12 +762,19 @@ __device__ __forceinline__ int seg_frame(const uint16_t* frame, int lo, int hi, 
 // ---------------------------------------------------------------------------------------
 // Phase 1: partial sum of every (segment, destination) row.
 // ---------------------------------------------------------------------------------------
+// A chunk's entries are staged as a frame of kMiniPerChunk mini-chunks of kMini entries
+// (16-byte aligned). The plan starts a new row at every mini-chunk, so each warp sums one
+// mini-chunk on its own: a warp-level version of the segmented sum above, its rows in a
+// private shared-memory buffer, then one coalesced write of them to the partial sums at the
+// mini-chunk's row offset (staged with the chunk). One CTA barrier per chunk frees the
+// frame and, at a segment change, the slice.
 constexpr int kSegThreads = 1024;                      // phase-1 CTA (one per SM)
-constexpr int kSegK = 8;                               // entries per thread per chunk
-constexpr int kFrame = kSegThreads * kSegK;            // 8192 staged entries
-constexpr int kSegChunkMax = kFrame - 16;              // entries per chunk (frame slack)
+constexpr int kSegK = 8;                               // entries per lane of a mini-chunk
+constexpr int kFrame = kMiniPerChunk * kMini;          // 8192 staged entries
 constexpr int kSegStages = 3;                          // chunks staged ahead
-constexpr int kRowBuf1 = kFrame + kFrame / 16 + 32;    // padded row buffer (floats)
+constexpr int kFrameBytes = 2 * kFrame + 2 * kMiniPerChunk;   // entries, then row offsets
+constexpr int kWarpRows = kMini + kMini / 16 + 16;     // padded rows of one mini-chunk
+static_assert(kMini == 32 * kSegK && kSegThreads / 32 == (int)kMiniPerChunk, "warp per mini-chunk");
 
 template <class XT>
 __host__ __device__ constexpr size_t seg_slice_bytes(int log2) {
@@ -740,17 +782,21 @@ __host__ __device__ constexpr size_t seg_slice_bytes(int log2) {
 }
 template <class XT>
 __host__ __device__ constexpr size_t seg_smem_bytes(int log2) {
-  return seg_slice_bytes<XT>(log2) + kSegStages * 2 * (size_t)kFrame + 4 * (size_t)kRowBuf1;
+  return seg_slice_bytes<XT>(log2) + kSegStages * (size_t)kFrameBytes +
+         4 * (size_t)kWarpRows * (kSegThreads / 32);
 }
 
-// Thread 0: bulk copy of chunk c's entries into `frame` (whole 16-byte granules from the
-// granule holding the chunk's first entry).
+// Thread 0: bulk copies of chunk c's entries (whole 16-byte granules from the granule
+// holding its first entry) and of its mini-chunk row offsets into `frame`.
 __device__ __forceinline__ void seg_issue_chunk(const SegArgs& A, const SegChunk& C,
-                                                uint16_t* frame, uint64_t* bar) {
-  const int64_t a0 = C.e0 & ~(int64_t)7;
-  const uint32_t bytes = (uint32_t)((((C.e0 - a0) + C.nent) * 2 + 15) & ~15ll);
-  mbar_expect_tx(bar, bytes);
-  bulk_g2s_stream(frame, A.ent[C.part] + a0, bytes, bar, l2_evict_first_policy());
+                                                unsigned char* frame, uint64_t* bar) {
+  const uint32_t a0 = C.e0 & ~7u;
+  const uint32_t bytes = (((C.e0 - a0) + C.nent) * 2 + 15) & ~15u;
+  mbar_expect_tx(bar, bytes + 2 * kMiniPerChunk);
+  const uint64_t pol = l2_evict_first_policy();
+  bulk_g2s_stream(frame, A.ent[C.part] + a0, bytes, bar, pol);
+  bulk_g2s_stream(frame + 2 * kFrame, A.mrow[C.part] + (size_t)C.cl * kMiniPerChunk,
+                  2 * kMiniPerChunk, bar, pol);
 }
 
 template <class XT>
@@ -758,14 +804,14 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
   extern __shared__ __align__(128) unsigned char smem[];
   XT* slice = reinterpret_cast<XT*>(smem);
-  uint16_t* frames = reinterpret_cast<uint16_t*>(smem + seg_slice_bytes<XT>(log2));
-  float* rowbuf = reinterpret_cast<float*>(smem + seg_slice_bytes<XT>(log2) +
-                                           kSegStages * 2 * (size_t)kFrame);
+  unsigned char* frames = smem + seg_slice_bytes<XT>(log2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* rows = reinterpret_cast<float*>(frames + kSegStages * (size_t)kFrameBytes) +
+                warp * kWarpRows;
   __shared__ uint64_t bar_slice, bar_chunk[kSegStages];
-  __shared__ Scan wtot[kSegThreads / 32];
   const uint32_t c0 = A.cta0[blockIdx.x], c1 = A.cta0[blockIdx.x + 1];
   if (c0 >= c1) return;
-  uint32_t phases = 0;      // bit s: parity of bar_chunk[s]; bit 4: bar_slice
+  uint32_t phases = 0;       // bit s: parity of bar_chunk[s]; bit 4: bar_slice
   uint32_t outstanding = 0;  // (thread 0) bit s: a copy on bar_chunk[s] not yet waited for;
                              // bit 4: the slice copy
   if (threadIdx.x == 0) {
@@ -773,7 +819,7 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
     for (int s = 0; s < kSegStages; ++s) mbar_init(&bar_chunk[s], 1);
     fence_mbar_init();
     for (uint32_t k = 0; k < kSegStages - 1 && c0 + k < c1; ++k) {
-      seg_issue_chunk(A, A.chunks[c0 + k], frames + k * kFrame, &bar_chunk[k]);
+      seg_issue_chunk(A, A.chunks[c0 + k], frames + k * kFrameBytes, &bar_chunk[k]);
       outstanding |= 1u << k;
     }
   }
@@ -802,7 +848,8 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
     }
     if (threadIdx.x == 0 && c + kSegStages - 1 < c1) {
       const int s2 = (stage + kSegStages - 1) % kSegStages;   // freed by chunk c - 1
-      seg_issue_chunk(A, A.chunks[c + kSegStages - 1], frames + s2 * kFrame, &bar_chunk[s2]);
+      seg_issue_chunk(A, A.chunks[c + kSegStages - 1], frames + s2 * kFrameBytes,
+                      &bar_chunk[s2]);
       outstanding |= 1u << s2;
     }
     ok = mbar_wait_bounded(&bar_chunk[stage], (phases >> stage) & 1u, A.err);
@@ -811,17 +858,64 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
       outstanding &= ~(1u << stage);
     }
     if (!__syncthreads_and(ok)) break;
-    const int lo = (int)(C.e0 & 7), hi = lo + (int)C.nent;
-    bool last;
-    int lrow;
-    float lacc;
-    const int nrows = seg_frame<kSegThreads, kSegK>(frames + stage * kFrame, lo, hi, slice, 0,
-                                                    0.f, rowbuf, wtot, &last, &lrow, &lacc);
-    if (last) rowbuf[pad_row(lrow)] = lacc;  // the chunk's last row
-    __syncthreads();
-    float* part = A.part[C.part] + C.row0;
-    for (int j = threadIdx.x; j < nrows; j += kSegThreads) part[j] = rowbuf[pad_row(j)];
-    __syncthreads();  // the frame, the row buffer and the slice are free again
+    const uint16_t* frame = reinterpret_cast<const uint16_t*>(frames + stage * kFrameBytes);
+    const int lo = (int)(C.e0 & 7u), hi = lo + (int)C.nent;
+    const int m0 = warp * (int)kMini;
+    if (m0 < hi) {  // warp-uniform: this warp's mini-chunk has entries
+      const int j0 = m0 + lane * kSegK;
+      const uint4 q = *reinterpret_cast<const uint4*>(frame + j0);
+      const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+      float val[kSegK];
+      uint32_t fm = 0;
+      #pragma unroll
+      for (int k = 0; k < kSegK; ++k) {
+        const bool in = j0 + k >= lo && j0 + k < hi;
+        const uint32_t e = in ? ((k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu)) : 0u;
+        fm |= (e >> 15) << k;
+        val[k] = in ? to_f(slice[e & kOffMask]) : 0.f;
+      }
+      // warp-level segmented scan: (sum since the lane's last row start, row starts)
+      float v = 0.f;
+      #pragma unroll
+      for (int k = 0; k < kSegK; ++k) v = ((fm >> k) & 1u) ? val[k] : v + val[k];
+      int n = __popc(fm);
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float yv = __shfl_up_sync(kFull, v, o);
+        const int yn = __shfl_up_sync(kFull, n, o);
+        if (lane >= o) {
+          v = n > 0 ? v : yv + v;
+          n += yn;
+        }
+      }
+      const int nrows = __shfl_sync(kFull, n, 31);
+      float ev = __shfl_up_sync(kFull, v, 1);
+      int en = __shfl_up_sync(kFull, n, 1);
+      if (lane == 0) {
+        ev = 0.f;
+        en = 0;
+      }
+      // walk: close the open row at each row start (the mini-chunk's first entry is one)
+      int row = en - 1;
+      float acc = ev;
+      #pragma unroll
+      for (int k = 0; k < kSegK; ++k) {
+        if ((fm >> k) & 1u) {
+          if (row >= 0) rows[pad_row(row)] = acc;
+          ++row;
+          acc = 0.f;
+        }
+        acc += val[k];
+      }
+      const int last = min(hi, m0 + (int)kMini) - 1;   // the mini-chunk's last entry
+      if (j0 <= last && last < j0 + kSegK) rows[pad_row(row)] = acc;
+      __syncwarp();
+      const uint16_t* mrow = reinterpret_cast<const uint16_t*>(frames + stage * kFrameBytes +
+                                                               2 * kFrame);
+      float* part = A.part[C.part] + C.row0 + mrow[warp];
+      for (int j = lane; j < nrows; j += 32) part[j] = rows[pad_row(j)];
+    }
+    __syncthreads();  // the frame, the row buffers and the slice are free again
   }
   if (!ok && threadIdx.x == 0) {
     // copies may still be in flight into shared memory: wait for them (bounded) first
@@ -834,9 +928,9 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
 // ---------------------------------------------------------------------------------------
 // Phase 2: per bin, add each destination's partial sums and update the vertex.
 // ---------------------------------------------------------------------------------------
-constexpr int kMergeThreads = 1024;                    // phase-2 CTA (one per SM)
+constexpr int kMergeThreads = 512;                     // phase-2 CTA (two per SM)
 constexpr int kMergeK = 8;
-constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 8192 staged positions per pass
+constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 4096 staged positions per pass
 constexpr int kMergePass = kMergeFrame - 16;           // positions per pass
 constexpr int kRowBuf2 = kMergeVerts + kMergeVerts / 16 + 32;
 constexpr size_t kMWin = 4ull * kWinMax;
@@ -854,7 +948,7 @@ __device__ __forceinline__ void merge_issue_pos(const uint16_t* plist, uint32_t 
 }
 
 template <class XT, bool SCALED>
-__global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_constant__ SegArgs A) {
+__global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_constant__ SegArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* win = reinterpret_cast<float*>(smem);
   uint16_t* pframe = reinterpret_cast<uint16_t*>(smem + kMWin);
@@ -962,7 +1056,7 @@ __global__ void __launch_bounds__(kMergeThreads, 1) k_pr_merge(const __grid_cons
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = res;
   __syncthreads();
   if (threadIdx.x < 32) {
-    float t = red[threadIdx.x];
+    float t = threadIdx.x < kMergeThreads / 32 ? red[threadIdx.x] : 0.f;
     t = warp_sum(t);
     if (threadIdx.x == 0 && t != 0.f)
       atomicAdd(A.slots + (blockIdx.x % A.nslots), (double)t);
@@ -997,7 +1091,7 @@ graph_status seg_prepare(graph* g, const SegParams& prm, bool* usable) {
   const int log2 = prm.log2 ? prm.log2 : kDefLog2;
   const int ce = prm.chunk ? prm.chunk : kDefChunk;
   const int wb = prm.bin ? prm.bin : kDefBin;
-  if (log2 < 6 || log2 > 15 || ce < 64 || ce > kChunkEntriesMax || wb < 64 || wb > kDefBin) {
+  if (log2 < 6 || log2 > 15 || ce < 64 || ce > kChunkEntriesMax || wb < 64 || wb > kMaxBin) {
     set_error("segmented PageRank parameters out of range (log2 %d, chunk %d, bin %d)", log2,
               ce, wb);
     return GRAPH_EINVAL;
@@ -1083,6 +1177,7 @@ graph_status seg_launch(graph* g, const SegIter& it) {
     A.r[p] = it.r[p];
     A.deg[p] = (const uint32_t*)w->pp[p].deg.p;
     A.ent[p] = (const uint16_t*)w->pp[p].ent.p;
+    A.mrow[p] = (const uint16_t*)w->pp[p].mrow.p;
     A.part[p] = (float*)w->pp[p].part.p;
     A.plist[p] = (const uint16_t*)w->pp[p].plist.p;
     A.runs[p] = (const uint2*)w->pp[p].runs.p;

@@ -125,7 +125,7 @@ def test_segmented_limits_and_bad_arguments(gpu):
     H = gpu.graph_load_csr(g.offsets, g.cols)
     gpu.graph_partition(H, "degree", degree_threshold=64)
     for kw in (dict(seg_log2=5), dict(seg_log2=16), dict(seg_chunk=63), dict(seg_chunk=9000),
-               dict(seg_bin=63), dict(seg_bin=30000)):
+               dict(seg_bin=63), dict(seg_bin=14337)):
         with pytest.raises(_lib.GraphError) as e:
             pr(gpu, H, "fp32", 3, method="segmented", **kw)
         assert e.value.status == _lib.GRAPH_EINVAL
@@ -136,7 +136,7 @@ def test_segmented_limits_and_bad_arguments(gpu):
     r = np.zeros(g.n)
     assert _lib.load().pagerank(H.handle, attr, r.ctypes.data, None) == _lib.GRAPH_EINVAL
     H.free()
-    # a hub adjacent to more than 4,095 segments of 64 sources exceeds the layout: auto
+    # a hub adjacent to more than 2,047 segments of 64 sources exceeds the layout: auto
     # gathers (and is still right), segmented is refused
     g = star_plus(300000, extra_seed=3)
     H = gpu.graph_load_csr(g.offsets, g.cols)

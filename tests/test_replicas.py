@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a threaded test process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, free_port(), out), nprocs=world, join=True)
     assert out[0][0] == out[1][0] == 20.0
