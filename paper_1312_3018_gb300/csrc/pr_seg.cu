@@ -212,18 +212,15 @@ __global__ void k_sg_flags(const uint32_t* sv, uint32_t ne, uint8_t* f) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < ne) f[j] = (j == 0 || sv[j] != sv[j - 1]) ? 1 : 0;
 }
-// Rows also start at the first entry of every chunk and of every mini-chunk: the 256-entry
-// pieces of the chunk's 16-byte-aligned frame that one warp of phase 1 sums on its own.
-__global__ void k_sg_chunkflag(const uint32_t* ce0, const uint32_t* cn, uint32_t nchunk,
-                               uint8_t* f) {
+// Rows also start at the first entry of every chunk.
+__global__ void k_sg_chunkflag(const uint32_t* ce0, uint32_t nchunk, uint8_t* f) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nchunk) return;
-  const uint32_t e0 = ce0[c], e1 = e0 + cn[c], a0 = e0 & ~7u;
-  f[e0] = 1;
-  for (uint32_t pos = a0 + kMini; pos < e1; pos += kMini) f[pos] = 1;
+  if (c < nchunk) f[ce0[c]] = 1;
 }
 
-// mrow[c][w]: rows of chunk c before mini-chunk w (rows of the chunk if w is past its end).
+// mrow[c][w]: rows of chunk c that start before mini-chunk w, the 256-entry piece of the
+// chunk's 16-byte-aligned frame that warp w of phase 1 sums (all the chunk's rows if w is
+// past its end).
 __global__ void k_sg_mrow(const uint32_t* ce0, const uint32_t* cn, const uint32_t* rowid,
                           uint32_t nchunk, uint32_t ne, uint32_t P, uint16_t* mrow) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -491,7 +488,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   GG_TRY(T.get(ne, (void**)&f));
   GG_TRY(T.get(4ull * ne, (void**)&rowid));
   k_sg_flags<<<grid_for(ne, 256), 256, 0, st>>>(sv, ne, f);
-  k_sg_chunkflag<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, dcn, nchunk, f);
+  k_sg_chunkflag<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, nchunk, f);
   GG_CUDA(cudaGetLastError());
   uint32_t nrow = 0;
   GG_TRY(exclusive_scan_u8_to_u32(g, f, rowid, ne, &nrow));
@@ -763,11 +760,15 @@ __device__ __forceinline__ int seg_frame(const uint16_t* frame, int lo, int hi, 
 // Phase 1: partial sum of every (segment, destination) row.
 // ---------------------------------------------------------------------------------------
 // A chunk's entries are staged as a frame of kMiniPerChunk mini-chunks of kMini entries
-// (16-byte aligned). The plan starts a new row at every mini-chunk, so each warp sums one
-// mini-chunk on its own: a warp-level version of the segmented sum above, its rows in a
-// private shared-memory buffer, then one coalesced write of them to the partial sums at the
-// mini-chunk's row offset (staged with the chunk). One CTA barrier per chunk frees the
-// frame and, at a segment change, the slice.
+// (16-byte aligned); warp w sums mini-chunk w on its own: a warp-level version of the
+// segmented sum above, with the rows that start in its mini-chunk in a private shared-memory
+// buffer. A row that runs past the end of a mini-chunk continues in the next ones: each
+// warp also leaves the head of its mini-chunk (the entries before its first row start, or
+// all of them) and whether it has a row start. After one CTA barrier every warp writes its
+// rows to the partial sums (coalesced, at the mini-chunk's staged row offset), adding to its
+// last row the heads of the following mini-chunks in order up to the next row start, so
+// every row keeps one fixed summation order. A second barrier frees the frame and, at a
+// segment change, the slice.
 constexpr int kSegThreads = 1024;                      // phase-1 CTA (one per SM)
 constexpr int kSegK = 8;                               // entries per lane of a mini-chunk
 constexpr int kFrame = kMiniPerChunk * kMini;          // 8192 staged entries
@@ -809,6 +810,8 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
   float* rows = reinterpret_cast<float*>(frames + kSegStages * (size_t)kFrameBytes) +
                 warp * kWarpRows;
   __shared__ uint64_t bar_slice, bar_chunk[kSegStages];
+  __shared__ float head_sh[kMiniPerChunk];    // head of each mini-chunk (see above)
+  __shared__ int starts_sh[kMiniPerChunk];    // the mini-chunk has a row start
   const uint32_t c0 = A.cta0[blockIdx.x], c1 = A.cta0[blockIdx.x + 1];
   if (c0 >= c1) return;
   uint32_t phases = 0;       // bit s: parity of bar_chunk[s]; bit 4: bar_slice
@@ -861,6 +864,7 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
     const uint16_t* frame = reinterpret_cast<const uint16_t*>(frames + stage * kFrameBytes);
     const int lo = (int)(C.e0 & 7u), hi = lo + (int)C.nent;
     const int m0 = warp * (int)kMini;
+    int nrows = 0;
     if (m0 < hi) {  // warp-uniform: this warp's mini-chunk has entries
       const int j0 = m0 + lane * kSegK;
       const uint4 q = *reinterpret_cast<const uint4*>(frame + j0);
@@ -888,32 +892,51 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
           n += yn;
         }
       }
-      const int nrows = __shfl_sync(kFull, n, 31);
+      nrows = __shfl_sync(kFull, n, 31);
       float ev = __shfl_up_sync(kFull, v, 1);
       int en = __shfl_up_sync(kFull, n, 1);
       if (lane == 0) {
         ev = 0.f;
         en = 0;
       }
-      // walk: close the open row at each row start (the mini-chunk's first entry is one)
+      // walk: close the open row at each row start; row -1 is the head (a row of an
+      // earlier mini-chunk)
       int row = en - 1;
       float acc = ev;
       #pragma unroll
       for (int k = 0; k < kSegK; ++k) {
         if ((fm >> k) & 1u) {
           if (row >= 0) rows[pad_row(row)] = acc;
+          else head_sh[warp] = acc;
           ++row;
           acc = 0.f;
         }
         acc += val[k];
       }
       const int last = min(hi, m0 + (int)kMini) - 1;   // the mini-chunk's last entry
-      if (j0 <= last && last < j0 + kSegK) rows[pad_row(row)] = acc;
-      __syncwarp();
+      if (j0 <= last && last < j0 + kSegK) {
+        if (row >= 0) rows[pad_row(row)] = acc;
+        else head_sh[warp] = acc;                      // no row start at all
+      }
+      if (lane == 0) starts_sh[warp] = nrows > 0;
+    } else if (lane == 0) {
+      starts_sh[warp] = 1;   // past the chunk's end: ends every carry
+      head_sh[warp] = 0.f;
+    }
+    __syncthreads();
+    if (nrows > 0) {
       const uint16_t* mrow = reinterpret_cast<const uint16_t*>(frames + stage * kFrameBytes +
                                                                2 * kFrame);
       float* part = A.part[C.part] + C.row0 + mrow[warp];
-      for (int j = lane; j < nrows; j += 32) part[j] = rows[pad_row(j)];
+      for (int j = lane; j < nrows; j += 32) {
+        float x = rows[pad_row(j)];
+        if (j == nrows - 1)   // the row open at the end continues in the next mini-chunks
+          for (int w2 = warp + 1; w2 < (int)kMiniPerChunk; ++w2) {
+            x += head_sh[w2];
+            if (starts_sh[w2]) break;
+          }
+        part[j] = x;
+      }
     }
     __syncthreads();  // the frame, the row buffers and the slice are free again
   }
