@@ -55,7 +55,7 @@ constexpr int kDefLog2 = 15, kDefChunk = 8176, kDefBin = 12288;
 constexpr int kMaxBin = (int)(kWinMax - kMaxPartials - 1);   // 14336
 
 struct SegChunk {   // 32 bytes
-  uint32_t e0;      // first entry in the partition's entry array
+  uint32_t e0;      // first entry in the partition's packed entry array (multiple of 8)
   uint32_t nent;    // entries (<= kChunkEntriesMax)
   uint32_t row0;    // first row (index into the partition's partial sums)
   uint32_t src0;    // first source id of the segment (in its space)
@@ -219,13 +219,12 @@ __global__ void k_sg_chunkflag(const uint32_t* ce0, uint32_t nchunk, uint8_t* f)
 }
 
 // mrow[c][w]: rows of chunk c that start before mini-chunk w, the 256-entry piece of the
-// chunk's 16-byte-aligned frame that warp w of phase 1 sums (all the chunk's rows if w is
-// past its end).
+// chunk that warp w of phase 1 sums (all the chunk's rows if w is past its end).
 __global__ void k_sg_mrow(const uint32_t* ce0, const uint32_t* cn, const uint32_t* rowid,
                           uint32_t nchunk, uint32_t ne, uint32_t P, uint16_t* mrow) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nchunk) return;
-  const uint32_t e0 = ce0[c], e1 = e0 + cn[c], a0 = e0 & ~7u;
+  const uint32_t e0 = ce0[c], e1 = e0 + cn[c], a0 = e0;
   const uint32_t r0 = rowid[e0];
   const uint32_t rend = e1 < ne ? rowid[e1] : P;
   for (uint32_t w = 0; w < kMiniPerChunk; ++w) {
@@ -235,13 +234,22 @@ __global__ void k_sg_mrow(const uint32_t* ce0, const uint32_t* cn, const uint32_
   }
 }
 
-// Entry words, and the destination of every row.
-__global__ void k_sg_ent(const uint32_t* sv, const uint16_t* sidx, const uint8_t* f,
-                         const uint32_t* rowid, uint32_t ne, uint16_t* ent, uint32_t* rowv) {
+// The destination of every row.
+__global__ void k_sg_rowv(const uint32_t* sv, const uint8_t* f, const uint32_t* rowid,
+                          uint32_t ne, uint32_t* rowv) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ne) return;
-  ent[j] = (uint16_t)(sidx[j] | (f[j] ? kRowStart : 0));
-  if (f[j]) rowv[rowid[j]] = sv[j];
+  if (j < ne && f[j]) rowv[rowid[j]] = sv[j];
+}
+
+// Entry words of chunk c at its 16-byte-aligned place pe0[c] (one warp per chunk).
+__global__ void k_sg_entpack(const uint16_t* sidx, const uint8_t* f, const uint32_t* ce0,
+                             const uint32_t* cn, const uint32_t* pe0, uint32_t nchunk,
+                             uint16_t* ent) {
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= nchunk) return;
+  const uint32_t e0 = ce0[c], n = cn[c], o = pe0[c];
+  for (uint32_t i = lane_id(); i < n; i += 32)
+    ent[o + i] = (uint16_t)(sidx[e0 + i] | (f[e0 + i] ? kRowStart : 0));
 }
 
 __global__ void k_sg_chunkrow(const uint32_t* ce0, const uint32_t* rowid, uint32_t nchunk,
@@ -494,12 +502,27 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   GG_TRY(exclusive_scan_u8_to_u32(g, f, rowid, ne, &nrow));
   if (nrow >= 0x7FFFFFF0u) return GRAPH_OK;
   SP.P = nrow;
-  GG_TRY(dalloc(g, SP.ent, 2ull * ne + 64));
+  // chunks start at 16-byte-aligned entry positions (the frame of phase 1 begins exactly at
+  // a chunk's first entry)
+  std::vector<uint32_t> pe0(nchunk);
+  uint64_t packed = 0;
+  for (uint32_t c = 0; c < nchunk; ++c) {
+    pe0[c] = (uint32_t)packed;
+    packed += (cn[c] + 7) & ~7u;
+  }
+  if (packed >= 0xFFFFFFF0ull) return GRAPH_OK;
+  uint32_t* dpe0;
+  GG_TRY(T.get(4ull * nchunk, (void**)&dpe0));
+  GG_TRY(to_dev(g, dpe0, pe0));
+  GG_TRY(dalloc(g, SP.ent, 2ull * packed + 64));
+  GG_CUDA(cudaMemsetAsync(SP.ent.p, 0, 2ull * packed + 64, st));
   uint32_t *rowv, *rowseg;
   GG_TRY(T.get(4ull * nrow, (void**)&rowv));
   GG_TRY(T.get(4ull * nrow, (void**)&rowseg));
-  k_sg_ent<<<grid_for(ne, 256), 256, 0, st>>>(sv, sidx, f, rowid, ne, (uint16_t*)SP.ent.p, rowv);
-  GG_CUDA(cudaMemsetAsync((uint16_t*)SP.ent.p + ne, 0, 64, st));
+  k_sg_rowv<<<grid_for(ne, 256), 256, 0, st>>>(sv, f, rowid, ne, rowv);
+  k_sg_entpack<<<grid_for(32ull * nchunk, 256), 256, 0, st>>>(sidx, f, dce0, dcn, dpe0, nchunk,
+                                                              (uint16_t*)SP.ent.p);
+  GG_CUDA(cudaGetLastError());
   k_sg_chunkrow<<<grid_for(nchunk, 256), 256, 0, st>>>(dce0, rowid, nchunk, dcrow);
   GG_TRY(dalloc(g, SP.mrow, 2ull * kMiniPerChunk * nchunk + 64));
   k_sg_mrow<<<grid_for(nchunk, 128), 128, 0, st>>>(dce0, dcn, rowid, nchunk, ne, nrow,
@@ -595,7 +618,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
   for (uint32_t c = 0; c < nchunk; ++c) {
     SegChunk& C = H.chunks[c];
     const uint32_t s = cseg[c];
-    C.e0 = ce0[c];
+    C.e0 = pe0[c];
     C.nent = cn[c];
     C.row0 = crow[c];
     C.cl = c;
@@ -869,16 +892,38 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
       const int j0 = m0 + lane * kSegK;
       const uint4 q = *reinterpret_cast<const uint4*>(frame + j0);
       const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
-      float val[kSegK];
-      uint32_t fm = 0;
-      #pragma unroll
-      for (int k = 0; k < kSegK; ++k) {
-        const bool in = j0 + k >= lo && j0 + k < hi;
-        const uint32_t e = in ? ((k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu)) : 0u;
-        fm |= (e >> 15) << k;
-        val[k] = in ? to_f(slice[e & kOffMask]) : 0.f;
+      const bool full = m0 + (int)kMini <= hi;
+      const uint32_t fl_or = (q.x | q.y | q.z | q.w) & 0x80008000u;
+      const uint32_t fl_and = q.x & q.y & q.z & q.w & 0x80008000u;
+      if (full && !__any_sync(kFull, fl_or != 0)) {
+        // no row start (long rows): the whole mini-chunk continues the open row
+        float sum = 0.f;
+        #pragma unroll
+        for (int k = 0; k < kSegK; ++k)
+          sum += to_f(slice[(k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu)]);
+        sum = warp_sum(sum);
+        if (lane == 0) {
+          head_sh[warp] = sum;
+          starts_sh[warp] = 0;
+        }
+        goto written;
       }
-      // warp-level segmented scan: (sum since the lane's last row start, row starts)
+      if (full && __all_sync(kFull, fl_and == 0x80008000u)) {
+        // every entry starts a row of its own: the rows are the gathered values
+        #pragma unroll
+        for (int k = 0; k < kSegK; ++k) {
+          const uint32_t e = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu);
+          rows[pad_row(lane * kSegK + k)] = to_f(slice[e & kOffMask]);
+        }
+        nrows = (int)kMini;
+        if (lane == 0) {
+          head_sh[warp] = 0.f;
+          starts_sh[warp] = 1;
+        }
+        goto written;
+      }
+      float val[kSegK];
+      uint32_t fm = 0;      // warp-level segmented scan: (sum since the lane's last row start, row starts)
       float v = 0.f;
       #pragma unroll
       for (int k = 0; k < kSegK; ++k) v = ((fm >> k) & 1u) ? val[k] : v + val[k];
@@ -923,6 +968,7 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
       starts_sh[warp] = 1;   // past the chunk's end: ends every carry
       head_sh[warp] = 0.f;
     }
+  written:
     __syncthreads();
     if (nrows > 0) {
       const uint16_t* mrow = reinterpret_cast<const uint16_t*>(frames + stage * kFrameBytes +
