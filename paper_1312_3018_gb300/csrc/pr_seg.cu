@@ -923,7 +923,15 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
         goto written;
       }
       float val[kSegK];
-      uint32_t fm = 0;      // warp-level segmented scan: (sum since the lane's last row start, row starts)
+      uint32_t fm = 0;
+      #pragma unroll
+      for (int k = 0; k < kSegK; ++k) {
+        const bool in = j0 + k >= lo && j0 + k < hi;
+        const uint32_t e = in ? ((k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu)) : 0u;
+        fm |= (e >> 15) << k;
+        val[k] = in ? to_f(slice[e & kOffMask]) : 0.f;
+      }
+      // warp-level segmented scan: (sum since the lane's last row start, row starts)
       float v = 0.f;
       #pragma unroll
       for (int k = 0; k < kSegK; ++k) v = ((fm >> k) & 1u) ? val[k] : v + val[k];
