@@ -352,17 +352,20 @@ __global__ void k_sg_pos(const uint32_t* rowv, const uint32_t* rowseg, const uin
 
 // Each destination's positions in ascending order (= segment order), the first marked
 // (one warp per vertex; rank by counting, positions of one vertex are distinct).
-__global__ void k_sg_plist(const uint32_t* pstart, uint32_t nz, const uint16_t* tmp,
-                           uint16_t* plist) {
+// Position lists are stored bin by bin, each bin's list starting at a multiple of 8
+// entries: destination v's list goes to pstart[v] + shift[bin of v].
+__global__ void k_sg_plist(const uint32_t* pstart, uint32_t nz, uint32_t wb, const uint16_t* tmp,
+                           const uint32_t* shift, uint16_t* plist) {
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t v = w0; v < nz; v += nw) {
     const uint32_t a = pstart[v], L = pstart[v + 1] - a;
+    const uint32_t o = a + shift[bin_key(pstart, v, wb)];
     for (uint32_t i = lane_id(); i < L; i += 32) {
       const uint16_t wi = tmp[a + i];
       uint32_t rank = 0;
       for (uint32_t j = 0; j < L; ++j) rank += tmp[a + j] < wi;
-      plist[a + rank] = (uint16_t)(wi | (rank == 0 ? kRowStart : 0));
+      plist[o + rank] = (uint16_t)(wi | (rank == 0 ? kRowStart : 0));
     }
   }
 }
@@ -598,17 +601,30 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
     GG_TRY(to_host(g, hbinpos, bpos, nbin + 1));
   }
 
-  // Position lists.
-  uint32_t* cur;
+  // Position lists, each bin's starting at a multiple of 8 entries.
+  std::vector<uint32_t> hppos(nbin + 1), hshift(nbin + 1, 0);
+  {
+    uint64_t acc = 0;
+    for (uint32_t k = 0; k < nbin; ++k) {
+      hppos[k] = (uint32_t)acc;
+      hshift[k] = hppos[k] - hbinpos[k];   // modulo 2^32
+      acc += ((uint64_t)(hbinpos[k + 1] - hbinpos[k]) + 7) & ~7ull;
+    }
+    if (acc >= 0xFFFFFFF0ull) return GRAPH_OK;
+    hppos[nbin] = (uint32_t)acc;
+  }
+  uint32_t *cur, *dshift;
   uint16_t* tmp;
   GG_TRY(T.get(4ull * nv, (void**)&cur));
   GG_TRY(T.get(2ull * nrow, (void**)&tmp));
-  GG_TRY(dalloc(g, SP.plist, 2ull * nrow + 64));
+  GG_TRY(T.get(4ull * (nbin + 1), (void**)&dshift));
+  GG_TRY(to_dev(g, dshift, hshift));
+  GG_TRY(dalloc(g, SP.plist, 2ull * hppos[nbin] + 64));
+  GG_CUDA(cudaMemsetAsync(SP.plist.p, 0, 2ull * hppos[nbin] + 64, st));
   GG_CUDA(cudaMemsetAsync(cur, 0, 4ull * nv, st));
   k_sg_pos<<<grid_for(nrow, 256), 256, 0, st>>>(rowv, rowseg, pstart, woff, rs, nrow, S, wb,
                                                 cur, tmp);
-  k_sg_plist<<<gridw, 256, 0, st>>>(pstart, nz, tmp, (uint16_t*)SP.plist.p);
-  GG_CUDA(cudaMemsetAsync((uint16_t*)SP.plist.p + nrow, 0, 64, st));
+  k_sg_plist<<<gridw, 256, 0, st>>>(pstart, nz, wb, tmp, dshift, (uint16_t*)SP.plist.p);
   GG_CUDA(cudaGetLastError());
   GG_TRY(dalloc(g, SP.part, 4ull * nrow + 64));
   GG_CUDA(cudaMemsetAsync(SP.part.p, 0, 4ull * nrow + 64, st));
@@ -637,7 +653,7 @@ graph_status build_part(graph* g, int p, int log2, uint32_t ce, uint32_t wb, Seg
     B.v1 = hbinv0[k + 1];
     B.run0 = hrunoff[k];
     B.run1 = hrunoff[k + 1];
-    B.pos0 = hbinpos[k];
+    B.pos0 = hppos[k];
     B.npos = hbinpos[k + 1] - hbinpos[k];
     B.wgran = hwgran[k];
     B.part = (uint32_t)p;
@@ -662,122 +678,24 @@ int sm_count(graph* g) {
 }
 
 // ---------------------------------------------------------------------------------------
-// The deterministic segmented sum shared by both phases.
+// The deterministic segmented sum used by both phases.
 // ---------------------------------------------------------------------------------------
-// A frame of staged 2-byte entries (table offset | row-start bit) is split over the CTA's
-// threads, kK consecutive entries each. A row-start bit begins a new row. Each thread
-// summarises its entries as (sum since its last row start, or of all of them; number of
-// row starts); an exclusive scan of these summaries over the threads, in fixed order, gives
-// every thread the running value of the row open at its first entry. Each row's value
-// therefore has one fixed summation tree, whatever the timing. Completed rows go to a
-// shared-memory row buffer at index pad(row) (one skipped slot every 16 rows, so that
-// threads closing rows 16 apart write different banks).
-struct Scan {
-  float v;  // running sum of the open row
-  int n;    // row starts
-};
-
-__device__ __forceinline__ Scan scan_op(const Scan& a, const Scan& b) {
-  return Scan{b.n > 0 ? b.v : a.v + b.v, a.n + b.n};
-}
-
+// Staged 2-byte entries (table offset | row-start bit) are split into mini-chunks of kMini
+// entries, one per warp, 8 consecutive entries per lane. A row-start bit begins a new row.
+// A warp sums its mini-chunk on its own: warp-uniform fast paths when the mini-chunk has no
+// row start (one sum) or a row start at every entry (the rows are the gathered values);
+// otherwise each lane summarises its entries as (sum since its last row start, or of all of
+// them; number of row starts), an exclusive warp scan of these summaries gives each lane
+// the running value of the row open at its first entry, and a walk closes rows at row
+// starts. Completed rows go to a shared-memory row buffer at index pad_row(row) (one
+// skipped slot every 16 rows, so that lanes closing rows 8 or 16 apart write different
+// banks); the entries before a mini-chunk's first row start (its head) continue a row of an
+// earlier mini-chunk and are added to it afterwards, in mini-chunk order. Every row's value
+// therefore has one fixed summation order, whatever the timing.
 __device__ __forceinline__ int pad_row(int r) { return r + (r >> 4); }
-
-template <int NT>
-__device__ __forceinline__ Scan block_seg_scan(Scan x, Scan* wtot, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Scan inc = x;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    Scan y;
-    y.v = __shfl_up_sync(kFull, inc.v, o);
-    y.n = __shfl_up_sync(kFull, inc.n, o);
-    if (lane >= o) inc = scan_op(y, inc);
-  }
-  if (lane == 31) wtot[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    constexpr int NW = NT / 32;
-    Scan t = lane < NW ? wtot[lane] : Scan{0.f, 0};
-    #pragma unroll
-    for (int o = 1; o < NW; o <<= 1) {
-      Scan y;
-      y.v = __shfl_up_sync(kFull, t.v, o);
-      y.n = __shfl_up_sync(kFull, t.n, o);
-      if (lane >= o) t = scan_op(y, t);
-    }
-    if (lane < NW) wtot[lane] = t;
-  }
-  __syncthreads();
-  Scan prev;
-  prev.v = __shfl_up_sync(kFull, inc.v, 1);
-  prev.n = __shfl_up_sync(kFull, inc.n, 1);
-  if (lane == 0) prev = Scan{0.f, 0};
-  Scan excl = prev;
-  if (warp > 0) excl = scan_op(wtot[warp - 1], prev);
-  *total = wtot[NT / 32 - 1].n;
-  __syncthreads();  // wtot is reused by the next call
-  return excl;
-}
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
-
-// Sums frame entries [lo, hi) (frame indices) with table values. Rows are numbered from
-// rb - 1 (the row open before the frame, continued from `carry`; no such row when rb = 0)
-// upward; every row closed inside the frame goes to rowbuf[pad_row(row)]. Returns the
-// number of row starts in the frame; the thread holding entry hi - 1 gets *last = true,
-// with *last_row / *last_acc the row still open at the frame's end and its running sum.
-template <int NT, int K, class TT>
-__device__ __forceinline__ int seg_frame(const uint16_t* frame, int lo, int hi, const TT* table,
-                                         int rb, float carry, float* rowbuf, Scan* wtot,
-                                         bool* last, int* last_row, float* last_acc) {
-  static_assert(K == 8, "one 16-byte load per thread");
-  const int j0 = threadIdx.x * K;
-  const uint4 q = *reinterpret_cast<const uint4*>(frame + j0);
-  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-  float val[K];
-  uint32_t fm = 0;
-  if (j0 >= lo && j0 + K <= hi) {
-    #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint32_t e = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
-      fm |= (e >> 15) << k;
-      val[k] = to_f(table[e & kOffMask]);
-    }
-  } else {
-    #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool in = j0 + k >= lo && j0 + k < hi;
-      const uint32_t e = in ? ((k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu)) : 0u;
-      fm |= (e >> 15) << k;
-      val[k] = in ? to_f(table[e & kOffMask]) : 0.f;
-    }
-  }
-  Scan mine;
-  mine.n = __popc(fm);
-  float a = 0.f;
-  #pragma unroll
-  for (int k = 0; k < K; ++k) a = ((fm >> k) & 1u) ? val[k] : a + val[k];
-  mine.v = a;
-  int total;
-  const Scan ex = block_seg_scan<NT>(mine, wtot, &total);
-  int row = rb + ex.n - 1;
-  float acc = ex.n > 0 ? ex.v : carry + ex.v;
-  #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if ((fm >> k) & 1u) {
-      if (row >= 0) rowbuf[pad_row(row)] = acc;
-      ++row;
-      acc = 0.f;
-    }
-    acc += val[k];
-  }
-  *last = j0 <= hi - 1 && hi - 1 < j0 + K;
-  *last_row = row;
-  *last_acc = acc;
-  return total;
-}
 
 // ---------------------------------------------------------------------------------------
 // Phase 1: partial sum of every (segment, destination) row.
@@ -1008,7 +926,7 @@ k_pr_seg(const __grid_constant__ SegArgs A, int log2) {
 constexpr int kMergeThreads = 512;                     // phase-2 CTA (two per SM)
 constexpr int kMergeK = 8;
 constexpr int kMergeFrame = kMergeThreads * kMergeK;   // 4096 staged positions per pass
-constexpr int kMergePass = kMergeFrame - 16;           // positions per pass
+constexpr int kMergePass = kMergeFrame;                // positions per pass (bins start aligned)
 constexpr int kRowBuf2 = kMergeVerts + kMergeVerts / 16 + 32;
 constexpr size_t kMWin = 4ull * kWinMax;
 constexpr size_t kMPos = 2ull * kMergeFrame;                 // one position frame
@@ -1024,6 +942,10 @@ __device__ __forceinline__ void merge_issue_pos(const uint16_t* plist, uint32_t 
   bulk_g2s_stream(frame, plist + a0, bytes, bar, l2_evict_first_policy());
 }
 
+// One pass of a bin: kMergeFrame positions, one mini-chunk of kMini per warp, summed like
+// phase 1 (warp-uniform fast paths, else a warp-level segmented sum); rows are the bin's
+// vertices. A row that runs past its mini-chunk (or pass) is finished by thread 0, which
+// adds the following mini-chunks' heads to it in order after the pass.
 template <class XT, bool SCALED>
 __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_constant__ SegArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1032,14 +954,16 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_cons
   uint32_t* sdeg = reinterpret_cast<uint32_t*>(smem + kMWin + 2 * kMPos);
   float* sr = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMDeg);
   float* rowbuf = reinterpret_cast<float*>(smem + kMWin + 2 * kMPos + kMDeg + kMRank);
+  constexpr int NW = kMergeThreads / 32;
   __shared__ uint64_t bar_w, bar_p[2];
-  __shared__ Scan wtot[kMergeThreads / 32];
-  __shared__ float carry_sh;
-  __shared__ int rows_sh;
-  __shared__ float red[kMergeThreads / 32];
+  __shared__ int cnt_sh[NW], starts_sh[NW], last_sh[NW];
+  __shared__ float head_sh[NW];
+  __shared__ int rows_sh, pending_sh;
+  __shared__ float red[NW];
   const SegBin B = A.bins[blockIdx.x];
   if (B.v0 >= B.v1) return;
   const int p = (int)B.part;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t q0 = B.v0 & ~3u;
   const uint32_t npass = (B.npos + kMergePass - 1) / kMergePass;
   if (threadIdx.x == 0) {
@@ -1053,8 +977,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_cons
     bulk_g2s_stream(sdeg, A.deg[p] + q0, vbytes, &bar_w, pol);
     bulk_g2s_stream(sr, reinterpret_cast<const float*>(A.r[p]) + q0, vbytes, &bar_w, pol);
     merge_issue_pos(A.plist[p], B.pos0, min(B.npos, (uint32_t)kMergePass), pframe, &bar_p[0]);
-    carry_sh = 0.f;
     rows_sh = 0;
+    pending_sh = -1;
   }
   __syncthreads();
   {
@@ -1087,23 +1011,105 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_cons
     }
     ok = okp;
     if (!__syncthreads_and(ok)) break;
-    const int lo = (int)(start & 7u), hi = lo + (int)cnt;
-    const int rb = rows_sh;
-    bool last;
-    int lrow;
-    float lacc;
-    const int nflags = seg_frame<kMergeThreads, kMergeK>(pframe + b * kMergeFrame, lo, hi, win,
-                                                         rb, carry_sh, rowbuf, wtot, &last,
-                                                         &lrow, &lacc);
-    // every thread has read rows_sh and carry_sh (barriers inside seg_frame)
-    if (last) {
-      if (q + 1 == npass) rowbuf[pad_row(lrow)] = lacc;
-      else {
-        carry_sh = lacc;
-        rows_sh = rb + nflags;
+    const uint16_t* frame = pframe + b * kMergeFrame;
+    const int hi = (int)cnt;             // frames start at multiples of 8 entries
+    const int m0 = warp * (int)kMini;
+    const int j0 = m0 + lane * kMergeK;
+    uint4 qv = make_uint4(0, 0, 0, 0);
+    if (m0 < hi) qv = *reinterpret_cast<const uint4*>(frame + j0);
+    const uint32_t wd[4] = {qv.x, qv.y, qv.z, qv.w};
+    uint32_t fm = 0;
+    #pragma unroll
+    for (int k = 0; k < kMergeK; ++k) {
+      const uint32_t e = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu);
+      if (j0 + k < hi) fm |= (e >> 15) << k;
+    }
+    const int nflag = __reduce_add_sync(kFull, __popc(fm));
+    if (lane == 0) cnt_sh[warp] = nflag;
+    __syncthreads();
+    int rb = rows_sh;   // rows of the bin that start before this warp's mini-chunk
+    for (int w2 = 0; w2 < warp; ++w2) rb += cnt_sh[w2];
+    if (m0 < hi) {
+      const bool full = m0 + (int)kMini <= hi;
+      if (full && nflag == 0) {
+        float sum = 0.f;
+        #pragma unroll
+        for (int k = 0; k < kMergeK; ++k)
+          sum += win[(k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu)];
+        sum = warp_sum(sum);
+        if (lane == 0) head_sh[warp] = sum;
+      } else if (full && nflag == (int)kMini) {
+        #pragma unroll
+        for (int k = 0; k < kMergeK; ++k) {
+          const uint32_t e = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu);
+          rowbuf[pad_row(rb + lane * kMergeK + k)] = win[e & kOffMask];
+        }
+        if (lane == 0) head_sh[warp] = 0.f;
+      } else {
+        float val[kMergeK];
+        #pragma unroll
+        for (int k = 0; k < kMergeK; ++k) {
+          const uint32_t e = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xFFFFu);
+          val[k] = j0 + k < hi ? win[e & kOffMask] : 0.f;
+        }
+        float v = 0.f;
+        #pragma unroll
+        for (int k = 0; k < kMergeK; ++k) v = ((fm >> k) & 1u) ? val[k] : v + val[k];
+        int n = __popc(fm);
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float yv = __shfl_up_sync(kFull, v, o);
+          const int yn = __shfl_up_sync(kFull, n, o);
+          if (lane >= o) {
+            v = n > 0 ? v : yv + v;
+            n += yn;
+          }
+        }
+        float ev = __shfl_up_sync(kFull, v, 1);
+        int en = __shfl_up_sync(kFull, n, 1);
+        if (lane == 0) {
+          ev = 0.f;
+          en = 0;
+        }
+        int row = en - 1;   // local row; -1: the head
+        float acc = ev;
+        #pragma unroll
+        for (int k = 0; k < kMergeK; ++k) {
+          if ((fm >> k) & 1u) {
+            if (row >= 0) rowbuf[pad_row(rb + row)] = acc;
+            else head_sh[warp] = acc;
+            ++row;
+            acc = 0.f;
+          }
+          acc += val[k];
+        }
+        const int last = min(hi, m0 + (int)kMini) - 1;
+        if (j0 <= last && last < j0 + kMergeK) {
+          if (row >= 0) rowbuf[pad_row(rb + row)] = acc;
+          else head_sh[warp] = acc;
+        }
       }
+      if (lane == 0) {
+        starts_sh[warp] = nflag > 0;
+        last_sh[warp] = rb + nflag - 1;
+      }
+    } else if (lane == 0) {   // past the pass's end: contributes nothing
+      head_sh[warp] = 0.f;
+      starts_sh[warp] = 0;
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+      // heads continue the row open before their mini-chunk, in order
+      int pending = pending_sh, total = 0;
+      for (int w2 = 0; w2 < NW; ++w2) {
+        if (pending >= 0) rowbuf[pad_row(pending)] += head_sh[w2];
+        if (starts_sh[w2]) pending = last_sh[w2];
+        total += cnt_sh[w2];
+      }
+      pending_sh = pending;
+      rows_sh += total;
+    }
+    // the next pass reads rows_sh / pending_sh after its first barrier
   }
   if (!ok) {
     // copies may still be in flight into shared memory: wait for them (bounded) first
@@ -1114,6 +1120,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_cons
     }
     return;
   }
+  __syncthreads();
   // Vertex updates (Figure 14), one thread per vertex of the bin.
   const float base = reinterpret_cast<const float*>(A.scal + 4)[0];
   float res = 0.f;
@@ -1130,10 +1137,10 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_pr_merge(const __grid_cons
     res += fabsf(rn - ro);
   }
   res = warp_sum(res);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = res;
+  if (lane == 0) red[warp] = res;
   __syncthreads();
   if (threadIdx.x < 32) {
-    float t = threadIdx.x < kMergeThreads / 32 ? red[threadIdx.x] : 0.f;
+    float t = threadIdx.x < NW ? red[threadIdx.x] : 0.f;
     t = warp_sum(t);
     if (threadIdx.x == 0 && t != 0.f)
       atomicAdd(A.slots + (blockIdx.x % A.nslots), (double)t);
