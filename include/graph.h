@@ -325,8 +325,7 @@ graph_status connected_components(graph_t* g, uint32_t* labels, const cc_attr* a
  * (tol <= 0: never).
  * How the neighbour sum is formed (method; the result is the same sum up to FP32 rounding
  * order):
- *   GRAPH_PR_AUTO       SEGMENTED for FP32 and FP16 when the graph fits its limits, else
- *                       GATHER
+ *   GRAPH_PR_AUTO       GATHER (measured faster than SEGMENTED on RMAT graphs here)
  *   GRAPH_PR_GATHER     every edge entry gathers its neighbour's contribution from global
  *                       memory (per-vertex work items by degree class)
  *   GRAPH_PR_SEGMENTED  FP32 / FP16 only: the source ids of each partition are cut into
@@ -339,7 +338,7 @@ graph_status connected_components(graph_t* g, uint32_t* labels, const cc_attr* a
  *                       until the next partition, graph_free or a call with other seg_*
  *                       values. Limits: at most 2,047 partial sums per vertex, at most 2,378
  *                       segments per partition and fewer than 2^31 edge entries per
- *                       partition; GRAPH_PR_SEGMENTED on a graph beyond them returns EINVAL.
+ *                       partition; a graph beyond them returns EINVAL.
  *   seg_log2   6 ... 15 (0: 15), seg_chunk 64 ... 8176 entries per first-pass chunk (0:
  *              8176), seg_bin 64 ... 14336 partial sums per second-pass bin (0: 12288, and
  *              at most 14336 - 6 * segments of the partition); ignored by GATHER.

@@ -304,8 +304,8 @@ def pagerank(g: Graph, *, damping: float = 0.85, max_iter: int = 20, tol: float 
              timing: bool = False, method: str = "auto", seg_log2: int = 0,
              seg_chunk: int = 0, seg_bin: int = 0):
     """FP64 ranks in global vertex order, and stats (residual = last L1 change).
-    method: 'auto' (segmented for FP32 / FP16 when the graph fits), 'gather' or
-    'segmented'; seg_* are the segmented layout's parameters (0 = default)."""
+    method: 'auto' (= 'gather'), 'gather' or 'segmented' (FP32 / FP16); seg_* are the
+    segmented layout's parameters (0 = default)."""
     torch = _torch()
     if ranks is None:
         ranks = (torch.empty(g.n, dtype=torch.float64, device="cuda") if out == "device"

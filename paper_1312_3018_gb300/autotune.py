@@ -1,4 +1,5 @@
-"""Choice of the hub/leaf degree threshold T for one resident graph.
+"""Choice of the hub/leaf degree threshold T and of the kernels' run-time tile and switch
+parameters for one resident graph.
 
 Section 6.3 shows that the partition strategy and the share of edges placed on each side
 decide performance; on one GPU the equivalent knob is the degree threshold T of the HIGH
@@ -8,7 +9,13 @@ iterations with the library's own CUDA-event statistics, scores a candidate by t
 one benchmark step (BFS + SSSP + iters_per_step PageRank iterations), and leaves the graph
 partitioned with the winner. Results are cached in a JSON file keyed by the graph's
 signature (n, m and the partition sizes the candidates produce), so a second run on the
-same graph only re-partitions.
+same graph only re-partitions; each entry records the device it was measured on.
+
+The other tuners time the run-time parameters of the kernels on the graph as partitioned:
+tune_pagerank picks the neighbour-sum method (per-edge gather, or the segmented layout
+with its segment, chunk and bin sizes), tune_bfs the direction-switch constants (alpha,
+beta) of the direction-optimised BFS. Both time with the library's CUDA-event statistics
+and keep the fastest candidate.
 """
 from __future__ import annotations
 
@@ -29,12 +36,44 @@ def _signature(G, H, candidates):
     return {"n": H.n, "m": H.m, "parts": parts}
 
 
+def _device_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:
+        return "unknown"
+
+
+def _step_ms(G, H, source, weighted, pr_iters, iters_per_step):
+    G.bfs(H, source)  # warm-up: allocates the workspaces
+    _, _, sb = G.bfs(H, source, timing=True)
+    total = sb["ms_total"]
+    if weighted:
+        G.sssp(H, source)
+        _, ss = G.sssp(H, source, timing=True)
+        total += ss["ms_total"]
+    G.pagerank(H, max_iter=1)
+    _, sp = G.pagerank(H, max_iter=pr_iters, timing=True)
+    total += (sp["ms_compute"] + sp["ms_exchange"]) / pr_iters * iters_per_step
+    return total
+
+
 def autotune_threshold(G, H, source: int, *, weighted: bool, candidates=DEFAULT_CANDIDATES,
                        pr_iters: int = 3, iters_per_step: int = 20, cache: str | None = None,
-                       retune: bool = False):
-    """Returns {"T": best, "ms": {T: step estimate}, "cached": bool}; H ends partitioned at
-    the best T. G is the paper_1312_3018_gb300 module (passed in to avoid an import cycle).
-    retune: time the candidates even when the cache holds this graph (and update it)."""
+                       retune: bool = False, report=()):
+    """Returns {"T": best, "ms": {T: step estimate}, "cached": bool, "measured_on": device,
+    "reported": {T: step estimate}}; H ends partitioned at the best T. G is the
+    paper_1312_3018_gb300 module (passed in to avoid an import cycle). retune: time the
+    candidates even when the cache holds this graph (and update it). report: thresholds
+    timed and returned beside the choice but never chosen (e.g. 1 << 31, a single
+    partition), also when the choice comes from the cache."""
+    def extra():
+        out = {}
+        for T in report:
+            G.graph_partition(H, "degree", degree_threshold=T)
+            out[str(T)] = _step_ms(G, H, source, weighted, pr_iters, iters_per_step)
+        return out
+
     sig = _signature(G, H, candidates)
     key = json.dumps(sig, sort_keys=True)
     if cache and os.path.exists(cache) and not retune:
@@ -43,27 +82,22 @@ def autotune_threshold(G, H, source: int, *, weighted: bool, candidates=DEFAULT_
                 table = json.load(f)
             if key in table:
                 best = table[key]["T"]
+                rep = extra()
                 G.graph_partition(H, "degree", degree_threshold=best)
-                return {"T": best, "ms": table[key]["ms"], "cached": True}
+                return {"T": best, "ms": table[key]["ms"], "cached": True,
+                        "measured_on": table[key].get("measured_on", "unrecorded"),
+                        "reported": rep}
         except (OSError, ValueError):
             pass
     scores = {}
     for T in candidates:
         G.graph_partition(H, "degree", degree_threshold=T)
-        G.bfs(H, source)  # warm-up: allocates the workspaces
-        _, _, sb = G.bfs(H, source, timing=True)
-        total = sb["ms_total"]
-        if weighted:
-            G.sssp(H, source)
-            _, ss = G.sssp(H, source, timing=True)
-            total += ss["ms_total"]
-        G.pagerank(H, max_iter=1)
-        _, sp = G.pagerank(H, max_iter=pr_iters, timing=True)
-        total += sp["ms_compute"] / pr_iters * iters_per_step + sp["ms_exchange"] / pr_iters * iters_per_step
-        scores[T] = total
+        scores[T] = _step_ms(G, H, source, weighted, pr_iters, iters_per_step)
+    rep = extra()
     best = min(scores, key=scores.get)
     G.graph_partition(H, "degree", degree_threshold=best)
-    result = {"T": best, "ms": {str(k): v for k, v in scores.items()}, "cached": False}
+    result = {"T": best, "ms": {str(k): v for k, v in scores.items()}, "cached": False,
+              "measured_on": _device_name(), "reported": rep}
     if cache:
         table = {}
         if os.path.exists(cache):
@@ -72,7 +106,7 @@ def autotune_threshold(G, H, source: int, *, weighted: bool, candidates=DEFAULT_
                     table = json.load(f)
             except (OSError, ValueError):
                 table = {}
-        table[key] = {"T": best, "ms": result["ms"]}
+        table[key] = {"T": best, "ms": result["ms"], "measured_on": result["measured_on"]}
         tmp = cache + ".tmp"
         with open(tmp, "w") as f:
             json.dump(table, f)
@@ -99,3 +133,58 @@ def autotune_multi_threshold(G, H, vbase, *, candidates=MULTI_CANDIDATES, iters:
     best = min(scores, key=scores.get)
     G.graph_partition(H, "degree", degree_threshold=best)
     return {"T": best, "ms": {str(k): v for k, v in scores.items()}}
+
+
+# PageRank neighbour-sum candidates: the per-edge gather kernel and the segmented layout at
+# a few segment / bin sizes (segments of 2^14 or 2^15 sources, bins of 6K or 12K partial
+# sums; chunks at the maximum).
+PAGERANK_CANDIDATES = (
+    {"method": "gather"},
+    {"method": "segmented", "seg_log2": 15, "seg_bin": 12288},
+    {"method": "segmented", "seg_log2": 15, "seg_bin": 6144},
+    {"method": "segmented", "seg_log2": 14, "seg_bin": 12288},
+)
+
+
+def tune_pagerank(G, H, *, precision: str = "fp32", iters: int = 3,
+                  candidates=PAGERANK_CANDIDATES):
+    """Times each candidate's compute phase per iteration (after one warm-up call that also
+    builds a segmented plan) and returns {"best": params, "ms_per_iter": {label: ms}}.
+    A candidate the graph does not fit (the library refuses it) is skipped."""
+    scores, best, best_ms = {}, None, None
+    for c in candidates:
+        label = ",".join(f"{k}={v}" for k, v in c.items())
+        try:
+            G.pagerank(H, max_iter=1, precision=precision, **c)
+            _, st = G.pagerank(H, max_iter=iters, precision=precision, timing=True, **c)
+        except RuntimeError:
+            scores[label] = None
+            continue
+        ms = st["ms_compute"] / iters
+        scores[label] = ms
+        if best_ms is None or ms < best_ms:
+            best, best_ms = dict(c), ms
+    return {"best": best, "ms_per_iter": scores}
+
+
+# Direction-switch constants of the direction-optimised BFS (top-down -> bottom-up when the
+# frontier's edges exceed the unexplored edges / alpha; back when the frontier falls below
+# n / beta). Beamer et al.'s published defaults are alpha = 15, beta = 18.
+BFS_ALPHAS = (6.0, 10.0, 15.0, 24.0, 40.0)
+BFS_BETAS = (8.0, 18.0, 32.0)
+
+
+def tune_bfs(G, H, sources, *, alphas=BFS_ALPHAS, betas=BFS_BETAS):
+    """Times BFS from each of `sources` for every (alpha, beta) pair and returns
+    {"alpha": a, "beta": b, "ms": {"a/b": mean ms per search}} for the fastest pair."""
+    G.bfs(H, int(sources[0]))   # warm-up
+    scores = {}
+    for a in alphas:
+        for b in betas:
+            total = 0.0
+            for s in sources:
+                _, _, st = G.bfs(H, int(s), alpha=a, beta=b, timing=True, want_parents=True)
+                total += st["ms_total"]
+            scores[(a, b)] = total / len(sources)
+    a, b = min(scores, key=scores.get)
+    return {"alpha": a, "beta": b, "ms": {f"{k[0]:g}/{k[1]:g}": v for k, v in scores.items()}}

@@ -772,15 +772,15 @@ PrArgs make_args(graph* g, int cur, double damping) {
 template <class PR>
 graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* stats) {
   cudaStream_t st = g->stream;
-  // Segmented neighbour sums (pr_seg.cu) for FP32 and FP16 when the graph fits the layout;
-  // the per-edge gather kernel otherwise.
+  // Segmented neighbour sums (pr_seg.cu) when asked for (FP32 and FP16); the per-edge
+  // gather kernel otherwise (GRAPH_PR_AUTO: it is the faster of the two on this GPU).
   constexpr bool kSegCapable = sizeof(typename PR::AT) == 4;
   bool seg = false;
   if (at.method == GRAPH_PR_SEGMENTED && !kSegCapable) {
     set_error("the segmented method needs FP32 or FP16 precision");
     return GRAPH_EINVAL;
   }
-  if (kSegCapable && at.method != GRAPH_PR_GATHER) {
+  if (kSegCapable && at.method == GRAPH_PR_SEGMENTED) {
     const SegParams prm{at.seg_log2, at.seg_chunk, at.seg_bin};
     GG_TRY(seg_prepare(g, prm, &seg));
     if (!seg && at.method == GRAPH_PR_SEGMENTED) {

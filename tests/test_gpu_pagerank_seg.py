@@ -1,5 +1,5 @@
-"""Segmented PageRank (the default for FP32 and FP16) against the FP64 oracle and against
-the per-edge gather kernel (Section 7.1, Figure 14).
+"""Segmented PageRank (method "segmented", FP32 and FP16) against the FP64 oracle and
+against the per-edge gather kernel (Section 7.1, Figure 14).
 
 The segmented method forms the same neighbour sums in another order: per (segment,
 destination) partial sums from shared memory, then each destination's partials in segment
@@ -136,20 +136,20 @@ def test_segmented_limits_and_bad_arguments(gpu):
     r = np.zeros(g.n)
     assert _lib.load().pagerank(H.handle, attr, r.ctypes.data, None) == _lib.GRAPH_EINVAL
     H.free()
-    # a hub adjacent to more than 2,047 segments of 64 sources exceeds the layout: auto
-    # gathers (and is still right), segmented is refused
+    # a hub adjacent to more than 2,047 segments of 64 sources exceeds the layout: the
+    # segmented method is refused (the plan records it), the gather method is right
     g = star_plus(300000, extra_seed=3)
     H = gpu.graph_load_csr(g.offsets, g.cols)
     gpu.graph_partition(H, "none")
     ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=6)
-    r, _ = pr(gpu, H, "fp32", 6, seg_log2=6)
-    assert np.abs(r - ref).sum() <= 1e-6
-    info = gpu.pagerank_plan(H)
-    assert info["built"] == 1 and info["usable"] == 0
     with pytest.raises(_lib.GraphError) as e:
         pr(gpu, H, "fp32", 6, method="segmented", seg_log2=6)
     assert e.value.status == _lib.GRAPH_EINVAL
-    r, _ = pr(gpu, H, "fp32", 6)   # default segments: fits
+    info = gpu.pagerank_plan(H)
+    assert info["built"] == 1 and info["usable"] == 0
+    r, _ = pr(gpu, H, "fp32", 6)   # auto: gather
+    assert np.abs(r - ref).sum() <= 1e-6
+    r, _ = pr(gpu, H, "fp32", 6, method="segmented")   # default segments: fits
     assert gpu.pagerank_plan(H)["usable"] == 1
     assert np.abs(r - ref).sum() <= 1e-6
     H.free()
@@ -161,16 +161,19 @@ def test_segmented_plan_follows_the_partition(gpu):
     ref, _, _ = oracle.pagerank(g.n, g.offsets, g.cols, 0.85, max_iter=10)
     gpu.graph_partition(H, "degree", degree_threshold=8)
     assert gpu.pagerank_plan(H)["built"] == 0
-    pr(gpu, H, "fp32", 10)
+    pr(gpu, H, "fp32", 10)                         # auto gathers: no plan
+    assert gpu.pagerank_plan(H)["built"] == 0
+    pr(gpu, H, "fp32", 10, method="segmented")
     a = gpu.pagerank_plan(H)
     gpu.graph_partition(H, "degree", degree_threshold=256)
     assert gpu.pagerank_plan(H)["built"] == 0      # re-partition drops the plan
-    r, _ = pr(gpu, H, "fp32", 10)
+    r, _ = pr(gpu, H, "fp32", 10, method="segmented")
     b = gpu.pagerank_plan(H)
     assert a["built"] == b["built"] == 1 and a["partials"] != b["partials"]
     assert np.abs(r - ref).sum() <= 1e-6
     # interleaved precisions and methods reuse the plan
-    for prec, m in (("fp64", "auto"), ("fp16", "auto"), ("fp32", "gather"), ("fp32", "auto")):
+    for prec, m in (("fp64", "auto"), ("fp16", "segmented"), ("fp32", "gather"),
+                    ("fp32", "segmented")):
         r, _ = pr(gpu, H, prec, 10, method=m)
         assert np.abs(r - ref).sum() <= (1e-12 if prec == "fp64" else TOL[prec])
     assert gpu.pagerank_plan(H)["partials"] == b["partials"]
