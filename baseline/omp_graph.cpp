@@ -117,8 +117,12 @@ int omp_sssp(uint32_t n, const int64_t* off, const uint32_t* col, const uint32_t
       #pragma omp for schedule(dynamic, 64)
       for (int64_t i = 0; i < (int64_t)ncur; ++i) {
         const uint32_t u = cur[i];
-        queued[u].store(0, std::memory_order_relaxed);
-        const uint64_t du = d[u].load(std::memory_order_relaxed);
+        // Clear the queued mark before reading the distance, in one total order with the
+        // lowering threads' minimum and mark (sequentially consistent): a lowering that this
+        // read misses sees the cleared mark and queues u again. With relaxed order the two
+        // could be reordered (weakly ordered hosts) and the improvement lost.
+        queued[u].store(0, std::memory_order_seq_cst);
+        const uint64_t du = d[u].load(std::memory_order_seq_cst);
         for (int64_t e = off[u]; e < off[u + 1]; ++e) {
           const uint32_t v = col[e];
           const uint64_t s = du + w[e];
@@ -128,9 +132,10 @@ int omp_sssp(uint32_t n, const int64_t* off, const uint32_t* col, const uint32_t
           }
           const uint32_t nd = (uint32_t)s;
           uint32_t old = d[v].load(std::memory_order_relaxed);
-          while (nd < old && !d[v].compare_exchange_weak(old, nd)) {
+          while (nd < old && !d[v].compare_exchange_weak(old, nd, std::memory_order_seq_cst,
+                                                          std::memory_order_relaxed)) {
           }
-          if (nd < old && !queued[v].exchange(1)) out.push(v);
+          if (nd < old && !queued[v].exchange(1, std::memory_order_seq_cst)) out.push(v);
         }
       }
       out.flush();

@@ -426,6 +426,32 @@ graph_status pagerank_hybrid(graph_t* g, const pagerank_attr* attr, int cpu_thre
                              double* ranks, graph_stats* stats, pagerank_hybrid_info* info);
 
 /* ---------------------------------------------------------------------------------------
+ * bfs_hybrid, sssp_hybrid -- BFS and SSSP with the paper's hybrid placement (Section 4.1,
+ * Figure 6; Section 6.2-6.3 for BFS, Section 7.3 for SSSP): partition 0 (with the DEGREE
+ * strategy, the high-degree vertices) is processed by cpu_threads host threads from host
+ * copies of its arrays, partition 1 by the GPU, in the same superstep. BFS: both sides
+ * expand their own frontier top-down (Figure 11); SSSP: both run the Bellman-Ford round of
+ * Figure 20 on their own active vertices (plain rounds). The communication phase moves only
+ * messages (Section 4.3.2): the claims (BFS: target, level, parent) or lowered outbox minima
+ * (SSSP: target, distance) each side produced for the other's vertices, as compact lists
+ * across the host/device boundary, applied with the same claim / minimum the GPU-only calls
+ * use. Results equal those of bfs() (levels; parents valid) and sssp() (distances).
+ *   source, levels, parents, dist, stats   as for bfs / sssp
+ *   attr         as for bfs (direction AUTO or TOPDOWN: top-down only) / sssp (delta = 0)
+ *   cpu_threads  as for pagerank_hybrid
+ *   info         per-processor sizes and times (the pagerank_hybrid report), or NULL
+ * The first call after graph_partition copies partition 0's offsets, edge ids (weights for
+ * SSSP), local-to-global ids (BFS) and outbox to host memory (kept with the BFS / SSSP
+ * workspace until re-partition or graph_free) and allocates pinned message buffers.
+ * Errors: EINVAL, ESTATE, ENOMEM (host or device), ECUDA, ETIMEOUT, ERANGE (SSSP overflow).
+ * ------------------------------------------------------------------------------------- */
+graph_status bfs_hybrid(graph_t* g, uint32_t source, uint32_t* levels, uint32_t* parents,
+                        const bfs_attr* attr, int cpu_threads, graph_stats* stats,
+                        pagerank_hybrid_info* info);
+graph_status sssp_hybrid(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* attr,
+                         int cpu_threads, graph_stats* stats, pagerank_hybrid_info* info);
+
+/* ---------------------------------------------------------------------------------------
  * pagerank_multi -- PageRank of many independent graphs in one pass of supersteps. The
  * paper ranks one graph per run (Section 7.1, Figure 14); here the loaded graph is the
  * disjoint union of ngraphs components, component c owning global vertex ids

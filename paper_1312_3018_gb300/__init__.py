@@ -241,6 +241,48 @@ def sssp(g: Graph, source: int, dist=None, *, out: str = "device", max_superstep
     return dist, stats.as_dict()
 
 
+def bfs_hybrid(g: Graph, source: int, levels=None, parents=None, *, cpu_threads: int = 0,
+               want_parents: bool = True, out: str = "device", max_supersteps: int = 0):
+    """BFS with partition 0 expanded on cpu_threads host threads and partition 1 on the GPU
+    (the paper's hybrid placement, top-down). Returns (levels, parents, stats);
+    stats["hybrid"] holds the per-processor sizes and times."""
+    torch = _torch()
+    levels = _out_u32(torch, g.n, out, levels)
+    if want_parents:
+        parents = _out_u32(torch, g.n, out, parents)
+    pl, mem = _ptr(levels)
+    pp, memp = _ptr(parents) if want_parents else (None, mem)
+    if memp != mem:
+        raise ValueError("levels and parents must live in the same memory")
+    attr = _lib.bfs_attr(mem, _DIR["topdown"], 0.0, 0.0, max_supersteps, 0)
+    stats = _lib.graph_stats()
+    info = _lib.pagerank_hybrid_info()
+    st = _lib.load().bfs_hybrid(g.handle, int(source), pl, pp, C.byref(attr), int(cpu_threads),
+                                C.byref(stats), C.byref(info))
+    _lib.check(st, "bfs_hybrid")
+    d = stats.as_dict()
+    d["hybrid"] = info.as_dict()
+    return levels, (parents if want_parents else None), d
+
+
+def sssp_hybrid(g: Graph, source: int, dist=None, *, cpu_threads: int = 0, out: str = "device",
+                max_supersteps: int = 0):
+    """SSSP (plain Bellman-Ford rounds) with partition 0 on cpu_threads host threads and
+    partition 1 on the GPU. Returns (distances, stats); stats["hybrid"] as for bfs_hybrid."""
+    torch = _torch()
+    dist = _out_u32(torch, g.n, out, dist)
+    pd, mem = _ptr(dist)
+    attr = _lib.sssp_attr(mem, max_supersteps, 0, 0)
+    stats = _lib.graph_stats()
+    info = _lib.pagerank_hybrid_info()
+    st = _lib.load().sssp_hybrid(g.handle, int(source), pd, C.byref(attr), int(cpu_threads),
+                                 C.byref(stats), C.byref(info))
+    _lib.check(st, "sssp_hybrid")
+    d = stats.as_dict()
+    d["hybrid"] = info.as_dict()
+    return dist, d
+
+
 def sssp_batch(g: Graph, sources, dist=None, *, out: str = "device", max_supersteps: int = 0,
                timing: bool = False, delta: int = 0):
     """k = len(sources) <= SSSP_BATCH_MAX shortest-path searches in one pass of Bellman-Ford

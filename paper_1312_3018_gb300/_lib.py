@@ -161,6 +161,10 @@ SIGNATURES = {
                               C.POINTER(graph_stats)]),
     "pagerank_hybrid": (_int, [_vp, C.POINTER(pagerank_attr), _int, _vp, C.POINTER(graph_stats),
                                C.POINTER(pagerank_hybrid_info)]),
+    "bfs_hybrid": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), _int, C.POINTER(graph_stats),
+                          C.POINTER(pagerank_hybrid_info)]),
+    "sssp_hybrid": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), _int, C.POINTER(graph_stats),
+                           C.POINTER(pagerank_hybrid_info)]),
     "bfs_csr_noalloc": (_int, [_u32, _i64, _vp, _vp, _u32, _vp, _vp, _vp]),
     "graph_server_create": (_int, [_vp, C.POINTER(graph_server_attr), C.POINTER(_vp)]),
     "graph_server_submit": (_int, [_vp, _int, _u32, _vp, C.POINTER(C.c_uint64)]),

@@ -17,8 +17,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <memory>
 
 #include "common.cuh"
+#include "hybrid.cuh"
 
 namespace gg {
 
@@ -32,15 +35,42 @@ struct BfsCounters {
   unsigned long long messages;
 };
 
+// Host side of bfs_hybrid: partition 0's CSR and ids (host copies made once per
+// partition), its search state, and pinned message arrays for both directions.
+struct HbfsHost {
+  std::vector<int64_t> off0;
+  std::vector<uint32_t> E0, l2g0, outbox0;
+  std::unique_ptr<std::atomic<uint64_t>[]> vis, oseen;   // partition 0 / its outbox slots
+  std::vector<uint32_t> level, parent;
+  uint32_t* pin_out = nullptr;  // [3 nout0]: (local id in partition 1, level, parent)
+  uint32_t* pin_in = nullptr;   // [3 nout1]: (local id in partition 0, level, parent)
+  DevBuf dmsg;                  // [3 max(nout0, nout1)] device staging of either direction
+  cudaEvent_t ev[3] = {};       // GPU compute start / end, device messages ready
+};
+
 struct BfsWs {
   DevBuf level[2], parent[2], visited[2], front[2][2], queue[2][2], hubq[2][2];
   DevBuf oseen[2], olevel[2], oparent[2], dirty[2], ghost[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
+  HbfsHost* hyb = nullptr;
 };
+
+void free_hbfs(graph* g, BfsWs* w) {
+  HbfsHost* h = w->hyb;
+  if (!h) return;
+  if (h->pin_out) cudaFreeHost(h->pin_out);
+  if (h->pin_in) cudaFreeHost(h->pin_in);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  dfree(g, h->dmsg);
+  delete h;
+  w->hyb = nullptr;
+}
 
 void free_bfs(graph* g) {
   if (!g->bfs) return;
   BfsWs* w = g->bfs;
+  free_hbfs(g, w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->level[p], &w->parent[p], &w->visited[p], &w->front[p][0],
                      &w->front[p][1], &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],
@@ -332,6 +362,50 @@ __global__ void k_bfs_collect(const __grid_constant__ BfsArgs A, uint32_t nv0, u
   if (parents) parents[gid] = S.parent[lid];
 }
 
+// bfs_hybrid, device to host: partition 1's outbox claims of this level as (owner's local
+// id in partition 0, level, parent).
+__global__ void k_hbfs_out(const __grid_constant__ BfsArgs A, uint32_t* out) {
+  const BfsSide& S = A.side[1];
+  const uint32_t cnt = A.ctr->dirty_tail[1];
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    const uint32_t idx = S.dirty[k];
+    out[3 * k] = S.P.outbox[idx];
+    out[3 * k + 1] = S.olevel[idx];
+    out[3 * k + 2] = S.oparent[idx];
+  }
+}
+
+// bfs_hybrid, host to device: messages (local id in partition 1, level, parent) from the
+// host's partition 0. An unvisited target takes the level and parent and joins the next
+// queue (the scatter of the communication phase, as in k_bfs_exchange).
+__global__ void __launch_bounds__(kThreads) k_hbfs_in(const __grid_constant__ BfsArgs A,
+                                                      const uint32_t* in, uint32_t cnt) {
+  LocalCounts c;
+  const BfsSide& Q = A.side[1];
+  const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i0 = warp_global * 32; i0 < cnt; i0 += nwarps * 32) {
+    const uint32_t i = i0 + lane_id();
+    bool dis = false;
+    uint32_t u = 0;
+    if (i < cnt) {
+      u = in[3 * i];
+      c.msg++;
+      if (bitmap_claim(Q.visited, u)) {
+        dis = true;
+        Q.level[u] = in[3 * i + 1];
+        Q.parent[u] = in[3 * i + 2];
+        atomicOr(&Q.next[u >> 5], 1u << (u & 31u));
+        c.nf++;
+        c.mf += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
+      }
+    }
+    warp_append_bucketed(dis, u, dis ? bucket_of(Q.P, u) : 0, A.ctr->tail[1], Q.nqueue, Q.P,
+                         Q.nhubq);
+  }
+  flush_counts(c, A.ctr);
+}
+
 graph_status alloc_ws(graph* g) {
   if (g->bfs) return GRAPH_OK;
   BfsWs* w = new BfsWs();
@@ -565,5 +639,312 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
     stats->launches = launches;
   }
   timer.finish(stats);
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// bfs_hybrid: partition 0 on host threads, partition 1 on the GPU (Section 4.1, Figure 6;
+// Section 6.2-6.3). Both sides expand their own frontier top-down in the same superstep
+// (Figure 11); only messages cross: the claims each side made on the other's vertices,
+// as (target, level, parent) lists.
+// ---------------------------------------------------------------------------------------
+namespace gg {
+namespace {
+
+graph_status ensure_hbfs(graph* g, BfsWs* w) {
+  if (w->hyb) return GRAPH_OK;
+  const Part& P0 = g->part[0];
+  const Part& P1 = g->part[1];
+  cudaStream_t st = g->stream;
+  HbfsHost* h = new HbfsHost();
+  w->hyb = h;
+  h->off0.resize((size_t)P0.nv + 1);
+  h->E0.resize((size_t)P0.ne);
+  h->l2g0.resize(P0.nv);
+  h->outbox0.resize(P0.nout);
+  h->level.resize(P0.nv);
+  h->parent.resize(P0.nv);
+  h->vis.reset(new std::atomic<uint64_t>[(P0.nv + 63) / 64 + 1]);
+  h->oseen.reset(new std::atomic<uint64_t>[(P0.nout + 63) / 64 + 1]);
+  GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1), cudaMemcpyDeviceToHost, st));
+  if (P0.ne) GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+  if (P0.nv) GG_CUDA(cudaMemcpyAsync(h->l2g0.data(), P0.l2g.p, 4ull * P0.nv, cudaMemcpyDeviceToHost, st));
+  if (P0.nout)
+    GG_CUDA(cudaMemcpyAsync(h->outbox0.data(), P0.outbox.p, 4ull * P0.nout, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  for (cudaEvent_t& e : h->ev) GG_CUDA(cudaEventCreate(&e));
+  const size_t b0 = 12ull * std::max<uint32_t>(P0.nout, 1), b1 = 12ull * std::max<uint32_t>(P1.nout, 1);
+  if (cudaHostAlloc((void**)&h->pin_out, b0, cudaHostAllocDefault) != cudaSuccess) h->pin_out = nullptr;
+  if (cudaHostAlloc((void**)&h->pin_in, b1, cudaHostAllocDefault) != cudaSuccess) h->pin_in = nullptr;
+  if (!h->pin_out || !h->pin_in) {
+    set_error("pinned host allocation of the message arrays failed");
+    return GRAPH_ENOMEM;
+  }
+  GG_TRY(dalloc(g, h->dmsg, std::max(b0, b1)));
+  return GRAPH_OK;
+}
+
+}  // namespace
+}  // namespace gg
+
+extern "C" graph_status bfs_hybrid(graph_t* g, uint32_t source, uint32_t* levels,
+                                   uint32_t* parents, const bfs_attr* attr, int cpu_threads,
+                                   graph_stats* stats, pagerank_hybrid_info* info) {
+  using Clock = std::chrono::steady_clock;
+  if (!g || !levels) {
+    set_error("graph or levels is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (source >= g->n) {
+    set_error("source %u >= n %u", source, g->n);
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before bfs_hybrid");
+    return GRAPH_ESTATE;
+  }
+  bfs_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if ((at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) ||
+      at.direction == GRAPH_BFS_BOTTOMUP || cpu_threads > GRAPH_HYBRID_MAX_THREADS) {
+    set_error("bad bfs_hybrid attributes (top-down only; out_mem; cpu_threads)");
+    return GRAPH_EINVAL;
+  }
+  const int nt = hybrid_threads(cpu_threads);
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  GG_TRY(ensure_ws(g));
+  BfsWs* w = g->bfs;
+  {
+    graph_status s = GRAPH_OK;
+    try {
+      s = ensure_hbfs(g, w);
+    } catch (const std::bad_alloc&) {
+      set_error("host allocation for the host partition failed");
+      s = GRAPH_ENOMEM;
+    }
+    if (s != GRAPH_OK) {
+      free_hbfs(g, w);
+      return s;
+    }
+  }
+  HbfsHost* h = w->hyb;
+  cudaStream_t st = g->stream;
+  const Part& P0 = g->part[0];
+  const uint32_t nv0 = P0.nv;
+  const auto t_start = Clock::now();
+  // Reset: the device state of partition 1, the host state of partition 0.
+  {
+    const Part& P1 = g->part[1];
+    GG_CUDA(cudaMemsetAsync(w->level[1].p, 0xFF, 4ull * P1.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->parent[1].p, 0xFF, 4ull * P1.nv, st));
+    GG_CUDA(cudaMemsetAsync(w->visited[1].p, 0, 4 * w->words[1], st));
+    GG_CUDA(cudaMemsetAsync(w->front[1][0].p, 0, 4 * w->words[1], st));
+    GG_CUDA(cudaMemsetAsync(w->oseen[1].p, 0, 4 * w->owords[1], st));
+    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(BfsCounters), st));
+  }
+  std::fill(h->level.begin(), h->level.end(), kInf);
+  std::fill(h->parent.begin(), h->parent.end(), kInf);
+  for (size_t i = 0; i < (nv0 + 63) / 64 + 1; ++i) h->vis[i].store(0, std::memory_order_relaxed);
+  for (size_t i = 0; i < (P0.nout + 63) / 64 + 1; ++i) h->oseen[i].store(0, std::memory_order_relaxed);
+  uint32_t gl = 0;
+  GG_CUDA(cudaMemcpyAsync(&gl, (const uint32_t*)g->g2l.p + source, 4, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  int cur = 0;
+  std::vector<uint32_t> F0;   // partition 0's frontier (local ids)
+  int64_t traversed = 0, inspected = 0, messages = 0, launches = 0, host_mf = 0;
+  if (gl & kRemote) {
+    BfsArgs A = make_args(g, cur, 0);
+    k_bfs_init<<<1, 1, 0, st>>>(A, (const uint32_t*)g->g2l.p, source,
+                                (uint32_t*)w->queue[0][cur].p, (uint32_t*)w->queue[1][cur].p,
+                                (uint32_t*)w->hubq[0][cur].p, (uint32_t*)w->hubq[1][cur].p);
+    GG_CUDA(cudaGetLastError());
+    launches++;
+  } else {
+    const uint32_t lid = gl;
+    h->level[lid] = 0;
+    h->parent[lid] = source;
+    host_claim(h->vis.get(), lid);
+    F0.push_back(lid);
+    host_mf = h->off0[lid + 1] - h->off0[lid];
+  }
+  BfsCounters* hc = (BfsCounters*)g->host_counters;
+  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(BfsCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  double ms_cpu = 0, ms_gpu = 0, ms_xchg = 0;
+  std::vector<std::vector<uint32_t>> disc(nt), mslot(nt), mpar(nt);
+  std::vector<int64_t> tmf(nt), tin(nt);
+  int64_t L = 0;
+  for (;; ++L) {
+    const BfsCounters c = *hc;
+    if (c.nf == 0 && F0.empty()) break;
+    if (L >= cap) {
+      set_error("bfs_hybrid reached the superstep cap (%lld)", (long long)cap);
+      return GRAPH_ETIMEOUT;
+    }
+    traversed += (int64_t)c.mf + host_mf;
+    host_mf = 0;
+    // GPU: partition 1's top-down level, then its claims on partition 0 as messages.
+    GG_CUDA(cudaMemsetAsync(g->counters.p, 0, sizeof(BfsCounters), st));
+    GG_CUDA(cudaMemsetAsync(w->front[1][1 - cur].p, 0, 4 * w->words[1], st));
+    BfsArgs A = make_args(g, cur, (uint32_t)L);
+    GG_CUDA(cudaEventRecord(h->ev[0], st));
+    {
+      Plan pl;
+      memset(&pl, 0, sizeof(pl));
+      const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+      const PartView V = g->part[1].view();
+      plan_add(pl, (const uint32_t*)w->hubq[1][cur].p, 0, c.tail[1][0], 1, 8, 0);
+      for (int b = 1; b < kNBucket; ++b)
+        plan_add(pl, (const uint32_t*)w->queue[1][cur].p + V.bstart[b], 0, c.tail[1][b], 1,
+                 gsh[b], b);
+      if (pl.nblocks) {
+        k_bfs_topdown<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+        launches++;
+      }
+    }
+    GG_CUDA(cudaEventRecord(h->ev[1], st));
+    k_hbfs_out<<<152 * 2, 256, 0, st>>>(A, (uint32_t*)h->dmsg.p);
+    launches++;
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(BfsCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaEventRecord(h->ev[2], st));
+    // Host: partition 0's top-down level (Figure 11) while the GPU works.
+    const auto tc0 = Clock::now();
+    for (int k = 0; k < nt; ++k) {
+      disc[k].clear();
+      mslot[k].clear();
+      mpar[k].clear();
+      tmf[k] = 0;
+      tin[k] = 0;
+    }
+    const uint32_t next_level = (uint32_t)L + 1;
+    host_dynamic(nt, F0.size(), 1, [&](int k, uint64_t a, uint64_t b) {
+      for (uint64_t i = a; i < b; ++i) {
+        const uint32_t v = F0[i];
+        const uint32_t vg = h->l2g0[v];
+        const int64_t e1 = h->off0[v + 1];
+        for (int64_t e = h->off0[v]; e < e1; ++e) {
+          const uint32_t x = h->E0[e];
+          if (!(x & kRemote)) {
+            if (host_claim(h->vis.get(), x)) {
+              h->level[x] = next_level;
+              h->parent[x] = vg;
+              disc[k].push_back(x);
+              tmf[k] += h->off0[x + 1] - h->off0[x];
+            }
+          } else if (host_claim(h->oseen.get(), x & kIdMask)) {
+            mslot[k].push_back(x & kIdMask);
+            mpar[k].push_back(vg);
+          }
+        }
+        tin[k] += e1 - h->off0[v];
+      }
+    });
+    const auto tc1 = Clock::now();
+    ms_cpu += std::chrono::duration<double, std::milli>(tc1 - tc0).count();
+    // Exchange: the GPU's claims on partition 0 come up and are applied on the host ...
+    GG_CUDA(cudaEventSynchronize(h->ev[2]));
+    float gms = 0;
+    GG_CUDA(cudaEventElapsedTime(&gms, h->ev[0], h->ev[1]));
+    ms_gpu += gms;
+    const auto tx0 = Clock::now();
+    const uint32_t n1 = hc->dirty_tail[1];
+    inspected += (int64_t)hc->inspected;
+    if (n1) {
+      GG_CUDA(cudaMemcpyAsync(h->pin_in, h->dmsg.p, 12ull * n1, cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<uint32_t> in_disc;
+    for (uint32_t i = 0; i < n1; ++i) {
+      const uint32_t u = h->pin_in[3 * i];
+      if (host_claim(h->vis.get(), u)) {
+        h->level[u] = h->pin_in[3 * i + 1];
+        h->parent[u] = h->pin_in[3 * i + 2];
+        in_disc.push_back(u);
+        host_mf += h->off0[u + 1] - h->off0[u];
+      }
+    }
+    // ... and the host's claims on partition 1 go down and are applied on the device.
+    uint32_t n0 = 0;
+    for (int k = 0; k < nt; ++k)
+      for (size_t j = 0; j < mslot[k].size(); ++j) {
+        h->pin_out[3 * n0] = h->outbox0[mslot[k][j]];
+        h->pin_out[3 * n0 + 1] = next_level;
+        h->pin_out[3 * n0 + 2] = mpar[k][j];
+        ++n0;
+      }
+    if (n0) {
+      GG_CUDA(cudaMemcpyAsync(h->dmsg.p, h->pin_out, 12ull * n0, cudaMemcpyHostToDevice, st));
+      k_hbfs_in<<<std::min(grid_for(32ull * n0, kThreads), 152u * 8), kThreads, 0, st>>>(
+          A, (const uint32_t*)h->dmsg.p, n0);
+      launches++;
+      GG_CUDA(cudaGetLastError());
+    }
+    // The counters now hold the level's discoveries in partition 1 from both kernels (the
+    // next queue's tails, nf, mf).
+    GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(BfsCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    messages += (int64_t)n1 + n0;
+    ms_xchg += std::chrono::duration<double, std::milli>(Clock::now() - tx0).count();
+    // Partition 0's next frontier.
+    F0.clear();
+    for (int k = 0; k < nt; ++k) {
+      F0.insert(F0.end(), disc[k].begin(), disc[k].end());
+      host_mf += tmf[k];
+      inspected += tin[k];
+    }
+    F0.insert(F0.end(), in_disc.begin(), in_disc.end());
+    cur = 1 - cur;
+  }
+  (void)t_start;
+  // Collect: the host partition's levels and parents join the device's, then the usual
+  // local -> global write.
+  if (nv0) {
+    GG_CUDA(cudaMemcpyAsync(w->level[0].p, h->level.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
+    GG_CUDA(cudaMemcpyAsync(w->parent[0].p, h->parent.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
+  }
+  uint32_t* dl = levels;
+  uint32_t* dp = parents;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 8ull * g->n));
+    dl = (uint32_t*)g->stage.p;
+    dp = parents ? dl + g->n : nullptr;
+  }
+  {
+    BfsArgs A = make_args(g, cur, 0);
+    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, dl, dp);
+    launches++;
+    GG_CUDA(cudaGetLastError());
+  }
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
+    if (parents) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
+  }
+  GG_CUDA(cudaStreamSynchronize(st));
+  const graph_status s = check_device_error(g);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)L;
+    stats->topdown_steps = (int)L;
+    stats->edges_traversed = traversed;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+    stats->ms_compute = std::max(ms_cpu, ms_gpu);
+    stats->ms_exchange = ms_xchg;
+    stats->ms_total = std::chrono::duration<double, std::milli>(Clock::now() - t_start).count();
+  }
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->cpu_threads = nt;
+    info->cpu_vertices = nv0;
+    info->gpu_vertices = g->part[1].nv;
+    info->cpu_edges = P0.ne;
+    info->gpu_edges = g->part[1].ne;
+    info->ms_cpu_compute = ms_cpu;
+    info->ms_gpu_compute = ms_gpu;
+    info->ms_exchange = ms_xchg;
+  }
   return s;
 }

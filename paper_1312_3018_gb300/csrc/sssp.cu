@@ -26,7 +26,11 @@
 // Distances are uint32; a relaxation saturates at 0xFFFFFFFE and flags an overflow.
 #include <string.h>
 
+#include <chrono>
+#include <memory>
+
 #include "common.cuh"
+#include "hybrid.cuh"
 #include "jobs.cuh"
 
 namespace gg {
@@ -42,14 +46,42 @@ struct SsspCounters {
   uint32_t clamped;                   // a final distance equals the saturation value
 };
 
+// Host side of sssp_hybrid: partition 0's CSR, weights and ids (host copies made once per
+// partition), its search state and outbox minima, and pinned message arrays.
+struct HsspHost {
+  std::vector<int64_t> off0;
+  std::vector<uint32_t> E0, W0, outbox0;
+  std::unique_ptr<std::atomic<uint32_t>[]> dist, omsg;
+  std::unique_ptr<std::atomic<uint8_t>[]> touched, odirty;
+  std::vector<uint32_t> snap;
+  uint32_t* pin_out = nullptr;  // [2 nout0]: (local id in partition 1, distance)
+  uint32_t* pin_in = nullptr;   // [2 nout1 + 4]: count, then (local id in partition 0, distance)
+  DevBuf dmsg;                  // device staging of either direction (same layout as pin_in)
+  cudaEvent_t ev[3] = {};
+};
+
 struct SsspWs {
   DevBuf dist[2], snap[2], touched[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
+  HsspHost* hyb = nullptr;
 };
+
+void free_hsssp(graph* g, SsspWs* w) {
+  HsspHost* h = w->hyb;
+  if (!h) return;
+  if (h->pin_out) cudaFreeHost(h->pin_out);
+  if (h->pin_in) cudaFreeHost(h->pin_in);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  dfree(g, h->dmsg);
+  delete h;
+  w->hyb = nullptr;
+}
 
 void free_sssp(graph* g) {
   if (!g->sssp) return;
   SsspWs* w = g->sssp;
+  free_hsssp(g, w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->touched[p], &w->queue[p][0],
                      &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1], &w->omsg[p],
@@ -341,6 +373,40 @@ __global__ void k_cc_tails(const __grid_constant__ SsspArgs A) {
     const PartView& P = A.side[p].P;
     A.ctr->tail[p][0] = P.nchunk;
     for (int b = 1; b < kNBucket; ++b) A.ctr->tail[p][b] = P.bstart[b + 1] - P.bstart[b];
+  }
+}
+
+// sssp_hybrid, device to host: partition 1's outbox slots lowered this round, as (owner's
+// local id in partition 0, minimum); out[0] counts them. One lane per dirty word.
+__global__ void k_hsssp_out(const __grid_constant__ SsspArgs A, uint32_t* out) {
+  const SsspSide& S = A.side[1];
+  const uint32_t word = blockIdx.x * blockDim.x + threadIdx.x;
+  if (word * 32 >= S.P.nout) return;
+  uint32_t bits = S.odirty[word];
+  if (!bits) return;
+  S.odirty[word] = 0;
+  const uint32_t at = atomicAdd(out, (uint32_t)__popc(bits));
+  uint32_t k = 0;
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint32_t idx = word * 32 + b;
+    out[4 + 2 * (at + k)] = S.P.outbox[idx];
+    out[4 + 2 * (at + k) + 1] = S.omsg[idx];
+    ++k;
+  }
+}
+
+// sssp_hybrid, host to device: (local id in partition 1, distance) messages from the host's
+// partition 0, applied with the minimum-and-mark of the communication phase.
+__global__ void k_hsssp_in(const __grid_constant__ SsspArgs A, const uint32_t* in, uint32_t cnt) {
+  const SsspSide& Q = A.side[1];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t u = in[2 * i], val = in[2 * i + 1];
+    if (val < Q.dist[u]) {
+      red_min(&Q.dist[u], val);
+      red_or(&Q.touched[u >> 5], 1u << (u & 31u));
+    }
   }
 }
 
@@ -833,5 +899,311 @@ extern "C" graph_status connected_components(graph_t* g, uint32_t* labels,
     stats->launches = launches;
   }
   timer.finish(stats);
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// sssp_hybrid: partition 0 on host threads, partition 1 on the GPU (Section 4.1, Figure 6;
+// Section 7.3). Both sides run the same Bellman-Ford round (Figure 20) on their own active
+// vertices; only outbox minima cross, as (target, distance) lists of the slots lowered in
+// the round. Plain rounds (no near-far order).
+// ---------------------------------------------------------------------------------------
+namespace gg {
+namespace {
+
+graph_status ensure_hsssp(graph* g, SsspWs* w) {
+  if (w->hyb) return GRAPH_OK;
+  const Part& P0 = g->part[0];
+  const Part& P1 = g->part[1];
+  cudaStream_t st = g->stream;
+  HsspHost* h = new HsspHost();
+  w->hyb = h;
+  h->off0.resize((size_t)P0.nv + 1);
+  h->E0.resize((size_t)P0.ne);
+  h->W0.resize((size_t)P0.ne);
+  h->outbox0.resize(P0.nout);
+  h->snap.resize(P0.nv);
+  h->dist.reset(new std::atomic<uint32_t>[P0.nv + 1]);
+  h->touched.reset(new std::atomic<uint8_t>[P0.nv + 1]);
+  h->omsg.reset(new std::atomic<uint32_t>[P0.nout + 1]);
+  h->odirty.reset(new std::atomic<uint8_t>[P0.nout + 1]);
+  GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1), cudaMemcpyDeviceToHost, st));
+  if (P0.ne) {
+    GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaMemcpyAsync(h->W0.data(), P0.W.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+  }
+  if (P0.nout)
+    GG_CUDA(cudaMemcpyAsync(h->outbox0.data(), P0.outbox.p, 4ull * P0.nout, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  for (cudaEvent_t& e : h->ev) GG_CUDA(cudaEventCreate(&e));
+  const size_t b0 = 8ull * std::max<uint32_t>(P0.nout, 1);
+  const size_t b1 = 8ull * std::max<uint32_t>(P1.nout, 1) + 16;
+  if (cudaHostAlloc((void**)&h->pin_out, b0, cudaHostAllocDefault) != cudaSuccess) h->pin_out = nullptr;
+  if (cudaHostAlloc((void**)&h->pin_in, b1, cudaHostAllocDefault) != cudaSuccess) h->pin_in = nullptr;
+  if (!h->pin_out || !h->pin_in) {
+    set_error("pinned host allocation of the message arrays failed");
+    return GRAPH_ENOMEM;
+  }
+  GG_TRY(dalloc(g, h->dmsg, std::max(b0, b1)));
+  return GRAPH_OK;
+}
+
+}  // namespace
+}  // namespace gg
+
+extern "C" graph_status sssp_hybrid(graph_t* g, uint32_t source, uint32_t* dist,
+                                    const sssp_attr* attr, int cpu_threads, graph_stats* stats,
+                                    pagerank_hybrid_info* info) {
+  using Clock = std::chrono::steady_clock;
+  if (!g || !dist) {
+    set_error("graph or dist is NULL");
+    return GRAPH_EINVAL;
+  }
+  if (source >= g->n) {
+    set_error("source %u >= n %u", source, g->n);
+    return GRAPH_EINVAL;
+  }
+  if (!g->weighted) {
+    set_error("sssp_hybrid needs edge weights (load the graph with weights)");
+    return GRAPH_EINVAL;
+  }
+  if (!g->partitioned) {
+    set_error("graph_partition must run before sssp_hybrid");
+    return GRAPH_ESTATE;
+  }
+  sssp_attr at;
+  memset(&at, 0, sizeof(at));
+  if (attr) at = *attr;
+  if ((at.out_mem != GRAPH_MEM_HOST && at.out_mem != GRAPH_MEM_DEVICE) || at.delta != 0 ||
+      cpu_threads > GRAPH_HYBRID_MAX_THREADS) {
+    set_error("bad sssp_hybrid attributes (plain rounds only: delta = 0; out_mem; cpu_threads)");
+    return GRAPH_EINVAL;
+  }
+  const int nt = hybrid_threads(cpu_threads);
+  const int64_t cap = at.max_supersteps > 0 ? at.max_supersteps : (int64_t)g->n + 1;
+  GG_TRY(ensure_ws(g));
+  SsspWs* w = g->sssp;
+  {
+    graph_status s = GRAPH_OK;
+    try {
+      s = ensure_hsssp(g, w);
+    } catch (const std::bad_alloc&) {
+      set_error("host allocation for the host partition failed");
+      s = GRAPH_ENOMEM;
+    }
+    if (s != GRAPH_OK) {
+      free_hsssp(g, w);
+      return s;
+    }
+  }
+  HsspHost* h = w->hyb;
+  cudaStream_t st = g->stream;
+  const Part& P0 = g->part[0];
+  const uint32_t nv0 = P0.nv, nout0 = P0.nout;
+  const auto t_start = Clock::now();
+  SsspCounters* dc = (SsspCounters*)g->counters.p;
+  SsspCounters* hc = (SsspCounters*)g->host_counters;
+  GG_TRY(launch_start(g, w, dc, source, st));   // resets both sides; seeds a partition-1 source
+  for (uint32_t v = 0; v < nv0; ++v) {
+    h->dist[v].store(kInf, std::memory_order_relaxed);
+    h->touched[v].store(0, std::memory_order_relaxed);
+    h->snap[v] = kInf;
+  }
+  for (uint32_t i = 0; i < nout0; ++i) {
+    h->omsg[i].store(kInf, std::memory_order_relaxed);
+    h->odirty[i].store(0, std::memory_order_relaxed);
+  }
+  uint32_t gl = 0;
+  GG_CUDA(cudaMemcpyAsync(&gl, (const uint32_t*)g->g2l.p + source, 4, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  std::vector<uint32_t> A0;   // partition 0's active vertices
+  if (!(gl & kRemote)) {
+    h->dist[gl].store(0, std::memory_order_relaxed);
+    A0.push_back(gl);
+    for (int b = 0; b < kNBucket; ++b) hc->tail[0][b] = 0;
+  }
+  int64_t inspected = 0, messages = 0, launches = 1, rounds = 0;
+  bool overflow = false;
+  double ms_cpu = 0, ms_gpu = 0, ms_xchg = 0;
+  std::vector<std::vector<uint32_t>> ttouch(nt), tdirty(nt);
+  std::vector<int64_t> tin(nt);
+  std::vector<uint8_t> tovf(nt);
+  int cur = 0;
+  const uint32_t owords1 = (uint32_t)((g->part[1].nout + 31) / 32);
+  const uint32_t words1 = (uint32_t)w->words[1];
+  for (;; ++rounds) {
+    SsspCounters c = *hc;
+    uint64_t dev_active = 0;
+    for (int b = 0; b < kNBucket; ++b) dev_active += c.tail[1][b];
+    if (dev_active == 0 && A0.empty()) break;
+    if (rounds >= cap) {
+      set_error("sssp_hybrid reached the superstep cap (%lld)", (long long)cap);
+      return GRAPH_ETIMEOUT;
+    }
+    // GPU: partition 1's round, then its lowered outbox slots as messages.
+    GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(SsspCounters), st));
+    GG_CUDA(cudaMemsetAsync(h->dmsg.p, 0, 16, st));
+    SsspArgs A = make_args(g, w, dc, cur);
+    GG_CUDA(cudaEventRecord(h->ev[0], st));
+    {
+      Plan pl;
+      memset(&pl, 0, sizeof(pl));
+      const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+      const PartView V = g->part[1].view();
+      plan_add(pl, (const uint32_t*)w->hubq[1][cur].p, 0, c.tail[1][0], 1, 8, 0);
+      for (int b = 1; b < kNBucket; ++b)
+        plan_add(pl, (const uint32_t*)w->queue[1][cur].p + V.bstart[b], 0, c.tail[1][b], 1,
+                 gsh[b], b);
+      if (pl.nblocks) {
+        k_sssp_relax<false><<<pl.nblocks, kThreads, 0, st>>>(pl, A);
+        launches++;
+      }
+    }
+    GG_CUDA(cudaEventRecord(h->ev[1], st));
+    if (owords1) {
+      k_hsssp_out<<<grid_for(owords1, 256), 256, 0, st>>>(A, (uint32_t*)h->dmsg.p);
+      launches++;
+    }
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaMemcpyAsync(h->pin_in, h->dmsg.p, 16, cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaEventRecord(h->ev[2], st));
+    // Host: partition 0's round (Figure 20) while the GPU works.
+    const auto tc0 = Clock::now();
+    for (int k = 0; k < nt; ++k) {
+      ttouch[k].clear();
+      tdirty[k].clear();
+      tin[k] = 0;
+      tovf[k] = 0;
+    }
+    host_dynamic(nt, A0.size(), 1, [&](int k, uint64_t a, uint64_t b) {
+      for (uint64_t i = a; i < b; ++i) {
+        const uint32_t u = A0[i];
+        const uint64_t du = h->dist[u].load(std::memory_order_relaxed);
+        h->snap[u] = (uint32_t)du;
+        const int64_t e1 = h->off0[u + 1];
+        for (int64_t e = h->off0[u]; e < e1; ++e) {
+          uint64_t s = du + h->W0[e];
+          if (s >= kInf) {
+            tovf[k] = 1;
+            s = kInf - 1;
+          }
+          const uint32_t x = h->E0[e];
+          if (!(x & kRemote)) {
+            if (host_min(&h->dist[x], (uint32_t)s) && !h->touched[x].exchange(1))
+              ttouch[k].push_back(x);
+          } else {
+            const uint32_t idx = x & kIdMask;
+            if (host_min(&h->omsg[idx], (uint32_t)s) && !h->odirty[idx].exchange(1))
+              tdirty[k].push_back(idx);
+          }
+        }
+        tin[k] += e1 - h->off0[u];
+      }
+    });
+    ms_cpu += std::chrono::duration<double, std::milli>(Clock::now() - tc0).count();
+    // Exchange: the GPU's lowered slots come up and lower partition 0 ...
+    GG_CUDA(cudaEventSynchronize(h->ev[2]));
+    float gms = 0;
+    GG_CUDA(cudaEventElapsedTime(&gms, h->ev[0], h->ev[1]));
+    ms_gpu += gms;
+    const auto tx0 = Clock::now();
+    const uint32_t n1 = h->pin_in[0];
+    if (n1) {
+      GG_CUDA(cudaMemcpyAsync(h->pin_in + 4, (const uint32_t*)h->dmsg.p + 4, 8ull * n1,
+                              cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<uint32_t> in_touch;
+    for (uint32_t i = 0; i < n1; ++i) {
+      const uint32_t u = h->pin_in[4 + 2 * i], val = h->pin_in[4 + 2 * i + 1];
+      if (host_min(&h->dist[u], val) && !h->touched[u].exchange(1)) in_touch.push_back(u);
+    }
+    // ... and the host's lowered slots go down and lower partition 1.
+    uint32_t n0 = 0;
+    for (int k = 0; k < nt; ++k)
+      for (uint32_t idx : tdirty[k]) {
+        h->odirty[idx].store(0, std::memory_order_relaxed);
+        h->pin_out[2 * n0] = h->outbox0[idx];
+        h->pin_out[2 * n0 + 1] = h->omsg[idx].load(std::memory_order_relaxed);
+        ++n0;
+      }
+    if (n0) {
+      GG_CUDA(cudaMemcpyAsync(h->dmsg.p, h->pin_out, 8ull * n0, cudaMemcpyHostToDevice, st));
+      k_hsssp_in<<<std::min(grid_for(n0, 256), 152u * 8), 256, 0, st>>>(
+          A, (const uint32_t*)h->dmsg.p, n0);
+      launches++;
+    }
+    // Filter: partition 1 on the device (its words only), partition 0 on the host.
+    {
+      SsspArgs F = A;
+      k_sssp_filter<<<grid_for(words1, kThreads), kThreads, 0, st>>>(F, 0u, words1, kInf);
+      launches++;
+    }
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+    A0.clear();
+    auto filter = [&](uint32_t x) {
+      h->touched[x].store(0, std::memory_order_relaxed);
+      if (h->dist[x].load(std::memory_order_relaxed) < h->snap[x]) A0.push_back(x);
+    };
+    for (int k = 0; k < nt; ++k) {
+      for (uint32_t x : ttouch[k]) filter(x);
+      inspected += tin[k];
+      overflow |= tovf[k] != 0;
+    }
+    for (uint32_t x : in_touch) filter(x);
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
+    overflow |= hc->overflow != 0;
+    messages += (int64_t)n1 + n0;
+    ms_xchg += std::chrono::duration<double, std::milli>(Clock::now() - tx0).count();
+    cur = 1 - cur;
+  }
+  // Collect: the host partition's distances join the device's.
+  if (nv0) {
+    std::vector<uint32_t> d0(nv0);
+    for (uint32_t v = 0; v < nv0; ++v) d0[v] = h->dist[v].load(std::memory_order_relaxed);
+    GG_CUDA(cudaMemcpyAsync(w->dist[0].p, d0.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+  }
+  uint32_t* dd = dist;
+  if (at.out_mem == GRAPH_MEM_HOST) {
+    GG_TRY(ensure_stage(g, 4ull * g->n + 64));
+    dd = (uint32_t*)g->stage.p;
+  }
+  GG_TRY(launch_collect(g, w, dc, cur, dd, st));
+  launches++;
+  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  graph_status s = check_device_error(g);
+  if (!hc->clamped) overflow = false;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->supersteps = (int)rounds;
+    stats->edges_traversed = (int64_t)hc->reached_degree;
+    stats->edges_inspected = inspected;
+    stats->messages = messages;
+    stats->launches = launches;
+    stats->ms_compute = std::max(ms_cpu, ms_gpu);
+    stats->ms_exchange = ms_xchg;
+    stats->ms_total = std::chrono::duration<double, std::milli>(Clock::now() - t_start).count();
+  }
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->cpu_threads = nt;
+    info->cpu_vertices = nv0;
+    info->gpu_vertices = g->part[1].nv;
+    info->cpu_edges = P0.ne;
+    info->gpu_edges = g->part[1].ne;
+    info->ms_cpu_compute = ms_cpu;
+    info->ms_gpu_compute = ms_gpu;
+    info->ms_exchange = ms_xchg;
+  }
+  if (s == GRAPH_OK && overflow) {
+    set_error("a shortest distance reached 2^32 - 1");
+    return GRAPH_ERANGE;
+  }
   return s;
 }
