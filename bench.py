@@ -356,7 +356,7 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5):
+def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5, source=None):
     """PageRank with the paper's hybrid placement (pagerank_hybrid: partition 0 on the
     host's cores, partition 1 on the GPU, message arrays crossing every superstep) next to
     the GPU-only call on the same partition, for HIGH splits that give the host a share of
@@ -394,6 +394,41 @@ def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5):
             "exchange_ms_per_iter": round(h["ms_exchange"] / iters, 3),
             "messages_per_iter": st["messages"] // max(st["supersteps"], 1),
             "l1_vs_gpu_only": float((rr - rg).abs().sum())})
+        if source is not None:
+            # BFS (top-down, Figure 11) and SSSP (plain rounds, Figure 20) with the same
+            # placement, against the GPU-only calls in the same direction / order
+            s = int(source)
+            G.bfs_hybrid(H, s, want_parents=False)
+            t = time.perf_counter()
+            hl, _, bst = G.bfs_hybrid(H, s, want_parents=False, out="host")
+            hb = (time.perf_counter() - t) * 1e3
+            G.bfs(H, s, want_parents=False, direction="topdown")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            gl, _, _ = G.bfs(H, s, want_parents=False, direction="topdown", out="host")
+            gb = (time.perf_counter() - t) * 1e3
+            G.sssp_hybrid(H, s)
+            t = time.perf_counter()
+            hd, sst = G.sssp_hybrid(H, s, out="host")
+            hs = (time.perf_counter() - t) * 1e3
+            G.sssp(H, s)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            gd, _ = G.sssp(H, s, out="host")
+            gs = (time.perf_counter() - t) * 1e3
+            out["points"][-1].update({
+                "bfs_hybrid_ms": round(hb, 2), "bfs_gpu_only_topdown_ms": round(gb, 2),
+                "bfs_hybrid_gteps": bst["edges_traversed"] / (hb / 1e3) / 1e9,
+                "bfs_levels_equal": bool(np.array_equal(hl, gl)),
+                "bfs_cpu_ms": round(bst["hybrid"]["ms_cpu_compute"], 2),
+                "bfs_gpu_ms": round(bst["hybrid"]["ms_gpu_compute"], 2),
+                "bfs_exchange_ms": round(bst["hybrid"]["ms_exchange"], 2),
+                "sssp_hybrid_ms": round(hs, 2), "sssp_gpu_only_plain_ms": round(gs, 2),
+                "sssp_hybrid_gteps": sst["edges_traversed"] / (hs / 1e3) / 1e9,
+                "sssp_distances_equal": bool(np.array_equal(hd, gd)),
+                "sssp_cpu_ms": round(sst["hybrid"]["ms_cpu_compute"], 2),
+                "sssp_gpu_ms": round(sst["hybrid"]["ms_gpu_compute"], 2),
+                "sssp_exchange_ms": round(sst["hybrid"]["ms_exchange"], 2)})
     out["note"] = ("pagerank_hybrid vs pagerank on the same HIGH partition (edge_share: the "
                    "host's share of edge entries); the graph fits in HBM here, so the host "
                    "side is the slower processor")
@@ -876,7 +911,7 @@ def main():
     precision = None if a.no_precision else precision_report(G, H, g, ref,
                                                              iters_step=a.pr_iters)
     # Last, because it re-partitions the graph.
-    hybrid = None if a.no_hybrid else hybrid_report(G, H, m, torch)
+    hybrid = None if a.no_hybrid else hybrid_report(G, H, m, torch, source=srcs[0])
     nproc = os.cpu_count()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
