@@ -201,6 +201,14 @@ graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint32_t* parent
  * the frontier's edges with the edges of vertices some search has not reached, weighted
  * by alpha), alpha, max_supersteps and timing as for bfs; beta is unused. No parents.
  * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator.
+ * Superstep loop: with attr->timing == 0 the supersteps run as one CUDA graph launch, a
+ * conditional while loop whose body holds two supersteps; a one-thread control kernel after
+ * each superstep applies the termination vote, the max_supersteps cap and the direction
+ * rule on the device and sets the loop condition, so the host waits once per call instead
+ * of once per superstep. The graph is captured on the first call and replayed while the
+ * graph, k, direction, alpha and cap stay the same. With attr->timing != 0 the host drives
+ * the supersteps (one round trip each) so that the phases can be timed; both loops give
+ * the same levels and statistics except stats->launches.
  * Device workspace: 24 bytes per vertex, 16 per outbox slot and 4 * roundup(k, 4) per
  * vertex of level lanes, kept with the graph until it is re-partitioned or freed.
  * Errors: EINVAL, ESTATE (not partitioned), ETIMEOUT (max_supersteps), ENOMEM, ECUDA.

@@ -38,14 +38,54 @@ struct MsCounters {
   u64 gained;     // searches (bits) that reached a new vertex this level
 };
 
+// Device-side control of a graph-driven bfs_batch (one superstep after another inside a
+// CUDA graph while loop, no host round trip): the level, the direction of the next
+// superstep, the termination vote and the statistics.
+struct MsCtl {
+  uint32_t L;          // level the next superstep expands
+  uint32_t pull;       // direction of the next superstep
+  uint32_t done;       // no search gained a vertex (or the cap was reached)
+  uint32_t timeout;    // the superstep cap was reached
+  uint32_t push_steps, pull_steps;
+  u64 traversed, inspected, messages;
+  // parameters
+  u64 m;               // edge entries of the graph (the direction rule's first "unexplored")
+  double alpha;
+  int direction;
+  int pad;
+  int64_t cap;
+};
+
+// The captured superstep graph of a workspace, and what it was captured for.
+struct MsGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  DevBuf ctl;
+  uint32_t k = 0, K = 0;
+  int direction = -1;
+  double alpha = 0;
+  int64_t cap_steps = 0;
+  void* counters = nullptr;
+};
+
 struct MsWs {
   DevBuf seen[2], mask[2][2], lvl[2], ghost[2], omsg[2];
   uint32_t K = 0;  // level lanes per vertex the lvl buffers hold
+  MsGraph graph;
 };
+
+void free_msgraph(graph* g, MsWs* w) {
+  MsGraph& G = w->graph;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.cap) cudaStreamDestroy(G.cap);
+  dfree(g, G.ctl);
+  G = MsGraph();
+}
 
 void free_msbfs(graph* g) {
   if (!g->ms) return;
   MsWs* w = g->ms;
+  free_msgraph(g, w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->seen[p], &w->mask[p][0], &w->mask[p][1], &w->lvl[p], &w->ghost[p],
                      &w->omsg[p]};
@@ -72,8 +112,17 @@ struct MsArgs {
   MsCounters* ctr;
   u64 full;     // bits of the k searches
   uint32_t K;
-  uint32_t L;   // level being expanded
+  uint32_t L;   // level being expanded (the host-driven loop)
+  MsCtl* ctl;   // graph-driven loop: level, direction and termination on the device, else null
 };
+
+// Graph-driven loop: whether a compute / communication kernel of direction `pull` runs
+// this superstep (the other direction's kernels return at once); CTA-uniform.
+__device__ __forceinline__ bool ms_skip(const MsArgs& A, uint32_t pull) {
+  if (!A.ctl) return false;
+  const volatile MsCtl* c = A.ctl;
+  return c->done || c->pull != pull;
+}
 
 struct MsSources {
   uint32_t id[GRAPH_BATCH_MAX];
@@ -130,6 +179,7 @@ __device__ __forceinline__ void push_edges(const MsSide& S, u64 fm, const uint32
 // per kHubChunk-edge chunk); vertices outside every frontier are skipped.
 __global__ void __launch_bounds__(kThreads)
 k_ms_push(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
+  if (ms_skip(A, 0)) return;
   Cnt c;
   for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
     const Seg& G = plan.seg[find_seg(plan, vb)];
@@ -161,6 +211,7 @@ k_ms_push(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
 // searches that reached outbox[i] of the other partition q; ORed into q's next mask less
 // what q has seen, then cleared for the next level.
 __global__ void __launch_bounds__(kThreads) k_ms_exchange(const __grid_constant__ MsArgs A) {
+  if (ms_skip(A, 0)) return;
   Cnt c;
   const uint64_t nout0 = A.side[0].P.nout;
   const uint64_t total = nout0 + A.side[1].P.nout;
@@ -184,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_exchange(const __grid_constant_
 // Communication phase before a pull level: ghost mask i of p = frontier mask of outbox
 // target i in the other partition.
 __global__ void k_ms_publish(const __grid_constant__ MsArgs A) {
+  if (ms_skip(A, 1)) return;
   const uint64_t nout0 = A.side[0].P.nout;
   const uint64_t total = nout0 + A.side[1].P.nout;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
@@ -205,6 +257,7 @@ __device__ __forceinline__ u64 frontier_of(const MsSide& S, uint32_t x) {
 // vertex is scanned chunk by chunk, one CTA per chunk, each warp a contiguous slice.
 __global__ void __launch_bounds__(kThreads)
 k_ms_pull(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
+  if (ms_skip(A, 1)) return;
   Cnt c;
   for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
     const Seg& G = plan.seg[find_seg(plan, vb)];
@@ -274,6 +327,12 @@ k_ms_pull(const __grid_constant__ Plan plan, const __grid_constant__ MsArgs A) {
 // cleared to serve as the next level's next buffer); new (vertex, search) pairs get level
 // L + 1 in the vertex's level lanes, written by the whole warp one vertex at a time.
 __global__ void __launch_bounds__(256) k_ms_advance(const __grid_constant__ MsArgs A) {
+  uint32_t L = A.L;
+  if (A.ctl) {
+    const volatile MsCtl* ctl = A.ctl;
+    if (ctl->done) return;
+    L = ctl->L;
+  }
   Cnt c;
   const uint32_t nv0 = A.side[0].P.nv;
   const uint64_t total = (uint64_t)nv0 + A.side[1].P.nv;
@@ -310,11 +369,62 @@ __global__ void __launch_bounds__(256) k_ms_advance(const __grid_constant__ MsAr
       const u64 mj = __shfl_sync(kFull, nx, j);
       uint32_t* row = A.side[pj].lvl + (size_t)vj * A.K;
       const uint32_t l = lane_id();
-      if ((mj >> l) & 1ull) row[l] = A.L + 1;
-      if ((mj >> (l + 32)) & 1ull) row[l + 32] = A.L + 1;
+      if ((mj >> l) & 1ull) row[l] = L + 1;
+      if ((mj >> (l + 32)) & 1ull) row[l + 32] = L + 1;
     }
   }
   flush(c, A.ctr);
+}
+
+// Graph-driven loop, before the first superstep: the statistics start from the seeding
+// (k_ms_init), level 0 is a push, the counters are cleared for it.
+__global__ void k_ms_ctl_init(MsCounters* ctr, MsCtl* ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const MsCounters c = *ctr;
+  ctl->L = 0;
+  ctl->pull = 0;
+  ctl->done = c.nf == 0;
+  ctl->timeout = 0;
+  ctl->push_steps = ctl->pull_steps = 0;
+  ctl->traversed = c.traversed;
+  ctl->inspected = ctl->messages = 0;
+  *ctr = MsCounters{};
+}
+
+// Graph-driven loop, after each superstep: the statistics, the termination vote (no
+// search gained a vertex; Section 4.1: every partition votes to finish), the cap, and the
+// next level's direction by the same rule the host loop applies (Beamer et al.: pull when
+// the frontier's edges times alpha exceed the edges of vertices some search has not
+// reached); the counters are cleared for the next superstep. With set_cond it sets the
+// while loop's condition (0 ends the loop).
+__global__ void k_ms_ctl_step(MsCounters* ctr, MsCtl* ctl, cudaGraphConditionalHandle h,
+                              int set_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!ctl->done) {
+    const MsCounters c = *ctr;
+    ctl->inspected += c.inspected;
+    ctl->messages += c.messages;
+    ctl->traversed += c.traversed;
+    if (ctl->pull) ctl->pull_steps++;
+    else ctl->push_steps++;
+    if (c.nf == 0) {
+      ctl->done = 1;
+    } else {
+      ctl->L = ctl->L + 1;
+      if ((int64_t)ctl->L >= ctl->cap) {
+        ctl->done = 1;
+        ctl->timeout = 1;
+      } else if (ctl->direction == GRAPH_BFS_TOPDOWN) {
+        ctl->pull = 0;
+      } else if (ctl->direction == GRAPH_BFS_BOTTOMUP) {
+        ctl->pull = 1;
+      } else {
+        ctl->pull = (double)c.mf * ctl->alpha > (double)c.mu;
+      }
+    }
+    *ctr = MsCounters{};
+  }
+  if (set_cond) cudaGraphSetConditional(h, ctl->done ? 0u : 1u);
 }
 
 __global__ void k_ms_init(const __grid_constant__ MsArgs A, const __grid_constant__ MsSources src,
@@ -493,6 +603,8 @@ Plan make_plan(graph* g) {
 }
 
 constexpr unsigned kSweepGrid = 152 * 8;
+
+uint64_t nout_ms(const graph* g) { return (uint64_t)g->part[0].nout + g->part[1].nout; }
 
 // One superstep (compute, communication, advance) with A's counters cleared first.
 graph_status launch_superstep(graph* g, const MsArgs& A, const Plan& pl, bool pull,
@@ -702,6 +814,76 @@ int bfs_lanes_poll(graph* g, BfsLanes* b, uint64_t* finished, int* steps,
 
 using namespace gg;
 
+namespace gg {
+namespace {
+
+// The supersteps of bfs_batch as one CUDA graph: a while loop (conditional node) whose
+// body is two supersteps (buffers of the even and odd levels), each of them the kernels of
+// both directions (the one the control block did not choose returns at once), the advance
+// and the control step; the second control step sets the loop condition. Captured once
+// per workspace, lane count, direction rule and cap; replayed by later calls.
+graph_status ensure_ms_graph(graph* g, MsWs* w, uint32_t k, int direction, double alpha,
+                             int64_t cap, const Plan& pl) {
+  MsGraph& G = w->graph;
+  if (G.exec && G.k == k && G.K == w->K && G.direction == direction && G.alpha == alpha &&
+      G.cap_steps == cap && G.counters == g->counters.p)
+    return GRAPH_OK;
+  free_msgraph(g, w);
+  GG_TRY(dalloc(g, G.ctl, sizeof(MsCtl)));
+  GG_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+  cudaGraph_t gr = nullptr;
+  GG_CUDA(cudaGraphCreate(&gr, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(G.cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    return cuda_fail(e, "building the superstep graph", __FILE__, __LINE__);
+  }
+  const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
+  const uint64_t nvt = (uint64_t)g->part[0].nv + g->part[1].nv;
+  const unsigned adv = grid_for(nvt, 256) < kSweepGrid ? grid_for(nvt, 256) : kSweepGrid;
+  MsCounters* ctr = (MsCounters*)g->counters.p;
+  MsCtl* ctl = (MsCtl*)G.ctl.p;
+  for (int cur = 0; cur < 2; ++cur) {
+    MsArgs A = make_args(g, cur, k, 0);
+    A.ctl = ctl;
+    if (pl.nblocks) k_ms_push<<<plan_grid(pl.nblocks), kThreads, 0, G.cap>>>(pl, A);
+    if (nout) k_ms_exchange<<<kSweepGrid, kThreads, 0, G.cap>>>(A);
+    if (nout) k_ms_publish<<<kSweepGrid, 256, 0, G.cap>>>(A);
+    if (pl.nblocks) k_ms_pull<<<plan_grid(pl.nblocks), kThreads, 0, G.cap>>>(pl, A);
+    k_ms_advance<<<adv, 256, 0, G.cap>>>(A);
+    k_ms_ctl_step<<<1, 32, 0, G.cap>>>(ctr, ctl, h, cur == 1);
+  }
+  cudaGraph_t body = nullptr;
+  e = cudaStreamEndCapture(G.cap, &body);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return cuda_fail(e, "capturing the supersteps", __FILE__, __LINE__);
+  }
+  G.k = k;
+  G.K = w->K;
+  G.direction = direction;
+  G.alpha = alpha;
+  G.cap_steps = cap;
+  G.counters = g->counters.p;
+  return GRAPH_OK;
+}
+
+}  // namespace
+}  // namespace gg
+
 extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t k,
                                   uint32_t* levels, const bfs_attr* attr, graph_stats* stats) {
   if (!g || !sources || !levels) {
@@ -753,14 +935,53 @@ extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t 
   k_ms_init<<<1, 64, 0, st>>>(make_args(g, cur, k, 0), src, k, (const uint32_t*)g->g2l.p);
   GG_CUDA(cudaGetLastError());
   MsCounters* hc = (MsCounters*)g->host_counters;
-  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
-  GG_CUDA(cudaStreamSynchronize(st));
-  timer.mark(2);
   const Plan pl = make_plan(g);
-  int64_t traversed = (int64_t)hc->traversed, inspected = 0, messages = 0, launches = 1;
+  int64_t traversed = 0, inspected = 0, messages = 0, launches = 1;
   int push_steps = 0, pull_steps = 0;
   uint64_t mu = (uint64_t)g->m;
   int64_t L = 0;
+  if (!at.timing) {
+    // Graph-driven: the supersteps and their termination vote run on the device.
+    const graph_status gs = ensure_ms_graph(g, w, k, at.direction, alpha, cap, pl);
+    if (gs != GRAPH_OK) {
+      free_msgraph(g, w);
+      return gs;
+    }
+    MsCtl hctl;
+    memset(&hctl, 0, sizeof(hctl));
+    hctl.m = (u64)g->m;
+    hctl.alpha = alpha;
+    hctl.direction = at.direction;
+    hctl.cap = cap;
+    MsCtl* dctl = (MsCtl*)w->graph.ctl.p;
+    GG_CUDA(cudaMemcpyAsync(dctl, &hctl, sizeof(hctl), cudaMemcpyHostToDevice, st));
+    k_ms_ctl_init<<<1, 32, 0, st>>>((MsCounters*)g->counters.p, dctl);
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaGraphLaunch(w->graph.exec, st));
+    GG_CUDA(cudaMemcpyAsync(&hctl, dctl, sizeof(hctl), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    if (hctl.timeout) {
+      set_error("bfs_batch reached the superstep cap (%lld)", (long long)cap);
+      return GRAPH_ETIMEOUT;
+    }
+    push_steps = (int)hctl.push_steps;
+    pull_steps = (int)hctl.pull_steps;
+    L = push_steps + pull_steps;
+    traversed = (int64_t)hctl.traversed;
+    inspected = (int64_t)hctl.inspected;
+    messages = (int64_t)hctl.messages;
+    // kernels: the control init, then per replay of the loop body its two supersteps, each
+    // with both directions' compute and communication kernels, the advance and the control
+    // step (the kernels of the direction not taken return at once)
+    const int64_t per = 2 * ((pl.nblocks ? 2 : 0) + (nout_ms(g) ? 2 : 0) + 2);
+    launches += 1 + per * std::max<int64_t>(1, (L + 1) / 2);
+    cur = (int)(L & 1);
+  }
+  if (at.timing) {
+  GG_CUDA(cudaMemcpyAsync(hc, g->counters.p, sizeof(MsCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
+  traversed = (int64_t)hc->traversed;
   for (;; ++L) {
     const MsCounters c = *hc;
     if (c.nf == 0) break;
@@ -784,6 +1005,7 @@ extern "C" graph_status bfs_batch(graph_t* g, const uint32_t* sources, uint32_t 
     messages += (int64_t)hc->messages;
     traversed += (int64_t)hc->traversed;
     cur = 1 - cur;
+  }
   }
   uint32_t* dl = levels;
   const size_t bytes = 4ull * k * g->n;

@@ -134,3 +134,46 @@ def test_batch_after_repartition_and_wider_batch(gpu):
     gpu.graph_partition(H, "degree", degree_threshold=16)
     check_batch(gpu, H, g, srcs[:9])
     H.free()
+
+
+STAT_KEYS = ("supersteps", "topdown_steps", "bottomup_steps", "edges_traversed",
+             "edges_inspected", "messages")
+
+
+@pytest.mark.parametrize("direction", ["auto", "topdown", "bottomup"])
+def test_batch_device_loop_matches_host_loop(gpu, direction):
+    """Without timing the supersteps run as one CUDA graph while loop (termination vote,
+    cap and direction rule on the device); with timing the host drives them. Same levels,
+    same step counts and statistics, for several alphas (the direction rule's switch
+    point) and batch widths (each change re-captures the graph)."""
+    g = rmat_graph(14)
+    H = gpu.graph_load_csr(g.offsets, g.cols)
+    gpu.graph_partition(H, "degree", degree_threshold=64)
+    srcs = synth.sources(g, 64, seed=5)
+    for k, alpha in ((40, 0.0), (3, 4.0), (64, 40.0), (40, 0.0)):
+        a, sa = gpu.bfs_batch(H, srcs[:k], direction=direction, alpha=alpha, out="host")
+        b, sb = gpu.bfs_batch(H, srcs[:k], direction=direction, alpha=alpha, out="host",
+                              timing=True)
+        assert np.array_equal(a, b)
+        for key in STAT_KEYS:
+            assert sa[key] == sb[key], key
+        check_batch(gpu, H, g, srcs[:k], direction)
+    H.free()
+
+
+@pytest.mark.parametrize("timing", [False, True])
+def test_batch_cap_boundary_both_loops(gpu, timing):
+    """A 10-vertex path from vertex 0 takes 10 supersteps: a cap of 10 is enough, 9 is not;
+    odd and even superstep counts end the device loop in either half of its body."""
+    g = synth.path(10)
+    H = gpu.graph_load_csr(g.offsets, g.cols)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(g.n, 0.5, 3))
+    lv, st = gpu.bfs_batch(H, [0], max_supersteps=10, out="host", timing=timing)
+    assert np.array_equal(lv[0], np.arange(10, dtype=np.uint32)) and st["supersteps"] == 10
+    with pytest.raises(gpu.GraphError, match="cap"):
+        gpu.bfs_batch(H, [0], max_supersteps=9, timing=timing)
+    for s, steps in ((1, 9), (2, 8), (5, 6)):
+        lv, st = gpu.bfs_batch(H, [s], out="host", timing=timing)
+        assert st["supersteps"] == steps
+        assert np.array_equal(lv[0], np.abs(np.arange(10) - s).astype(np.uint32))
+    H.free()
