@@ -263,6 +263,13 @@ graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist, const sssp_attr* 
  * (delta = 0), which is the faster choice for batches.
  * stats->edges_traversed is the sum over the k searches of each search's TEPS numerator;
  * edges_inspected counts edge entries read (once per pass, whatever the number of lanes).
+ * Superstep loop: with attr->timing == 0 the rounds run as one CUDA graph launch (a
+ * conditional while loop; one-thread control kernels move the near-far threshold, build
+ * each round's relax plan from the queue tails, apply the termination vote and the cap,
+ * and set the loop condition), so the host waits once per call; the graph is captured on
+ * the first call after a partition and replayed. With attr->timing != 0 the host drives
+ * the rounds so that the phases can be timed. Both give the same distances and statistics
+ * except stats->launches.
  * Device workspace: about 76 bytes per vertex (distance and queued rows, lane mask, queues)
  * and 32 per outbox slot, kept with the graph until it is re-partitioned or freed.
  * Errors: EINVAL, ESTATE, ETIMEOUT, ERANGE, ENOMEM, ECUDA.

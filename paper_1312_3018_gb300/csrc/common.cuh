@@ -85,13 +85,13 @@ struct Plan {
   uint32_t nblocks;
 };
 
-inline uint32_t seg_blocks(uint32_t count, int gshift) {
+__host__ __device__ inline uint32_t seg_blocks(uint32_t count, int gshift) {
   uint32_t per = (gshift >= 8) ? 1u : (uint32_t)(kThreads >> gshift);
   return (count + per - 1) / per;
 }
 
-inline void plan_add(Plan& pl, const uint32_t* items, uint32_t v0, uint32_t count, int part,
-                     int gshift, int bucket) {
+__host__ __device__ inline void plan_add(Plan& pl, const uint32_t* items, uint32_t v0,
+                                         uint32_t count, int part, int gshift, int bucket) {
   if (count == 0) return;
   Seg& s = pl.seg[pl.nseg++];
   s.items = items;

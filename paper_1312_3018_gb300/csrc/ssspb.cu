@@ -41,14 +41,49 @@ struct SbCounters {
   uint32_t clamped;
 };
 
+// Device-side control of a graph-driven sssp_batch (the rounds inside one CUDA graph while
+// loop, no host round trip): the near-far threshold, the termination vote, the cap, the
+// statistics and the round's relax plan, which a one-thread kernel builds from the queue
+// tails the filter left.
+struct SbCtl {
+  uint32_t done;       // nothing queued and nothing waiting (or the cap was reached)
+  uint32_t timeout;    // the superstep cap was reached
+  uint32_t refilter;   // this half of the loop body moves the near-far threshold first
+  uint32_t round;      // this half of the loop body runs a round
+  uint32_t tau, delta;
+  uint32_t overflow;
+  uint32_t bodies;     // loop body executions
+  int64_t rounds, cap;
+  unsigned long long inspected, messages;
+  Plan plan;
+};
+
+// The captured round graph of a workspace and the counters it was captured with.
+struct SbGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  DevBuf ctl;
+  void* counters = nullptr;
+};
+
 struct SbWs {
   DevBuf dist[2], snap[2], tbits[2], amask[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
+  SbGraph graph;
 };
+
+void free_sbgraph(graph* g, SbWs* w) {
+  SbGraph& G = w->graph;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.cap) cudaStreamDestroy(G.cap);
+  dfree(g, G.ctl);
+  G = SbGraph();
+}
 
 void free_ssspb(graph* g) {
   if (!g->sb) return;
   SbWs* w = g->sb;
+  free_sbgraph(g, w);
   for (int p = 0; p < 2; ++p) {
     DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->tbits[p],    &w->amask[p],
                      &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1],
@@ -76,7 +111,18 @@ struct SbSide {
 struct SbArgs {
   SbSide side[2];
   SbCounters* ctr;
+  SbCtl* ctl;   // graph-driven loop, else null
+  int slot;     // graph-driven loop: 1 the threshold move's filter, 2 the round's kernels
 };
+
+// Graph-driven loop: whether this kernel's slot is idle in this half of the loop body (the
+// other kernels of the body then return at once); CTA-uniform.
+__device__ __forceinline__ bool sb_skip(const SbArgs& A) {
+  if (!A.ctl) return false;
+  const volatile SbCtl* c = A.ctl;
+  if (c->done) return true;
+  return A.slot == 1 ? !c->refilter : !c->round;
+}
 
 __device__ __forceinline__ uint32_t sb_sat_add(uint32_t a, uint32_t b, bool& ovf) {
   const uint64_t s = (uint64_t)a + (uint64_t)b;
@@ -179,8 +225,7 @@ __device__ __forceinline__ void relax_edges_b(const SbSide& S, const uint32_t* d
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_sb_relax(const __grid_constant__ Plan plan, const __grid_constant__ SbArgs A) {
+__device__ __forceinline__ void sb_relax(const Plan& plan, const SbArgs& A) {
   unsigned long long insp = 0;
   bool ovf = false;
   for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
@@ -232,9 +277,29 @@ k_sb_relax(const __grid_constant__ Plan plan, const __grid_constant__ SbArgs A) 
   sb_flush(insp, 0, ovf, A.ctr);
 }
 
+__global__ void __launch_bounds__(kThreads)
+k_sb_relax(const __grid_constant__ Plan plan, const __grid_constant__ SbArgs A) {
+  sb_relax(plan, A);
+}
+
+// The graph-driven loop's relax: the plan the control kernel built, copied to shared
+// memory; a fixed grid walks its blocks.
+__global__ void __launch_bounds__(kThreads)
+k_sb_relax_dev(const Plan* plan, const __grid_constant__ SbArgs A) {
+  if (sb_skip(A)) return;
+  __shared__ Plan sp;
+  constexpr int kWords = (int)(sizeof(Plan) / 4);
+  static_assert(sizeof(Plan) % 4 == 0, "plan copied as words");
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(&sp)[i] = reinterpret_cast<const volatile uint32_t*>(plan)[i];
+  __syncthreads();
+  sb_relax(sp, A);
+}
+
 // Communication phase: apply the dirty outbox rows of p to their owners in q.
 __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant__ SbArgs A,
                                                           uint32_t words0) {
+  if (sb_skip(A)) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i < words0 ? 0 : 1;
   const uint32_t word = p == 0 ? i : i - words0;
@@ -271,6 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant_
 __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ SbArgs A,
                                                         uint32_t words0, uint32_t words,
                                                         uint32_t tau) {
+  if (sb_skip(A)) return;
+  if (A.ctl) tau = ((const volatile SbCtl*)A.ctl)->tau;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
@@ -319,6 +386,91 @@ __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ 
   if (lane_id() == 0 && nfar) {
     atomicAdd(&A.ctr->far, nfar);
     atomicMax(&A.ctr->far_key, key);
+  }
+}
+
+__device__ __forceinline__ uint64_t sb_active(const SbCounters& c) {
+  uint64_t a = 0;
+  for (int p = 0; p < 2; ++p)
+    for (int b = 0; b < kNBucket; ++b) a += c.tail[p][b];
+  return a;
+}
+
+// Graph-driven loop, first kernel of each half of the body: when nothing is queued but
+// lanes wait at or above the near-far threshold, the threshold moves to their smallest
+// distance + delta and the counters are cleared for the filter that queues what now lies
+// below it.
+__global__ void k_sb_ctl_pre(SbCounters* ctr, SbCtl* ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl->refilter = 0;
+  if (ctl->done) return;
+  const SbCounters c = *ctr;
+  if (sb_active(c) == 0 && c.far != 0) {
+    const uint64_t t = (uint64_t)(~c.far_key) + ctl->delta;
+    ctl->tau = t >= kInf ? kInf : (uint32_t)t;
+    ctl->refilter = 1;
+    *ctr = SbCounters();
+  }
+}
+
+// The round's queues of one parity, for the plan the control kernel builds.
+struct SbQueues {
+  const uint32_t* hubq[2];
+  const uint32_t* queue[2];
+  uint32_t bstart[2][kNBucket];
+};
+
+// Graph-driven loop, before the round: the termination vote (nothing queued and nothing
+// waiting: every search has converged, Section 4.1), the cap, and the relax plan from the
+// queue tails (hub chunks, then the vertex buckets of each partition); the counters are
+// cleared for the round. Nothing queued while lanes still wait leaves the threshold move
+// to the next half of the body.
+__global__ void k_sb_ctl_plan(SbCounters* ctr, SbCtl* ctl, const __grid_constant__ SbQueues q) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl->round = 0;
+  if (ctl->done) return;
+  const SbCounters c = *ctr;
+  if (sb_active(c) == 0) {
+    if (c.far == 0) ctl->done = 1;
+    return;
+  }
+  if (ctl->rounds >= ctl->cap) {
+    ctl->done = 1;
+    ctl->timeout = 1;
+    return;
+  }
+  Plan pl;
+  pl.nseg = 0;
+  pl.nblocks = 0;
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    plan_add(pl, q.hubq[p], 0, c.tail[p][0], p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, q.queue[p] + q.bstart[p][b], 0, c.tail[p][b], p, gsh[b], b);
+  }
+  ctl->plan = pl;
+  *ctr = SbCounters();
+  ctl->round = 1;
+}
+
+// Graph-driven loop, after the round: statistics, and the vote for the next round taken
+// at once when nothing is queued or waiting. With set_cond it sets the while loop's
+// condition (0 ends the loop).
+__global__ void k_sb_ctl_post(SbCounters* ctr, SbCtl* ctl, cudaGraphConditionalHandle h,
+                              int set_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!ctl->done && ctl->round) {
+    const SbCounters c = *ctr;
+    ctl->inspected += c.inspected;
+    ctl->messages += c.messages;
+    ctl->overflow |= c.overflow;
+    ctl->rounds++;
+    ctl->round = 0;
+    if (sb_active(c) == 0 && c.far == 0) ctl->done = 1;
+  }
+  if (set_cond) {
+    ctl->bodies++;
+    cudaGraphSetConditional(h, ctl->done ? 0u : 1u);
   }
 }
 
@@ -527,6 +679,75 @@ graph_status launch_collect(graph* g, SbWs* w, SbCounters* ctr, int cur, const O
   const SbArgs A = make_args(g, w, ctr, cur);
   k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, rows, ctr);
   GG_CUDA(cudaGetLastError());
+  return GRAPH_OK;
+}
+
+// The rounds of sssp_batch as one CUDA graph: a while loop (conditional node) whose body is
+// two halves, one per queue parity, each: threshold move (control kernel, then the filter
+// appending into the queues this half reads), plan (control kernel), relax, exchange,
+// filter (appending into the other parity's queues) and the post-round control kernel; the
+// second half's control kernel sets the loop condition. Kernels whose slot is idle return
+// at once. Captured once per workspace and counters buffer.
+graph_status ensure_sb_graph(graph* g, SbWs* w) {
+  SbGraph& G = w->graph;
+  if (G.exec && G.counters == g->counters.p) return GRAPH_OK;
+  free_sbgraph(g, w);
+  GG_TRY(dalloc(g, G.ctl, sizeof(SbCtl)));
+  GG_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+  cudaGraph_t gr = nullptr;
+  GG_CUDA(cudaGraphCreate(&gr, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(G.cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    return cuda_fail(e, "building the round graph", __FILE__, __LINE__);
+  }
+  SbCounters* ctr = (SbCounters*)g->counters.p;
+  SbCtl* ctl = (SbCtl*)G.ctl.p;
+  const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
+  const uint32_t owords0 = (uint32_t)w->owords[0], owords = owords0 + (uint32_t)w->owords[1];
+  for (int cur = 0; cur < 2; ++cur) {
+    SbArgs R = make_args(g, w, ctr, 1 - cur);  // the threshold move queues into `cur`
+    R.ctl = ctl;
+    R.slot = 1;
+    SbArgs A = make_args(g, w, ctr, cur);
+    A.ctl = ctl;
+    A.slot = 2;
+    SbQueues q;
+    memset(&q, 0, sizeof(q));
+    for (int p = 0; p < 2; ++p) {
+      const PartView V = g->part[p].view();
+      q.hubq[p] = (const uint32_t*)w->hubq[p][cur].p;
+      q.queue[p] = (const uint32_t*)w->queue[p][cur].p;
+      for (int b = 0; b < kNBucket; ++b) q.bstart[p][b] = V.bstart[b];
+    }
+    k_sb_ctl_pre<<<1, 32, 0, G.cap>>>(ctr, ctl);
+    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, G.cap>>>(R, words0, words, kInf);
+    k_sb_ctl_plan<<<1, 32, 0, G.cap>>>(ctr, ctl, q);
+    k_sb_relax_dev<<<plan_grid(~0u), kThreads, 0, G.cap>>>(&ctl->plan, A);
+    if (owords) k_sb_exchange<<<grid_for(owords, kThreads), kThreads, 0, G.cap>>>(A, owords0);
+    k_sb_filter<<<grid_for(words, kThreads), kThreads, 0, G.cap>>>(A, words0, words, kInf);
+    k_sb_ctl_post<<<1, 32, 0, G.cap>>>(ctr, ctl, h, cur == 1);
+  }
+  cudaGraph_t body = nullptr;
+  e = cudaStreamEndCapture(G.cap, &body);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return cuda_fail(e, "capturing the rounds", __FILE__, __LINE__);
+  }
+  G.counters = g->counters.p;
   return GRAPH_OK;
 }
 
@@ -739,13 +960,43 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
   GG_TRY(launch_start(g, w, dc, sources, k, st));
-  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
-  GG_CUDA(cudaStreamSynchronize(st));
-  timer.mark(2);
   int64_t inspected = 0, messages = 0, launches = 2, rounds = 0;
   bool overflow = false;
   int cur = 0;
   uint32_t tau = at.delta ? at.delta : kInf;  // the sources have distance 0 < delta
+  if (!at.timing) {
+    // Graph-driven: the rounds, the threshold moves and the termination vote run on the
+    // device; the host waits once.
+    const graph_status gs = ensure_sb_graph(g, w);
+    if (gs != GRAPH_OK) {
+      free_sbgraph(g, w);
+      return gs;
+    }
+    SbCtl hctl;
+    memset(&hctl, 0, sizeof(hctl));
+    hctl.tau = tau;
+    hctl.delta = at.delta;
+    hctl.cap = cap;
+    SbCtl* dctl = (SbCtl*)w->graph.ctl.p;
+    GG_CUDA(cudaMemcpyAsync(dctl, &hctl, sizeof(hctl), cudaMemcpyHostToDevice, st));
+    GG_CUDA(cudaGraphLaunch(w->graph.exec, st));
+    GG_CUDA(cudaMemcpyAsync(&hctl, dctl, sizeof(hctl), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    if (hctl.timeout) {
+      set_error("sssp_batch reached the superstep cap (%lld)", (long long)cap);
+      return GRAPH_ETIMEOUT;
+    }
+    rounds = hctl.rounds;
+    inspected = (int64_t)hctl.inspected;
+    messages = (int64_t)hctl.messages;
+    overflow = hctl.overflow != 0;
+    // per body execution: two halves of pre, filter, plan, relax, exchange, filter, post
+    const uint64_t owords = w->owords[0] + w->owords[1];
+    launches += (int64_t)hctl.bodies * 2 * (owords ? 7 : 6);
+  } else {
+  GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  timer.mark(2);
   for (;; ++rounds) {
     SbCounters c = *hc;
     while (active_count(c) == 0 && c.far != 0) {
@@ -769,6 +1020,7 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
     messages += (int64_t)hc->messages;
     overflow |= hc->overflow != 0;
     cur = 1 - cur;
+  }
   }
   uint32_t* dd = dist;
   if (at.out_mem == GRAPH_MEM_HOST) {

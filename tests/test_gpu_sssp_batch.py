@@ -152,3 +152,51 @@ def test_sssp_batch_overflow_reports_range_error(gpu):
     with pytest.raises(gpu.GraphError, match="out of range"):
         gpu.sssp_batch(H, [0, 3])
     H.free()
+
+
+@pytest.mark.parametrize("delta", [0, 1, 16, 300])
+def test_sssp_batch_device_loop_matches_host_loop(gpu, delta):
+    """Without timing the rounds run as one CUDA graph while loop (threshold moves, the
+    termination vote and the cap on the device); with timing the host drives them. Same
+    distances and TEPS numerator, plain rounds and near-far order, on two partitions (the
+    graph is captured again after re-partitioning). Round and relaxation counts are
+    compared loosely: a vertex relaxes with the newest distances of its row, which depend
+    on the order in which the round's atomic minima land, so the counts vary slightly from
+    call to call in either loop."""
+    g = rmat_graph(13)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    srcs = [int(s) for s in synth.sources(g, 8, seed=4)]
+    for T in (64, 1 << 30):
+        gpu.graph_partition(H, "degree", degree_threshold=T)
+        for k in (8, 3):
+            a, sa = gpu.sssp_batch(H, srcs[:k], out="host", delta=delta)
+            b, sb = gpu.sssp_batch(H, srcs[:k], out="host", delta=delta, timing=True)
+            assert np.array_equal(a, b)
+            assert sa["edges_traversed"] == sb["edges_traversed"]
+            assert abs(sa["supersteps"] - sb["supersteps"]) <= 2
+            assert abs(sa["edges_inspected"] - sb["edges_inspected"]) <= 0.1 * sb["edges_inspected"]
+            for row, s in enumerate(srcs[:k]):
+                assert np.array_equal(a[row], oracle.sssp(g.n, g.offsets, g.cols, g.weights, s))
+    H.free()
+
+
+@pytest.mark.parametrize("timing", [False, True])
+@pytest.mark.parametrize("delta", [0, 2])
+def test_sssp_batch_cap_boundary_both_loops(gpu, timing, delta):
+    """The exact number of rounds a search needs is enough as a cap and one fewer is not,
+    in both loops; odd and even round counts end the device loop in either half of its
+    body."""
+    g = synth.from_edges(12, [(i, i + 1) for i in range(11)], w=[1] * 11)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(g.n, 0.5, 5))
+    for s in (0, 3, 6):
+        ref = np.abs(np.arange(12) - s).astype(np.uint32)
+        d, st = gpu.sssp_batch(H, [s], out="host", delta=delta, timing=timing)
+        assert np.array_equal(d[0], ref)
+        r = st["supersteps"]
+        d, _ = gpu.sssp_batch(H, [s], out="host", delta=delta, timing=timing,
+                              max_supersteps=r)
+        assert np.array_equal(d[0], ref)
+        with pytest.raises(gpu.GraphError, match="cap"):
+            gpu.sssp_batch(H, [s], delta=delta, timing=timing, max_supersteps=r - 1)
+    H.free()
