@@ -700,10 +700,18 @@ def main():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, bst = G.bfs_batch(H, bsrc, blv, timing=True)
+            _, bst = G.bfs_batch(H, bsrc, blv)
             e1.record(stream)
             torch.cuda.synchronize()
             bms.append(e0.elapsed_time(e1))
+        # the host-driven loop (one round trip per superstep) with its phase times
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, bst_host = G.bfs_batch(H, bsrc, blv, timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        host_loop_ms = e0.elapsed_time(e1)
         del blv
         single_ms, single_e = 0.0, 0
         G.bfs(H, int(bsrc[0]), lv, want_parents=False)
@@ -723,11 +731,16 @@ def main():
                  "single_gteps": single_e / (single_ms / 1e3) / 1e9,
                  "speedup": single_ms / best, "supersteps": bst["supersteps"],
                  "push_steps": bst["topdown_steps"], "pull_steps": bst["bottomup_steps"],
-                 "ms_compute": round(bst["ms_compute"], 3),
-                 "ms_exchange": round(bst["ms_exchange"], 3),
+                 "ms_compute": round(bst_host["ms_compute"], 3),
+                 "ms_exchange": round(bst_host["ms_exchange"], 3),
+                 "host_loop_ms": round(host_loop_ms, 3),
                  "edges_inspected": bst["edges_inspected"],
-                 "note": "bfs_batch, levels only, k x n uint32 device output; best of 3; "
-                         "singles are bfs() calls without parents on the same sources"}
+                 "launches": bst["launches"],
+                 "note": "bfs_batch, levels only, k x n uint32 device output; best of 3 of "
+                         "the graph-driven loop (supersteps in one CUDA graph while loop); "
+                         "host_loop_ms, ms_compute, ms_exchange: one call of the host-driven "
+                         "loop with phase timing; singles are bfs() calls without parents on "
+                         "the same sources"}
 
     # Batched SSSP: the first 8 sources as one sssp_batch call (plain rounds, shared edge
     # reads), against the same 8 searches one sssp() call each in plain rounds and in the
@@ -742,10 +755,17 @@ def main():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, sst = G.sssp_batch(H, ksrc, bd, timing=True)
+            _, sst = G.sssp_batch(H, ksrc, bd)
             e1.record(stream)
             torch.cuda.synchronize()
             sms_.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.sssp_batch(H, ksrc, bd, timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sssp_host_loop_ms = e0.elapsed_time(e1)
         # the same batch in near-far order (one threshold for all lanes), for reference
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -771,6 +791,7 @@ def main():
         best = min(sms_)
         batch_sssp = {"k": len(ksrc), "ms": round(best, 3),
                       "near_far_batch_ms": round(nf_batch_ms, 3),
+                      "host_loop_ms": round(sssp_host_loop_ms, 3),
                       "gteps": sst["edges_traversed"] / (best / 1e3) / 1e9,
                       "supersteps": sst["supersteps"],
                       "edges_inspected": sst["edges_inspected"],
@@ -779,7 +800,9 @@ def main():
                       "single_near_far_ms_total": round(singles[a.sssp_delta][0], 3),
                       "speedup_vs_near_far": singles[a.sssp_delta][0] / best,
                       "note": "sssp_batch (8 distance lanes per vertex, plain rounds), k x n "
-                              "uint32 device output, best of 3; near_far_batch_ms: the same "
+                              "uint32 device output, best of 3 of the graph-driven loop (rounds "
+                              "in one CUDA graph while loop); host_loop_ms: one call of the "
+                              "host-driven loop; near_far_batch_ms: the same "
                               "batch with one near-far threshold for all lanes (delta of the "
                               "step); singles are sssp() calls on the same sources"}
 
