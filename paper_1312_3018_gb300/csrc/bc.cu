@@ -17,7 +17,14 @@
 // delta(v) = sigma(v) * sum, c(v), and adds delta(v) to its score. Writing the dependency
 // as sigma(v) times a sum of per-vertex quotients needs one division per vertex instead of
 // one per edge (this GPU's FP64 rate is low).
+//
+// Level queues: a vertex enters its partition's level-ordered queue (by degree bucket; hub
+// vertices as their chunks) when it is discovered, and the tails recorded after each
+// forward level delimit the levels, so every compute kernel of either cycle walks exactly
+// the vertices of its level instead of testing the level of every vertex.
 #include <string.h>
+
+#include <vector>
 
 #include "common.cuh"
 
@@ -28,19 +35,22 @@ struct BcCounters {
   unsigned long long reached_degree;
   unsigned long long inspected;
   unsigned long long messages;
+  uint32_t tail[2][kNBucket];  // level-queue tails (hub chunks, buckets 1..3), per source
 };
+constexpr size_t kBcLevelCounters = 4 * sizeof(unsigned long long);  // cleared per level
 
 struct BcWs {
   DevBuf dist[2], sigma[2], cq[2], score[2], hacc[2];
   DevBuf odist[2], gdist[2], gval[2];
+  DevBuf lq[2], lh[2];  // level-ordered vertex queue (by bucket) and hub chunk queue
 };
 
 void free_bc(graph* g) {
   if (!g->bc) return;
   BcWs* w = g->bc;
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->dist[p], &w->sigma[p], &w->cq[p], &w->score[p], &w->hacc[p],
-                     &w->odist[p], &w->gdist[p], &w->gval[p]};
+    DevBuf* all[] = {&w->dist[p],  &w->sigma[p], &w->cq[p],   &w->score[p], &w->hacc[p],
+                     &w->odist[p], &w->gdist[p], &w->gval[p], &w->lq[p],    &w->lh[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
   delete w;
@@ -59,6 +69,9 @@ struct BcSide {
   uint32_t* odist;  // level given to each outbox target by this partition (INF: none)
   uint32_t* gdist;  // published level of each outbox target
   double* gval;     // published sigma (forward) or c (backward) of each outbox target
+  uint32_t* lq;     // [nv] level-ordered queue: bucket b at lq + bstart[b]
+  uint32_t* lh;     // [nchunk] level-ordered hub chunks
+  uint32_t* tail;   // [kNBucket] this partition's queue tails
 };
 
 struct BcArgs {
@@ -90,22 +103,32 @@ __device__ __forceinline__ double group_sum_d(double v, int gshift) {
   return v;
 }
 
-// Forward push from the vertices at level L over edges first, first + stride, ...
+// Forward push from a vertex at level L over edges first, first + stride, ... < deg
+// (warp-uniform trip count: every lane takes part in the queue appends). A discovered
+// local neighbour gets level L + 1 and enters the level queue; a boundary neighbour is
+// marked in its outbox slot.
 __device__ __forceinline__ void discover_edges(const BcSide& S, uint32_t L, const uint32_t* Ep,
                                                int first, int deg, int stride, Cnt& c) {
   const uint64_t pol = l2_evict_first_policy();
-  for (int i = first; i < deg; i += stride) {
-    c.insp++;
-    const uint32_t x = ld_stream(Ep + i, pol);
-    if (!(x & kRemote)) {
-      if (S.dist[x] == kInf && atomicCAS(&S.dist[x], kInf, L + 1) == kInf) {
-        c.disc++;
-        c.deg += (unsigned long long)(S.P.off[x + 1] - S.P.off[x]);
+  for (int i = first; __any_sync(kFull, i < deg); i += stride) {
+    bool dis = false;
+    uint32_t x = 0;
+    if (i < deg) {
+      c.insp++;
+      x = ld_stream(Ep + i, pol);
+      if (!(x & kRemote)) {
+        if (S.dist[x] == kInf && atomicCAS(&S.dist[x], kInf, L + 1) == kInf) {
+          dis = true;
+          c.disc++;
+          c.deg += (unsigned long long)(S.P.off[x + 1] - S.P.off[x]);
+        }
+      } else {
+        const uint32_t idx = x & kIdMask;
+        if (S.odist[idx] == kInf) atomicCAS(&S.odist[idx], kInf, L + 1);
       }
-    } else {
-      const uint32_t idx = x & kIdMask;
-      if (S.odist[idx] == kInf) atomicCAS(&S.odist[idx], kInf, L + 1);
     }
+    if (__any_sync(kFull, dis))
+      warp_append_bucketed(dis, x, dis ? bucket_of(S.P, x) : 0, S.tail, S.lq, S.P, S.lh);
   }
 }
 
@@ -117,19 +140,20 @@ k_bc_discover(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs 
     const BcSide& S = A.side[G.part];
     const uint32_t rel = vb - G.blk0;
     if (G.gshift >= 8) {
-      const uint32_t ch = G.v0 + rel;
+      const uint32_t ch = G.items[rel];
       const uint32_t v = S.P.chunk_vertex[ch];
-      if (S.dist[v] != A.L) continue;  // CTA-uniform
       const int64_t e0 = S.P.chunk_first[ch];
       const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
       discover_edges(S, A.L, S.P.E + e0, threadIdx.x, (int)(e1 - e0), kThreads, c);
     } else {
       const int gs = G.gshift;
       const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
-      if (gi >= G.count) continue;
-      const uint32_t v = G.v0 + gi;
-      if (S.dist[v] != A.L) continue;
-      const int64_t s = S.P.off[v], t = S.P.off[v + 1];
+      int64_t s = 0, t = 0;
+      if (gi < G.count) {
+        const uint32_t v = G.items[gi];
+        s = S.P.off[v];
+        t = S.P.off[v + 1];
+      }
       discover_edges(S, A.L, S.P.E + s, threadIdx.x & ((1 << gs) - 1), (int)(t - s), 1 << gs, c);
     }
   }
@@ -137,21 +161,31 @@ k_bc_discover(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs 
 }
 
 // Outbox slots marked with level L + 1 this superstep give their owner that level.
+// One partition at a time, a warp over 32 consecutive slots, so that the owner's queue
+// appends are warp-wide.
 __global__ void __launch_bounds__(kThreads) k_bc_exchange(const __grid_constant__ BcArgs A) {
   Cnt c;
-  const uint64_t n0 = A.side[0].P.nout, total = n0 + A.side[1].P.nout;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const int p = i < n0 ? 0 : 1;
-    const uint32_t idx = (uint32_t)(p == 0 ? i : i - n0);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (int p = 0; p < 2; ++p) {
     const BcSide& S = A.side[p];
-    if (S.odist[idx] != A.L + 1) continue;
-    c.msg++;
     const BcSide& Q = A.side[1 - p];
-    const uint32_t u = S.P.outbox[idx];
-    if (Q.dist[u] == kInf && atomicCAS(&Q.dist[u], kInf, A.L + 1) == kInf) {
-      c.disc++;
-      c.deg += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
+    const uint64_t total = S.P.nout;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
+         base += stride) {
+      const uint64_t i = base + lane_id();
+      bool dis = false;
+      uint32_t u = 0;
+      if (i < total && S.odist[i] == A.L + 1) {
+        c.msg++;
+        u = S.P.outbox[i];
+        if (Q.dist[u] == kInf && atomicCAS(&Q.dist[u], kInf, A.L + 1) == kInf) {
+          dis = true;
+          c.disc++;
+          c.deg += (unsigned long long)(Q.P.off[u + 1] - Q.P.off[u]);
+        }
+      }
+      if (__any_sync(kFull, dis))
+        warp_append_bucketed(dis, u, dis ? bucket_of(Q.P, u) : 0, Q.tail, Q.lq, Q.P, Q.lh);
     }
   }
   flush(c, A.ctr);
@@ -195,9 +229,9 @@ __device__ __forceinline__ void finish_vertex(const BcSide& S, uint32_t v, doubl
   }
 }
 
-// Pull over the vertices at level `at` (forward: the new level, summing sigma of level
-// at - 1; backward: level at, summing c of level at + 1). Hub vertices are summed chunk by
-// chunk into hacc and finished by k_bc_hubs.
+// Pull over the vertices at level `at`, taken from the level queue (forward: the new level,
+// summing sigma of level at - 1; backward: level at, summing c of level at + 1). Hub
+// vertices are summed chunk by chunk into hacc and finished by k_bc_hubs.
 __global__ void __launch_bounds__(kThreads)
 k_bc_pull(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A, uint32_t at,
           int backward) {
@@ -209,9 +243,8 @@ k_bc_pull(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A, u
     const BcSide& S = A.side[G.part];
     const uint32_t rel = vb - G.blk0;
     if (G.gshift >= 8) {
-      const uint32_t ch = G.v0 + rel;
+      const uint32_t ch = G.items[rel];
       const uint32_t v = S.P.chunk_vertex[ch];
-      if (S.dist[v] != at) continue;  // CTA-uniform
       const int64_t e0 = S.P.chunk_first[ch];
       const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
       double s = 0;
@@ -237,12 +270,10 @@ k_bc_pull(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A, u
     uint32_t v = 0;
     int64_t s0 = 0, t0 = 0;
     if (gi < G.count) {
-      v = G.v0 + gi;
-      if (S.dist[v] == at) {
-        act = true;
-        s0 = S.P.off[v];
-        t0 = S.P.off[v + 1];
-      }
+      v = G.items[gi];
+      act = true;
+      s0 = S.P.off[v];
+      t0 = S.P.off[v + 1];
     }
     double s = 0;
     for (int64_t e = s0 + gl; e < t0; e += (1 << gs)) {
@@ -277,6 +308,9 @@ __global__ void k_bc_source(const __grid_constant__ BcArgs A, const uint32_t* g2
   S.sigma[lid] = 1.0;
   A.ctr->discovered = 1;
   A.ctr->reached_degree = (unsigned long long)(S.P.off[lid + 1] - S.P.off[lid]);
+  const int b = bucket_of(S.P, lid);
+  if (b == 0) append_hub_chunks(S.P, lid, &S.tail[0], S.lh);
+  else if (b < kNBucket) S.lq[S.P.bstart[b] + S.tail[b]++] = lid;
 }
 
 __global__ void k_bc_collect(const __grid_constant__ BcArgs A, uint32_t nv0, uint32_t n,
@@ -303,6 +337,8 @@ graph_status alloc_ws(graph* g) {
     GG_TRY(dalloc(g, w->odist[p], 4ull * P.nout));
     GG_TRY(dalloc(g, w->gdist[p], 4ull * P.nout));
     GG_TRY(dalloc(g, w->gval[p], 8ull * P.nout));
+    GG_TRY(dalloc(g, w->lq[p], 4ull * P.nv));
+    GG_TRY(dalloc(g, w->lh[p], 4ull * P.nchunk));
   }
   if (g->counters.bytes < sizeof(BcCounters) || !g->counters.p) {
     dfree(g, g->counters);
@@ -333,21 +369,32 @@ BcArgs make_args(graph* g, uint32_t L) {
     S.odist = (uint32_t*)w->odist[p].p;
     S.gdist = (uint32_t*)w->gdist[p].p;
     S.gval = (double*)w->gval[p].p;
+    S.lq = (uint32_t*)w->lq[p].p;
+    S.lh = (uint32_t*)w->lh[p].p;
+    S.tail = ((BcCounters*)g->counters.p)->tail[p];
   }
   A.ctr = (BcCounters*)g->counters.p;
   A.L = L;
   return A;
 }
 
-Plan dense_plan(graph* g) {
+// Queue tails at a level boundary: [p][0] hub chunks, [p][1..3] vertices of bucket b.
+struct LevelMark {
+  uint32_t t[2][kNBucket];
+};
+
+// The vertices of one level: the queue entries between two level boundaries.
+Plan level_plan(graph* g, const LevelMark& a, const LevelMark& b) {
+  BcWs* w = g->bc;
   Plan pl;
   memset(&pl, 0, sizeof(pl));
   const int gsh[kNBucket] = {8, 5, kSubShift, 0};
   for (int p = 0; p < 2; ++p) {
     const PartView V = g->part[p].view();
-    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
-    for (int b = 1; b < kNBucket; ++b)
-      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+    plan_add(pl, (const uint32_t*)w->lh[p].p + a.t[p][0], 0, b.t[p][0] - a.t[p][0], p, 8, 0);
+    for (int k = 1; k < kNBucket; ++k)
+      plan_add(pl, (const uint32_t*)w->lq[p].p + V.bstart[k] + a.t[p][k], 0,
+               b.t[p][k] - a.t[p][k], p, gsh[k], k);
   }
   return pl;
 }
@@ -385,7 +432,6 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
   PhaseTimer timer;
   timer.start(at.timing != 0 && stats != nullptr, st);
   timer.mark(2);
-  const Plan pl = dense_plan(g);
   const uint64_t nout = (uint64_t)g->part[0].nout + g->part[1].nout;
   const unsigned sweep = 152 * 8;
   const unsigned hub_grid = 152;
@@ -396,6 +442,13 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
     GG_CUDA(cudaMemsetAsync(w->hacc[p].p, 0, 8ull * g->part[p].nhub, st));
   }
   int64_t launches = 0, traversed = 0, inspected = 0, messages = 0, steps = 0;
+  // marks[L] .. marks[L + 1]: the queue entries of the vertices at level L
+  std::vector<LevelMark> marks;
+  auto mark_now = [&]() {
+    LevelMark m;
+    memcpy(m.t, hc->tail, sizeof(m.t));
+    marks.push_back(m);
+  };
   for (uint32_t si = 0; si < k; ++si) {
     for (int p = 0; p < 2; ++p) {
       const Part& P = g->part[p];
@@ -410,7 +463,13 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
     GG_CUDA(cudaStreamSynchronize(st));
     int64_t reached = (int64_t)hc->reached_degree;
     launches++;
-    // Forward cycle.
+    marks.clear();
+    marks.push_back(LevelMark{});
+    mark_now();
+    GG_CUDA(cudaMemsetAsync(dc, 0, kBcLevelCounters, st));
+    // Forward cycle: level L's queue entries discover level L + 1 (push, then the outbox
+    // marks to their owners); the host reads the tails that now delimit level L + 1, the
+    // ghosts are published and level L + 1 sums its path counts.
     uint32_t L = 0;
     for (;; ++L) {
       if (L >= g->n) {
@@ -419,24 +478,15 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
         return GRAPH_ETIMEOUT;
       }
       const BcArgs A = make_args(g, L);
-      GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(BcCounters), st));
       timer.mark(2);
-      if (pl.nblocks) k_bc_discover<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A);
+      const Plan pd = level_plan(g, marks[L], marks[L + 1]);
+      if (pd.nblocks) k_bc_discover<<<plan_grid(pd.nblocks), kThreads, 0, st>>>(pd, A);
       GG_CUDA(cudaGetLastError());
       timer.mark(0);
-      if (nout) {
-        k_bc_exchange<<<sweep, kThreads, 0, st>>>(A);
-        k_bc_publish<<<sweep, 256, 0, st>>>(A, 0);
-      }
+      if (nout) k_bc_exchange<<<sweep, kThreads, 0, st>>>(A);
       GG_CUDA(cudaGetLastError());
       timer.mark(1);
-      if (pl.nblocks) {
-        k_bc_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A, L + 1, 0);
-        k_bc_hubs<<<hub_grid, 256, 0, st>>>(A, L + 1, 0);
-      }
-      GG_CUDA(cudaGetLastError());
-      timer.mark(0);
-      launches += (pl.nblocks ? 3 : 0) + (nout ? 2 : 0);
+      launches += (pd.nblocks ? 1 : 0) + (nout ? 1 : 0);
       GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
       GG_CUDA(cudaStreamSynchronize(st));
       inspected += (int64_t)hc->inspected;
@@ -444,28 +494,43 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
       reached += (int64_t)hc->reached_degree;
       steps++;
       if (hc->discovered == 0) break;
+      mark_now();
+      GG_CUDA(cudaMemsetAsync(dc, 0, kBcLevelCounters, st));
+      if (nout) k_bc_publish<<<sweep, 256, 0, st>>>(A, 0);
+      GG_CUDA(cudaGetLastError());
+      timer.mark(1);
+      const Plan pp = level_plan(g, marks[L + 1], marks[L + 2]);
+      if (pp.nblocks) {
+        k_bc_pull<<<plan_grid(pp.nblocks), kThreads, 0, st>>>(pp, A, L + 1, 0);
+        k_bc_hubs<<<hub_grid, 256, 0, st>>>(A, L + 1, 0);
+      }
+      GG_CUDA(cudaGetLastError());
+      timer.mark(0);
+      launches += (nout ? 1 : 0) + (pp.nblocks ? 2 : 0);
     }
     // L is now the deepest level (the ghost levels published last are final). Backward
-    // cycle: levels L .. 1; the deepest level has no successors.
+    // cycle: levels L .. 1 from their queue entries, with no host round trip; the deepest
+    // level has no successors.
+    GG_CUDA(cudaMemsetAsync(dc, 0, kBcLevelCounters, st));
     for (uint32_t lv = L; lv >= 1; --lv) {
       const BcArgs A = make_args(g, lv);
-      GG_CUDA(cudaMemsetAsync(dc, 0, sizeof(BcCounters), st));
       timer.mark(2);
       if (nout && lv < L) k_bc_publish<<<sweep, 256, 0, st>>>(A, 1);
       GG_CUDA(cudaGetLastError());
       timer.mark(1);
-      if (pl.nblocks) {
-        k_bc_pull<<<plan_grid(pl.nblocks), kThreads, 0, st>>>(pl, A, lv, 1);
+      const Plan pb = level_plan(g, marks[lv], marks[lv + 1]);
+      if (pb.nblocks) {
+        k_bc_pull<<<plan_grid(pb.nblocks), kThreads, 0, st>>>(pb, A, lv, 1);
         k_bc_hubs<<<hub_grid, 256, 0, st>>>(A, lv, 1);
       }
       GG_CUDA(cudaGetLastError());
       timer.mark(0);
-      launches += (pl.nblocks ? 2 : 0) + (nout && lv < L ? 1 : 0);
-      GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
-      GG_CUDA(cudaStreamSynchronize(st));
-      inspected += (int64_t)hc->inspected;
+      launches += (pb.nblocks ? 2 : 0) + (nout && lv < L ? 1 : 0);
       steps++;
     }
+    GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    inspected += (int64_t)hc->inspected;
     traversed += 2 * reached;
   }
   double* out = scores;
