@@ -65,6 +65,23 @@ def test_bc_long_path_exact(gpu):
     H.free()
 
 
+def test_bc_path_seventy_thousand_levels(gpu):
+    """A 70,000-vertex path from one end: levels up to 69,999 (beyond any 16-bit level
+    encoding), 70,000 forward and 69,999 backward supersteps over the level queues. Closed
+    form: from source 0, vertex v >= 1 lies on the paths to the n - 1 - v vertices beyond
+    it."""
+    n = 70000
+    g = synth.path(n)
+    H = gpu.graph_load_csr(g.offsets, g.cols)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(g.n, 0.5, 6))
+    sc, st = gpu.betweenness(H, [0], out="host")
+    want = (n - 1 - np.arange(n)).astype(np.float64)
+    want[0] = 0.0
+    assert np.array_equal(sc, want)
+    assert st["edges_traversed"] == 2 * (2 * (n - 1))
+    H.free()
+
+
 def test_bc_edge_cases(gpu):
     g = synth.from_edges(9, [(0, 1), (1, 2), (4, 5), (5, 6), (6, 7)])
     H = gpu.graph_load_csr(g.offsets, g.cols)
