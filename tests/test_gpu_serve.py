@@ -198,3 +198,41 @@ def test_server_rejects_bad_requests(gpu):
         ref = oracle.bfs(g.n, g.offsets, g.cols, 3, want_parents=False)[0]
         assert np.array_equal(buf.cpu().numpy().view(np.uint32), ref)
     H.free()
+
+
+def test_server_rmat23_serving_workload_sampled_parity(gpu):
+    """The serving workload the benchmark measures: RMAT scale 23 (8.4M vertices, ~260M
+    edge entries, weights 1..64), degree threshold 2048, near-far SSSP width 16, batched
+    SSSP jobs on, 300 queries (70% BFS, 30% SSSP) submitted as one burst so that BFS lanes
+    and SSSP slots and batches all fill. Every query must complete without error; a sample
+    of the completed queries (four BFS, three SSSP, different sources) is compared with the
+    oracle element by element."""
+    import torch
+    g = rmat_graph(23)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=2048)
+    srcs = synth.sources(g, 4096, seed=5)
+    rng = np.random.default_rng(11)
+    kinds = np.where(rng.random(300) < 0.7, "bfs", "sssp")
+    picks = srcs[rng.integers(len(srcs), size=300)]
+    with gpu.Server(H, out="device", sssp_delta=16, sssp_batch=True) as srv:
+        for k, s in zip(kinds, picks):
+            srv.submit(str(k), int(s), torch.empty(g.n, dtype=torch.int32, device="cuda"))
+        done = drain(gpu, srv, len(kinds), timeout_s=300.0)
+        info = srv.info()
+    assert all(c["status"] == 0 for c in done)
+    assert info["max_lanes_busy"] > 1 and info["sssp_batched"] > 0
+    sample, seen = [], set()
+    for kind, want in (("bfs", 4), ("sssp", 3)):
+        for c in done:
+            if c["kind"] == kind and c["source"] not in seen and want > 0:
+                sample.append(c)
+                seen.add(c["source"])
+                want -= 1
+    assert len(sample) == 7
+    cache = {}
+    for c in sample:
+        got = as_u32(gpu, c["out"].cpu().numpy())
+        ref = expected(g, c["kind"], c["source"], cache)
+        assert np.array_equal(got, ref), f"{c['kind']} from {c['source']} differs"
+    H.free()
