@@ -22,6 +22,14 @@
 // vertices as their chunks) when it is discovered, and the tails recorded after each
 // forward level delimit the levels, so every compute kernel of either cycle walks exactly
 // the vertices of its level instead of testing the level of every vertex.
+//
+// Direction of a forward level (after Beamer et al.'s rule for BFS): when the frontier's
+// edges outnumber half of the edges of the vertices not yet discovered, the level is
+// pulled instead: every undiscovered vertex sums the path counts of its neighbours at the
+// frontier level (boundary neighbours through the ghost copies) and is discovered when the
+// sum is non-zero, which forms discovery and path counts in one pass over the undiscovered
+// vertices' edges instead of a push over the frontier's edges and a pull over the new
+// vertices' edges.
 #include <string.h>
 
 #include <vector>
@@ -38,6 +46,9 @@ struct BcCounters {
   uint32_t tail[2][kNBucket];  // level-queue tails (hub chunks, buckets 1..3), per source
 };
 constexpr size_t kBcLevelCounters = 4 * sizeof(unsigned long long);  // cleared per level
+// A forward level is pulled when its frontier's edges times this factor exceed the edges
+// of the vertices not yet discovered.
+constexpr double kBcPullAlpha = 2.0;
 
 struct BcWs {
   DevBuf dist[2], sigma[2], cq[2], score[2], hacc[2];
@@ -299,6 +310,98 @@ __global__ void k_bc_hubs(const __grid_constant__ BcArgs A, uint32_t at, int bac
   }
 }
 
+// Pulled forward level L: every vertex with dist INF (dense plan) sums sigma over its
+// neighbours at level L; a non-zero sum discovers it at level L + 1 with that path count
+// and queues it. Hub chunks add their partial sums into hacc; k_bc_hubs_discover finishes
+// the hubs.
+__global__ void __launch_bounds__(kThreads)
+k_bc_pull_discover(const __grid_constant__ Plan plan, const __grid_constant__ BcArgs A) {
+  Cnt c;
+  const uint32_t L = A.L;
+  __shared__ double red[kThreads / 32];
+  for (uint32_t vb = blockIdx.x; vb < plan.nblocks; vb += gridDim.x) {
+    const Seg& G = plan.seg[find_seg(plan, vb)];
+    const BcSide& S = A.side[G.part];
+    const uint32_t rel = vb - G.blk0;
+    if (G.gshift >= 8) {
+      const uint32_t ch = G.v0 + rel;
+      const uint32_t v = S.P.chunk_vertex[ch];
+      if (S.dist[v] != kInf) continue;  // CTA-uniform
+      const int64_t e0 = S.P.chunk_first[ch];
+      const int64_t e1 = min(e0 + (int64_t)kHubChunk, S.P.off[v + 1]);
+      double s = 0;
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+        c.insp++;
+        s += pull_one(S, S.P.E[e], L, 0);
+      }
+      s = group_sum_d(s, 5);
+      if (lane_id() == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+        if (t != 0.0) atomicAdd(&S.hacc[v], t);
+      }
+      __syncthreads();
+      continue;
+    }
+    const int gs = G.gshift;
+    const uint32_t gi = rel * (kThreads >> gs) + (threadIdx.x >> gs);
+    const int gl = threadIdx.x & ((1 << gs) - 1);
+    bool act = false;
+    uint32_t v = 0;
+    int64_t s0 = 0, t0 = 0;
+    if (gi < G.count) {
+      v = G.v0 + gi;
+      if (S.dist[v] == kInf) {
+        act = true;
+        s0 = S.P.off[v];
+        t0 = S.P.off[v + 1];
+      }
+    }
+    double s = 0;
+    for (int64_t e = s0 + gl; e < t0; e += (1 << gs)) {
+      c.insp++;
+      s += pull_one(S, S.P.E[e], L, 0);
+    }
+    s = group_sum_d(s, gs);
+    const bool dis = act && gl == 0 && s != 0.0;
+    if (dis) {
+      S.dist[v] = L + 1;
+      S.sigma[v] = s;
+      c.disc++;
+      c.deg += (unsigned long long)(t0 - s0);
+    }
+    warp_append_bucketed(dis, v, dis ? (int)G.bucket : 0, S.tail, S.lq, S.P, S.lh);
+  }
+  flush(c, A.ctr);
+}
+
+// Hub vertices after a pulled level: an undiscovered hub whose chunk sums are non-zero is
+// discovered at level L + 1 with their sum as its path count, and its chunks are queued.
+__global__ void k_bc_hubs_discover(const __grid_constant__ BcArgs A) {
+  Cnt c;
+  for (int p = 0; p < 2; ++p) {
+    const BcSide& S = A.side[p];
+    const uint32_t nh = S.P.bstart[1];
+    for (uint32_t base = blockIdx.x * blockDim.x; base < nh; base += gridDim.x * blockDim.x) {
+      const uint32_t v = base + threadIdx.x;
+      if (v < nh && S.dist[v] == kInf) {
+        const double h = S.hacc[v];
+        if (h != 0.0) {
+          S.hacc[v] = 0.0;
+          S.dist[v] = A.L + 1;
+          S.sigma[v] = h;
+          c.disc++;
+          c.deg += (unsigned long long)(S.P.off[v + 1] - S.P.off[v]);
+          append_hub_chunks(S.P, v, &S.tail[0], S.lh);
+        }
+      }
+    }
+  }
+  flush(c, A.ctr);
+}
+
 __global__ void k_bc_source(const __grid_constant__ BcArgs A, const uint32_t* g2l,
                             uint32_t source) {
   const uint32_t gl = g2l[source];
@@ -383,6 +486,20 @@ struct LevelMark {
   uint32_t t[2][kNBucket];
 };
 
+// Every vertex with edges (hub chunks, buckets 1..3): the plan of a pulled level.
+Plan dense_plan(graph* g) {
+  Plan pl;
+  memset(&pl, 0, sizeof(pl));
+  const int gsh[kNBucket] = {8, 5, kSubShift, 0};
+  for (int p = 0; p < 2; ++p) {
+    const PartView V = g->part[p].view();
+    plan_add(pl, nullptr, 0, V.nchunk, p, 8, 0);
+    for (int b = 1; b < kNBucket; ++b)
+      plan_add(pl, nullptr, V.bstart[b], V.bstart[b + 1] - V.bstart[b], p, gsh[b], b);
+  }
+  return pl;
+}
+
 // The vertices of one level: the queue entries between two level boundaries.
 Plan level_plan(graph* g, const LevelMark& a, const LevelMark& b) {
   BcWs* w = g->bc;
@@ -441,7 +558,8 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
     GG_CUDA(cudaMemsetAsync(w->score[p].p, 0, 8ull * g->part[p].nv, st));
     GG_CUDA(cudaMemsetAsync(w->hacc[p].p, 0, 8ull * g->part[p].nhub, st));
   }
-  int64_t launches = 0, traversed = 0, inspected = 0, messages = 0, steps = 0;
+  int64_t launches = 0, traversed = 0, inspected = 0, messages = 0, steps = 0, pulled = 0;
+  const Plan dense = dense_plan(g);
   // marks[L] .. marks[L + 1]: the queue entries of the vertices at level L
   std::vector<LevelMark> marks;
   auto mark_now = [&]() {
@@ -467,10 +585,12 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
     marks.push_back(LevelMark{});
     mark_now();
     GG_CUDA(cudaMemsetAsync(dc, 0, kBcLevelCounters, st));
-    // Forward cycle: level L's queue entries discover level L + 1 (push, then the outbox
-    // marks to their owners); the host reads the tails that now delimit level L + 1, the
-    // ghosts are published and level L + 1 sums its path counts.
+    // Forward cycle. Pushed level: level L's queue entries discover level L + 1 (push, then
+    // the outbox marks to their owners); the host reads the tails that now delimit level
+    // L + 1, the ghosts are published and level L + 1 sums its path counts. Pulled level:
+    // the ghosts are published, the undiscovered vertices pull, the host reads the tails.
     uint32_t L = 0;
+    int64_t frontier = reached;  // degree sum of level L
     for (;; ++L) {
       if (L >= g->n) {
         set_error("betweenness reached the level cap");
@@ -479,6 +599,29 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
       }
       const BcArgs A = make_args(g, L);
       timer.mark(2);
+      if ((double)frontier * kBcPullAlpha > (double)(g->m - reached)) {
+        if (nout) k_bc_publish<<<sweep, 256, 0, st>>>(A, 0);
+        GG_CUDA(cudaGetLastError());
+        timer.mark(1);
+        if (dense.nblocks) {
+          k_bc_pull_discover<<<plan_grid(dense.nblocks), kThreads, 0, st>>>(dense, A);
+          k_bc_hubs_discover<<<hub_grid, 256, 0, st>>>(A);
+        }
+        GG_CUDA(cudaGetLastError());
+        timer.mark(0);
+        launches += (nout ? 1 : 0) + (dense.nblocks ? 2 : 0);
+        GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(BcCounters), cudaMemcpyDeviceToHost, st));
+        GG_CUDA(cudaStreamSynchronize(st));
+        inspected += (int64_t)hc->inspected;
+        reached += (int64_t)hc->reached_degree;
+        frontier = (int64_t)hc->reached_degree;
+        steps++;
+        pulled++;
+        if (hc->discovered == 0) break;
+        mark_now();
+        GG_CUDA(cudaMemsetAsync(dc, 0, kBcLevelCounters, st));
+        continue;
+      }
       const Plan pd = level_plan(g, marks[L], marks[L + 1]);
       if (pd.nblocks) k_bc_discover<<<plan_grid(pd.nblocks), kThreads, 0, st>>>(pd, A);
       GG_CUDA(cudaGetLastError());
@@ -492,6 +635,7 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
       inspected += (int64_t)hc->inspected;
       messages += (int64_t)hc->messages;
       reached += (int64_t)hc->reached_degree;
+      frontier = (int64_t)hc->reached_degree;
       steps++;
       if (hc->discovered == 0) break;
       mark_now();
@@ -548,6 +692,7 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->supersteps = (int)steps;
+    stats->bottomup_steps = (int)pulled;
     stats->edges_traversed = traversed;
     stats->edges_inspected = inspected;
     stats->messages = messages;
