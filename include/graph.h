@@ -292,8 +292,12 @@ graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t k, uint32_
  *            graph's textbook betweenness (unordered pairs) is half of the all-source sum.
  * The stored graph must be symmetric (successors are taken from the same adjacency that
  * gives predecessors). Path counts are FP64; they are exact while below 2^53.
+ * A forward level whose frontier's edges, times 2, exceed the edges of the vertices not yet
+ * discovered is pulled: every undiscovered vertex sums the path counts of its neighbours at
+ * the frontier level and is discovered by a non-zero sum (same levels and path counts).
  * stats->edges_traversed: twice the degree sum of the vertices each source reaches
- * (Section 5: forward and backward phases), summed over the sources.
+ * (Section 5: forward and backward phases), summed over the sources; stats->bottomup_steps:
+ * the pulled forward levels.
  * Errors: EINVAL, ESTATE, ETIMEOUT, ENOMEM, ECUDA.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
