@@ -350,16 +350,17 @@ __global__ void k_bfs_init(const __grid_constant__ BfsArgs A, const uint32_t* g2
   }
 }
 
-__global__ void k_bfs_collect(const __grid_constant__ BfsArgs A, uint32_t nv0, uint32_t n,
+// Results in global order: thread i reads vertex i's local entry through g2l, so the writes
+// (possibly over the host link) are coalesced.
+__global__ void k_bfs_collect(const __grid_constant__ BfsArgs A, uint32_t n, const uint32_t* g2l,
                               uint32_t* levels, uint32_t* parents) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int p = i < nv0 ? 0 : 1;
-  const uint32_t lid = p == 0 ? i : i - nv0;
-  const BfsSide& S = A.side[p];
-  const uint32_t gid = S.P.l2g[lid];
-  levels[gid] = S.level[lid];
-  if (parents) parents[gid] = S.parent[lid];
+  const uint32_t gl = g2l[i];
+  const BfsSide& S = A.side[gl >> 31];
+  const uint32_t lid = gl & kIdMask;
+  levels[i] = S.level[lid];
+  if (parents) parents[i] = S.parent[lid];
 }
 
 // bfs_hybrid, device to host: partition 1's outbox claims of this level as (owner's local
@@ -608,23 +609,19 @@ extern "C" graph_status bfs(graph_t* g, uint32_t source, uint32_t* levels, uint3
   }
   // Collect (local -> global order).
   graph_status s = GRAPH_OK;
-  uint32_t* dl = levels;
-  uint32_t* dp = parents;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    dl = (uint32_t*)g->stage.p;
-    dp = parents ? dl + g->n : nullptr;
-  }
+  void *dl = nullptr, *dp = nullptr;
+  bool sl = false, sp = false;
+  GG_TRY(out_target(g, levels, at.out_mem, 8ull * g->n, 0, &dl, &sl));
+  if (parents) GG_TRY(out_target(g, parents, at.out_mem, 8ull * g->n, 4ull * g->n, &dp, &sp));
   {
     BfsArgs A = make_args(g, cur, 0);
-    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, dl, dp);
+    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->n, (const uint32_t*)g->g2l.p,
+                                                       (uint32_t*)dl, (uint32_t*)dp);
     launches++;
     GG_CUDA(cudaGetLastError());
   }
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
-    if (parents) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
-  }
+  if (sl) GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
+  if (sp) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));
   s = check_device_error(g);
@@ -904,23 +901,19 @@ extern "C" graph_status bfs_hybrid(graph_t* g, uint32_t source, uint32_t* levels
     GG_CUDA(cudaMemcpyAsync(w->level[0].p, h->level.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
     GG_CUDA(cudaMemcpyAsync(w->parent[0].p, h->parent.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
   }
-  uint32_t* dl = levels;
-  uint32_t* dp = parents;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    dl = (uint32_t*)g->stage.p;
-    dp = parents ? dl + g->n : nullptr;
-  }
+  void *dl = nullptr, *dp = nullptr;
+  bool sl = false, sp = false;
+  GG_TRY(out_target(g, levels, at.out_mem, 8ull * g->n, 0, &dl, &sl));
+  if (parents) GG_TRY(out_target(g, parents, at.out_mem, 8ull * g->n, 4ull * g->n, &dp, &sp));
   {
     BfsArgs A = make_args(g, cur, 0);
-    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, dl, dp);
+    k_bfs_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->n, (const uint32_t*)g->g2l.p,
+                                                       (uint32_t*)dl, (uint32_t*)dp);
     launches++;
     GG_CUDA(cudaGetLastError());
   }
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
-    if (parents) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
-  }
+  if (sl) GG_TRY(deliver(g, levels, dl, 4ull * g->n, GRAPH_MEM_HOST));
+  if (sp) GG_TRY(deliver(g, parents, dp, 4ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaStreamSynchronize(st));
   const graph_status s = check_device_error(g);
   if (stats) {

@@ -363,6 +363,13 @@ graph_status exclusive_scan_i64(graph* g, const int64_t* in, int64_t* out, uint6
 
 // Copies an n-element result from the staging/device buffer to the caller's array.
 graph_status deliver(graph* g, void* dst, const void* dev_src, size_t bytes, int out_mem);
+// Where a collect kernel writes a result bound for dst: dst itself for device outputs; for
+// host outputs, the device address of dst when it is page-locked host memory mapped into the
+// device's address space (the kernel's stores then cross the host link directly, at the
+// link's rate, with no staging copy), else the staging buffer at byte offset stage_off of a
+// staging area of stage_bytes (*staged = true: the caller copies it out with deliver()).
+graph_status out_target(graph* g, void* dst, int out_mem, size_t stage_bytes, size_t stage_off,
+                        void** target, bool* staged);
 
 void free_bfs(graph* g);
 void free_sssp(graph* g);

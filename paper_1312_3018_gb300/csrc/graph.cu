@@ -105,6 +105,25 @@ graph_status deliver(graph* g, void* dst, const void* dev_src, size_t bytes, int
   return GRAPH_OK;
 }
 
+graph_status out_target(graph* g, void* dst, int out_mem, size_t stage_bytes, size_t stage_off,
+                        void** target, bool* staged) {
+  *staged = false;
+  *target = dst;
+  if (out_mem == GRAPH_MEM_DEVICE) return GRAPH_OK;
+  cudaPointerAttributes a;
+  memset(&a, 0, sizeof(a));
+  if (cudaPointerGetAttributes(&a, dst) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+      a.devicePointer) {
+    *target = a.devicePointer;
+    return GRAPH_OK;
+  }
+  cudaGetLastError();  // an unregistered pointer is not an error here
+  GG_TRY(ensure_stage(g, stage_bytes));
+  *target = (char*)g->stage.p + stage_off;
+  *staged = true;
+  return GRAPH_OK;
+}
+
 unsigned plan_grid(uint32_t plan_blocks) {
   static int sms = 0;
   if (!sms) {

@@ -619,15 +619,15 @@ __global__ void k_pr_init(const __grid_constant__ PrArgs A, uint32_t nv0, uint32
   }
 }
 
+// Ranks in global order: thread i reads vertex i's local rank through g2l, so the writes
+// (possibly over the host link) are coalesced.
 template <class RT>
-__global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t nv0, uint32_t n,
+__global__ void k_pr_collect(const __grid_constant__ PrArgs A, uint32_t n, const uint32_t* g2l,
                              double* out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int p = i < nv0 ? 0 : 1;
-  const uint32_t v = p == 0 ? i : i - nv0;
-  const PrSide& S = A.side[p];
-  out[S.P.l2g[v]] = (double)((const RT*)S.r)[v];
+  const uint32_t gl = g2l[i];
+  out[i] = (double)((const RT*)A.side[gl >> 31].r)[gl & kIdMask];
 }
 
 // Threads per vertex (log2) of a class-c tile: kLeafEdges >> (c-1) vertices share the
@@ -863,18 +863,17 @@ graph_status run(graph* g, const pagerank_attr& at, double* ranks, graph_stats* 
       if (last_res < at.tol) break;
     }
   }
-  double* out = ranks;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    out = (double*)g->stage.p;
-  }
+  void* out = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, ranks, at.out_mem, 8ull * g->n, 0, &out, &staged));
   {
     PrArgs A = make_args(g, cur, at.damping);
-    k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, out);
+    k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(
+        A, g->n, (const uint32_t*)g->g2l.p, (double*)out);
     GG_CUDA(cudaGetLastError());
     launches++;
   }
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
+  if (staged) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(&last_res, (double*)w->scal.p + 2, 8, cudaMemcpyDeviceToHost, st));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));
@@ -1095,15 +1094,13 @@ graph_status run_multi(graph* g, uint32_t G, const uint32_t* vbase, const pagera
   }
   GG_CUDA(cudaGraphLaunch(m->exec, st));
   timer.mark(0);
-  double* out = ranks;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    out = (double*)g->stage.p;
-  }
-  k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, K & 1, d),
-                                                                     nv0, g->n, out);
+  void* out = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, ranks, at.out_mem, 8ull * g->n, 0, &out, &staged));
+  k_pr_collect<typename PR::RT><<<grid_for(g->n, 256), 256, 0, st>>>(
+      make_args(g, K & 1, d), g->n, (const uint32_t*)g->g2l.p, (double*)out);
   GG_CUDA(cudaGetLastError());
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
+  if (staged) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
   std::vector<double> hres(G);
   GG_CUDA(cudaMemcpyAsync(hres.data(), m->res.p, 8ull * G, cudaMemcpyDeviceToHost, st));
   timer.mark(2);
@@ -1451,16 +1448,15 @@ graph_status run_hybrid(graph* g, const pagerank_attr& at, int nt, double* ranks
   // write.
   if (nv0)
     GG_CUDA(cudaMemcpyAsync(w->r[0].p, r0, vs * nv0, cudaMemcpyHostToDevice, st));
-  double* out = ranks;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    out = (double*)g->stage.p;
-  }
+  void* out = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, ranks, at.out_mem, 8ull * g->n, 0, &out, &staged));
   A = make_args(g, cur, at.damping);
-  k_pr_collect<T><<<grid_for(g->n, 256), 256, 0, st>>>(A, nv0, g->n, out);
+  k_pr_collect<T><<<grid_for(g->n, 256), 256, 0, st>>>(A, g->n, (const uint32_t*)g->g2l.p,
+                                                       (double*)out);
   GG_CUDA(cudaGetLastError());
   launches++;
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
+  if (staged) GG_TRY(deliver(g, ranks, out, 8ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaStreamSynchronize(st));
   const graph_status s = check_device_error(g);
   if (stats) {

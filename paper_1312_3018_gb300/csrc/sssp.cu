@@ -325,9 +325,10 @@ __global__ void k_sssp_init(const __grid_constant__ SsspArgs A, const uint32_t* 
   }
 }
 
-__global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t nv0, uint32_t n,
-                               uint32_t* dist, unsigned long long* reached_degree,
-                               uint32_t* clamped) {
+// Degree sum of the reached vertices and the clamped flag, in local order (coalesced reads
+// of distances and offsets).
+__global__ void k_sssp_reached(const __grid_constant__ SsspArgs A, uint32_t nv0, uint32_t n,
+                               unsigned long long* reached_degree, uint32_t* clamped) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long d = 0;
   if (i < n) {
@@ -335,12 +336,21 @@ __global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t nv0,
     const uint32_t lid = p == 0 ? i : i - nv0;
     const SsspSide& S = A.side[p];
     const uint32_t dv = S.dist[lid];
-    dist[S.P.l2g[lid]] = dv;
     if (dv != kInf) d = (unsigned long long)(S.P.off[lid + 1] - S.P.off[lid]);
     if (dv == kInf - 1) atomicOr(clamped, 1u);
   }
   d = warp_sum(d);
   if (lane_id() == 0 && d) atomicAdd(reached_degree, d);
+}
+
+// Distances in global order: thread i reads vertex i's local entry through g2l, so the
+// writes (possibly over the host link) are coalesced.
+__global__ void k_sssp_collect(const __grid_constant__ SsspArgs A, uint32_t n, const uint32_t* g2l,
+                               uint32_t* dist) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t gl = g2l[i];
+  dist[i] = A.side[gl >> 31].dist[gl & kIdMask];
 }
 
 // Connected components start: every vertex labelled with its global id, every vertex
@@ -564,8 +574,9 @@ graph_status launch_collect(graph* g, SsspWs* w, SsspCounters* ctr, int cur, uin
                             cudaStream_t st) {
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
   const SsspArgs A = make_args(g, w, ctr, cur);
-  k_sssp_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, out,
+  k_sssp_reached<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n,
                                                        &ctr->reached_degree, &ctr->clamped);
+  k_sssp_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->n, (const uint32_t*)g->g2l.p, out);
   GG_CUDA(cudaGetLastError());
   return GRAPH_OK;
 }
@@ -788,14 +799,12 @@ extern "C" graph_status sssp(graph_t* g, uint32_t source, uint32_t* dist,
     overflow |= hc->overflow != 0;
     cur = 1 - cur;
   }
-  uint32_t* dd = dist;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 4ull * g->n + 64));
-    dd = (uint32_t*)g->stage.p;
-  }
-  GG_TRY(launch_collect(g, w, dc, cur, dd, st));
-  launches++;
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
+  void* dd = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, dist, at.out_mem, 4ull * g->n + 64, 0, &dd, &staged));
+  GG_TRY(launch_collect(g, w, dc, cur, (uint32_t*)dd, st));
+  launches += 2;
+  if (staged) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));
@@ -879,14 +888,12 @@ extern "C" graph_status connected_components(graph_t* g, uint32_t* labels,
     messages += (int64_t)hc->messages;
     cur = 1 - cur;
   }
-  uint32_t* out = labels;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 4ull * g->n + 64));
-    out = (uint32_t*)g->stage.p;
-  }
-  GG_TRY(launch_collect(g, w, dc, cur, out, st));
-  launches++;
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, labels, out, 4ull * g->n, GRAPH_MEM_HOST));
+  void* out = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, labels, at.out_mem, 4ull * g->n + 64, 0, &out, &staged));
+  GG_TRY(launch_collect(g, w, dc, cur, (uint32_t*)out, st));
+  launches += 2;
+  if (staged) GG_TRY(deliver(g, labels, out, 4ull * g->n, GRAPH_MEM_HOST));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));
   const graph_status s = check_device_error(g);
@@ -1167,14 +1174,12 @@ extern "C" graph_status sssp_hybrid(graph_t* g, uint32_t source, uint32_t* dist,
     GG_CUDA(cudaMemcpyAsync(w->dist[0].p, d0.data(), 4ull * nv0, cudaMemcpyHostToDevice, st));
     GG_CUDA(cudaStreamSynchronize(st));
   }
-  uint32_t* dd = dist;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 4ull * g->n + 64));
-    dd = (uint32_t*)g->stage.p;
-  }
-  GG_TRY(launch_collect(g, w, dc, cur, dd, st));
-  launches++;
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
+  void* dd = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, dist, at.out_mem, 4ull * g->n + 64, 0, &dd, &staged));
+  GG_TRY(launch_collect(g, w, dc, cur, (uint32_t*)dd, st));
+  launches += 2;
+  if (staged) GG_TRY(deliver(g, dist, dd, 4ull * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SsspCounters), cudaMemcpyDeviceToHost, st));
   GG_CUDA(cudaStreamSynchronize(st));
   graph_status s = check_device_error(g);
