@@ -416,14 +416,13 @@ __global__ void k_bc_source(const __grid_constant__ BcArgs A, const uint32_t* g2
   else if (b < kNBucket) S.lq[S.P.bstart[b] + S.tail[b]++] = lid;
 }
 
-__global__ void k_bc_collect(const __grid_constant__ BcArgs A, uint32_t nv0, uint32_t n,
+// Scores in global order (coalesced writes; each thread reads its vertex through g2l).
+__global__ void k_bc_collect(const __grid_constant__ BcArgs A, uint32_t n, const uint32_t* g2l,
                              double* out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int p = i < nv0 ? 0 : 1;
-  const uint32_t lid = p == 0 ? i : i - nv0;
-  const BcSide& S = A.side[p];
-  out[S.P.l2g[lid]] = S.score[lid];
+  const uint32_t gl = g2l[i];
+  out[i] = A.side[gl >> 31].score[gl & kIdMask];
 }
 
 graph_status alloc_ws(graph* g) {
@@ -677,15 +676,14 @@ extern "C" graph_status betweenness(graph_t* g, const uint32_t* sources, uint32_
     inspected += (int64_t)hc->inspected;
     traversed += 2 * reached;
   }
-  double* out = scores;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 8ull * g->n));
-    out = (double*)g->stage.p;
-  }
-  k_bc_collect<<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, 0), g->part[0].nv, g->n, out);
+  void* out = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, scores, at.out_mem, 8ull * g->n, 0, &out, &staged));
+  k_bc_collect<<<grid_for(g->n, 256), 256, 0, st>>>(make_args(g, 0), g->n,
+                                                   (const uint32_t*)g->g2l.p, (double*)out);
   GG_CUDA(cudaGetLastError());
   launches++;
-  if (at.out_mem == GRAPH_MEM_HOST) GG_TRY(deliver(g, scores, out, 8ull * g->n, GRAPH_MEM_HOST));
+  if (staged) GG_TRY(deliver(g, scores, out, 8ull * g->n, GRAPH_MEM_HOST));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));
   const graph_status s = check_device_error(g);

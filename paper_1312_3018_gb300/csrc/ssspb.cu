@@ -495,9 +495,9 @@ struct OutRows {
   uint32_t* p[kSbLanes];
 };
 
-// Lane l's distances into rows.p[l], and each lane's reached degree sum.
-__global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uint32_t n,
-                             uint32_t k, const __grid_constant__ OutRows rows, SbCounters* ctr) {
+// Each lane's reached degree sum and the clamped flag, in local order (coalesced reads).
+__global__ void k_sb_reached(const __grid_constant__ SbArgs A, uint32_t nv0, uint32_t n,
+                             uint32_t k, SbCounters* ctr) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long d[kSbLanes] = {0};
   if (i < n) {
@@ -505,12 +505,10 @@ __global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uin
     const uint32_t v = p == 0 ? i : i - nv0;
     const SbSide& S = A.side[p];
     const Row r = load_row(S.dist + (size_t)v * kSbLanes);
-    const uint32_t gid = S.P.l2g[v];
     const unsigned long long deg = (unsigned long long)(S.P.off[v + 1] - S.P.off[v]);
     #pragma unroll
     for (int l = 0; l < kSbLanes; ++l) {
       if ((uint32_t)l >= k) break;
-      rows.p[l][gid] = r.d[l];
       if (r.d[l] != kInf) d[l] = deg;
       if (r.d[l] == kInf - 1) atomicOr(&ctr->clamped, 1u);
     }
@@ -520,6 +518,21 @@ __global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t nv0, uin
     if ((uint32_t)l >= k) break;
     const unsigned long long s = warp_sum(d[l]);
     if (lane_id() == 0 && s) atomicAdd(&ctr->reached_degree[l], s);
+  }
+}
+
+// Lane l's distances into rows.p[l] in global order: thread i reads vertex i's row through
+// g2l, so the writes of every lane's row (possibly over the host link) are coalesced.
+__global__ void k_sb_collect(const __grid_constant__ SbArgs A, uint32_t n, const uint32_t* g2l,
+                             uint32_t k, const __grid_constant__ OutRows rows) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t gl = g2l[i];
+  const Row r = load_row(A.side[gl >> 31].dist + (size_t)(gl & kIdMask) * kSbLanes);
+  #pragma unroll
+  for (int l = 0; l < kSbLanes; ++l) {
+    if ((uint32_t)l >= k) break;
+    rows.p[l][i] = r.d[l];
   }
 }
 
@@ -677,7 +690,8 @@ graph_status launch_collect(graph* g, SbWs* w, SbCounters* ctr, int cur, const O
                             uint32_t k, cudaStream_t st) {
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SbCounters), st));
   const SbArgs A = make_args(g, w, ctr, cur);
-  k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, rows, ctr);
+  k_sb_reached<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->part[0].nv, g->n, k, ctr);
+  k_sb_collect<<<grid_for(g->n, 256), 256, 0, st>>>(A, g->n, (const uint32_t*)g->g2l.p, k, rows);
   GG_CUDA(cudaGetLastError());
   return GRAPH_OK;
 }
@@ -1022,18 +1036,16 @@ extern "C" graph_status sssp_batch(graph_t* g, const uint32_t* sources, uint32_t
     cur = 1 - cur;
   }
   }
-  uint32_t* dd = dist;
-  if (at.out_mem == GRAPH_MEM_HOST) {
-    GG_TRY(ensure_stage(g, 4ull * k * g->n + 64));
-    dd = (uint32_t*)g->stage.p;
-  }
+  void* ddv = nullptr;
+  bool staged = false;
+  GG_TRY(out_target(g, dist, at.out_mem, 4ull * k * g->n + 64, 0, &ddv, &staged));
+  uint32_t* dd = (uint32_t*)ddv;
   OutRows rows;
   memset(&rows, 0, sizeof(rows));
   for (uint32_t l = 0; l < k; ++l) rows.p[l] = dd + (size_t)l * g->n;
   GG_TRY(launch_collect(g, w, dc, cur, rows, k, st));
-  launches++;
-  if (at.out_mem == GRAPH_MEM_HOST)
-    GG_TRY(deliver(g, dist, dd, 4ull * k * g->n, GRAPH_MEM_HOST));
+  launches += 2;
+  if (staged) GG_TRY(deliver(g, dist, dd, 4ull * k * g->n, GRAPH_MEM_HOST));
   GG_CUDA(cudaMemcpyAsync(hc, dc, sizeof(SbCounters), cudaMemcpyDeviceToHost, st));
   timer.mark(2);
   GG_CUDA(cudaStreamSynchronize(st));

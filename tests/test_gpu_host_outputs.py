@@ -54,3 +54,25 @@ def test_host_outputs_pinned_and_pageable(gpu, T):
         gpu.pagerank(H, ranks=ranks, max_iter=10, precision="fp32", out="host")
         assert np.array_equal(ranks, r_d)
     H.free()
+
+
+def test_host_outputs_batched_sssp_and_betweenness(gpu):
+    import torch
+    g = rmat_graph(13)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "degree", degree_threshold=32)
+    srcs = [int(s) for s in synth.sources(g, 5, seed=6)]
+    d_d, _ = gpu.sssp_batch(H, srcs, out="device")
+    d_d = gpu.as_numpy_u32(d_d)
+    for row, s in enumerate(srcs):
+        assert np.array_equal(d_d[row], oracle.sssp(g.n, g.offsets, g.cols, g.weights, s))
+    for dist in (pinned(torch, len(srcs) * g.n, torch.int32).view(np.uint32).reshape(len(srcs), g.n),
+                 np.zeros((len(srcs), g.n), np.uint32)):
+        gpu.sssp_batch(H, srcs, dist, out="host")
+        assert np.array_equal(dist, d_d)
+    b_d, _ = gpu.betweenness(H, srcs[:3], out="device")
+    b_d = b_d.cpu().numpy()
+    for sc in (pinned(torch, g.n, torch.float64), np.zeros(g.n)):
+        gpu.betweenness(H, srcs[:3], sc, out="host")
+        assert np.allclose(sc, b_d, rtol=1e-12, atol=0)
+    H.free()
