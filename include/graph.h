@@ -132,6 +132,29 @@ graph_status graph_export_partition(const graph_t* g, int p, uint32_t* l2g, int6
                                     uint32_t* E, uint32_t* W, uint32_t* outbox,
                                     uint32_t* g2l);
 
+/* ---------------------------------------------------------------------------------------
+ * graph_set_edge_memory -- where the edge arrays live: device memory (the default) or
+ * page-locked host memory mapped into the device's address space, which the kernels then
+ * read over the host link (Section 4.3.4 (iii), Section 8: immutable, sequentially read
+ * edge arrays of a partition kept in mapped host memory so that graphs larger than the
+ * GPU's memory can be processed; GB300's link to the Grace host carries about 190 GB/s).
+ *   which  bit 0: partition 0's edge ids and weights; bit 1: partition 1's; bit 2: the
+ *          loaded CSR's column and weight arrays (read again only by graph_partition and
+ *          by pagerank_multi's first call). 1 ... 7.
+ *   mem    GRAPH_MEM_HOST or GRAPH_MEM_DEVICE.
+ * Every algorithm works with either placement and gives the same results; offsets, vertex
+ * state and messages stay in device memory. The call copies the arrays (blocking), frees
+ * their old copies and drops the algorithms' workspaces, which the next calls rebuild.
+ * Re-partitioning puts the new partitions' edge arrays in device memory. Errors: EINVAL
+ * (bad which or mem), ESTATE (bits 0-1 before graph_partition), ENOMEM (no page-locked
+ * host memory, or no device memory to move back to), ECUDA.
+ * ------------------------------------------------------------------------------------- */
+graph_status graph_set_edge_memory(graph_t* g, int which, int mem);
+
+/* Current placement: bit 0 / 1 / 2 set when partition 0's / partition 1's / the loaded
+ * CSR's edge arrays are in host memory. Errors: EINVAL. */
+graph_status graph_get_edge_memory(const graph_t* g, int* placement);
+
 /* Per-call statistics (all optional; pass NULL). Times are CUDA-event times on the
  * handle's stream, filled when the attribute `timing` is non-zero. */
 typedef struct {

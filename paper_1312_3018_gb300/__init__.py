@@ -173,6 +173,29 @@ def graph_export_partition(g: Graph, p: int, weights: bool = False) -> dict:
                 cls_end=info["cls_end"][p], g2l=g2l)
 
 
+_EDGE_PARTS = {"part0": 1, "part1": 2, "input": 4}
+
+
+def graph_set_edge_memory(g: Graph, which, mem: str):
+    """Moves edge arrays to page-locked host memory ("host"; kernels read them over the host
+    link) or back to device memory ("device"). which: "part0", "part1", "input" or a list
+    of them."""
+    if isinstance(which, str):
+        which = [which]
+    mask = 0
+    for w in which:
+        mask |= _EDGE_PARTS[w]
+    memv = {"host": GRAPH_MEM_HOST, "device": GRAPH_MEM_DEVICE}[mem]
+    _lib.check(_lib.load().graph_set_edge_memory(g.handle, mask, memv), "graph_set_edge_memory")
+
+
+def graph_get_edge_memory(g: Graph) -> dict:
+    """{"part0": "host"|"device", "part1": ..., "input": ...}"""
+    v = C.c_int(0)
+    _lib.check(_lib.load().graph_get_edge_memory(g.handle, C.byref(v)), "graph_get_edge_memory")
+    return {k: ("host" if v.value & b else "device") for k, b in _EDGE_PARTS.items()}
+
+
 def _out_u32(torch, n, out, given):
     if given is not None:
         return given

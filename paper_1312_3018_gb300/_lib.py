@@ -149,6 +149,8 @@ SIGNATURES = {
     "graph_partition": (_int, [_vp, C.POINTER(graph_partition_attr)]),
     "graph_get_partition_info": (_int, [_vp, C.POINTER(graph_partition_info)]),
     "graph_export_partition": (_int, [_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "graph_set_edge_memory": (_int, [_vp, _int, _int]),
+    "graph_get_edge_memory": (_int, [_vp, C.POINTER(_int)]),
     "bfs": (_int, [_vp, _u32, _vp, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "bfs_batch": (_int, [_vp, _vp, _u32, _vp, C.POINTER(bfs_attr), C.POINTER(graph_stats)]),
     "sssp": (_int, [_vp, _u32, _vp, C.POINTER(sssp_attr), C.POINTER(graph_stats)]),

@@ -664,7 +664,7 @@ graph_status ensure_hbfs(graph* g, BfsWs* w) {
   h->vis.reset(new std::atomic<uint64_t>[(P0.nv + 63) / 64 + 1]);
   h->oseen.reset(new std::atomic<uint64_t>[(P0.nout + 63) / 64 + 1]);
   GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1), cudaMemcpyDeviceToHost, st));
-  if (P0.ne) GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+  if (P0.ne) GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDefault, st));
   if (P0.nv) GG_CUDA(cudaMemcpyAsync(h->l2g0.data(), P0.l2g.p, 4ull * P0.nv, cudaMemcpyDeviceToHost, st));
   if (P0.nout)
     GG_CUDA(cudaMemcpyAsync(h->outbox0.data(), P0.outbox.p, 4ull * P0.nout, cudaMemcpyDeviceToHost, st));

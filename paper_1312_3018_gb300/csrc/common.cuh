@@ -277,8 +277,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Host side
 // ------------------------------------------------------------------------------------
 struct DevBuf {
-  void* p = nullptr;
+  void* p = nullptr;      // device address (for host-resident buffers: the device alias)
   size_t bytes = 0;
+  void* host = nullptr;   // page-locked host allocation behind p, or null (device memory)
 };
 
 struct Part {

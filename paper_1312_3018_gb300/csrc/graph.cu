@@ -59,6 +59,11 @@ graph_status dalloc(graph* g, DevBuf& b, size_t bytes) {
 }
 
 void dfree(graph* g, DevBuf& b) {
+  if (b.host) {
+    cudaFreeHost(b.host);
+    b = DevBuf();
+    return;
+  }
   if (!b.p) return;
   if (g->rt.free) g->rt.free(b.p, b.bytes, g->rt.ctx);
   else if (!g->rt.alloc) cudaFree(b.p);
@@ -928,12 +933,103 @@ graph_status graph_export_partition(const graph_t* g, int p, uint32_t* l2g, int6
   cudaStream_t s = g->stream;
   if (l2g && P.nv) GG_CUDA(cudaMemcpyAsync(l2g, P.l2g.p, 4ull * P.nv, cudaMemcpyDeviceToHost, s));
   if (off) GG_CUDA(cudaMemcpyAsync(off, P.off.p, 8ull * (P.nv + 1), cudaMemcpyDeviceToHost, s));
-  if (E && P.ne) GG_CUDA(cudaMemcpyAsync(E, P.E.p, 4ull * P.ne, cudaMemcpyDeviceToHost, s));
-  if (W && P.ne) GG_CUDA(cudaMemcpyAsync(W, P.W.p, 4ull * P.ne, cudaMemcpyDeviceToHost, s));
+  // (the edge arrays may be host-resident: let the runtime infer the direction)
+  if (E && P.ne) GG_CUDA(cudaMemcpyAsync(E, P.E.p, 4ull * P.ne, cudaMemcpyDefault, s));
+  if (W && P.ne) GG_CUDA(cudaMemcpyAsync(W, P.W.p, 4ull * P.ne, cudaMemcpyDefault, s));
   if (outbox && P.nout)
     GG_CUDA(cudaMemcpyAsync(outbox, P.outbox.p, 4ull * P.nout, cudaMemcpyDeviceToHost, s));
   if (g2l) GG_CUDA(cudaMemcpyAsync(g2l, g->g2l.p, 4ull * g->n, cudaMemcpyDeviceToHost, s));
   GG_CUDA(cudaStreamSynchronize(s));
+  return GRAPH_OK;
+}
+
+namespace gg {
+namespace {
+
+// Moves a buffer into page-locked host memory mapped into the device (p becomes the
+// device alias of the host allocation), or back into device memory.
+graph_status move_to_host(graph* g, DevBuf& b) {
+  if (b.host || !b.p) return GRAPH_OK;
+  void* h = nullptr;
+  if (cudaHostAlloc(&h, b.bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cannot allocate %zu bytes of page-locked host memory", b.bytes);
+    return GRAPH_ENOMEM;
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMemcpyAsync(h, b.p, b.bytes, cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h);
+    return cuda_fail(e, "moving an edge array to host memory", __FILE__, __LINE__);
+  }
+  const size_t bytes = b.bytes;
+  dfree(g, b);
+  b.p = d;
+  b.bytes = bytes;
+  b.host = h;
+  return GRAPH_OK;
+}
+
+graph_status move_to_device(graph* g, DevBuf& b) {
+  if (!b.host) return GRAPH_OK;
+  DevBuf nb;
+  GG_TRY(dalloc(g, nb, b.bytes));
+  cudaError_t e = cudaMemcpyAsync(nb.p, b.host, b.bytes, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    dfree(g, nb);
+    return cuda_fail(e, "moving an edge array to device memory", __FILE__, __LINE__);
+  }
+  cudaFreeHost(b.host);
+  b = nb;
+  return GRAPH_OK;
+}
+
+}  // namespace
+}  // namespace gg
+
+extern "C" graph_status graph_set_edge_memory(graph_t* g, int which, int mem) {
+  if (!g || which <= 0 || which > 7 || (mem != GRAPH_MEM_HOST && mem != GRAPH_MEM_DEVICE)) {
+    set_error("bad graph, edge-array mask or memory kind");
+    return GRAPH_EINVAL;
+  }
+  if ((which & 3) && !g->partitioned) {
+    set_error("graph_partition must run before a partition's edges can move");
+    return GRAPH_ESTATE;
+  }
+  GG_CUDA(cudaStreamSynchronize(g->stream));
+  // Workspaces and captured supersteps hold edge-array addresses: they are rebuilt on
+  // their next use.
+  free_bfs(g);
+  free_sssp(g);
+  free_pr(g);
+  free_msbfs(g);
+  free_bc(g);
+  free_ssspb(g);
+  free_seg(g);
+  DevBuf* bufs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (which & 1) { bufs[0] = &g->part[0].E; bufs[1] = &g->part[0].W; }
+  if (which & 2) { bufs[2] = &g->part[1].E; bufs[3] = &g->part[1].W; }
+  if (which & 4) { bufs[4] = &g->col; bufs[5] = &g->w; }
+  for (DevBuf* b : bufs) {
+    if (!b) continue;
+    GG_TRY(mem == GRAPH_MEM_HOST ? move_to_host(g, *b) : move_to_device(g, *b));
+  }
+  return GRAPH_OK;
+}
+
+extern "C" graph_status graph_get_edge_memory(const graph_t* g, int* placement) {
+  if (!g || !placement) {
+    set_error("graph or placement is NULL");
+    return GRAPH_EINVAL;
+  }
+  int m = 0;
+  if (g->part[0].E.host) m |= 1;
+  if (g->part[1].E.host) m |= 2;
+  if (g->col.host) m |= 4;
+  *placement = m;
   return GRAPH_OK;
 }
 

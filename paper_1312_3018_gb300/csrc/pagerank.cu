@@ -141,6 +141,7 @@ struct PrArgs {
   float damping_f, n_f, d_over_n_f;
   double nzero;       // number of degree-zero vertices
   int* err;
+  int e_host[2];      // partition p's edge ids live in host memory: no bulk copy of them
 };
 
 // Many independent graphs in one launch (pagerank_multi): vertex v of partition p belongs
@@ -370,6 +371,8 @@ __device__ void issue_item(const PrArgs& A, uint32_t k, Desc& d, uint32_t* sE, i
     d.rshift = d.v0 - q0;
     rbytes = (q1 - q0) * (uint32_t)sizeof(RT);
   }
+  // Edge ids in host memory are read by the CTA's threads after the wait instead.
+  if (A.e_host[it.part]) ebytes = 0;
   mbar_expect_tx(bar, ebytes + obytes + rbytes);
   const uint64_t pol = l2_evict_first_policy();
   if (ebytes) bulk_g2s_stream(sE, S.P.E + a0, ebytes, bar, pol);
@@ -434,6 +437,13 @@ k_pr_compute(const __grid_constant__ PrPlan plan, const __grid_constant__ PrArgs
   if (__syncthreads_and(ok)) {
     const Desc d = dsh;
     const PrSide& S = A.side[d.part];
+    if (A.e_host[d.part] && d.kind != kItemZero) {
+      // host-resident edge ids: the same granules, loaded over the host link by the threads
+      const int64_t a0 = d.e0 - (int64_t)d.eshift;
+      const int64_t cnt = ((d.e1 + 3) & ~(int64_t)3) - a0;
+      for (int64_t i = threadIdx.x; i < cnt; i += kThreads) sE[i] = S.P.E[a0 + i];
+      __syncthreads();
+    }
     if (d.kind == kItemHub) {
       // One chunk (at most kHubChunk edges) of a hub's adjacency: each warp's partial sum
       // goes to hubsum[item][warp]; k_pr_hubs adds a hub's partials in order and updates
@@ -766,6 +776,7 @@ PrArgs make_args(graph* g, int cur, double damping) {
   A.d_over_n_f = (float)(damping / (double)g->n);
   A.nzero = (double)zero;
   A.err = (int*)g->err.p;
+  for (int p = 0; p < 2; ++p) A.e_host[p] = g->part[p].E.host != nullptr;
   return A;
 }
 
@@ -1200,7 +1211,7 @@ graph_status ensure_hyb(graph* g, PrWs* w, int nt) {
     GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1),
                             cudaMemcpyDeviceToHost, st));
     if (P0.ne)
-      GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDefault, st));
     if (P1.nout)
       GG_CUDA(cudaMemcpyAsync(h->outbox1.data(), P1.outbox.p, 4ull * P1.nout,
                               cudaMemcpyDeviceToHost, st));

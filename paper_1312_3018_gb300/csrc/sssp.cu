@@ -936,8 +936,8 @@ graph_status ensure_hsssp(graph* g, SsspWs* w) {
   h->odirty.reset(new std::atomic<uint8_t>[P0.nout + 1]);
   GG_CUDA(cudaMemcpyAsync(h->off0.data(), P0.off.p, 8ull * (P0.nv + 1), cudaMemcpyDeviceToHost, st));
   if (P0.ne) {
-    GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
-    GG_CUDA(cudaMemcpyAsync(h->W0.data(), P0.W.p, 4ull * P0.ne, cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaMemcpyAsync(h->E0.data(), P0.E.p, 4ull * P0.ne, cudaMemcpyDefault, st));
+    GG_CUDA(cudaMemcpyAsync(h->W0.data(), P0.W.p, 4ull * P0.ne, cudaMemcpyDefault, st));
   }
   if (P0.nout)
     GG_CUDA(cudaMemcpyAsync(h->outbox0.data(), P0.outbox.p, 4ull * P0.nout, cudaMemcpyDeviceToHost, st));
