@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the hybrid (host + GPU) PageRank measurement")
+    ap.add_argument("--no-host-edges", action="store_true",
+                    help="skip the edge arrays in mapped host memory measurement")
     ap.add_argument("--no-sssp-batch", action="store_true",
                     help="serving: SSSP queries on single-query jobs only")
     ap.add_argument("--serve-max-sssp", type=int, default=0,
@@ -354,6 +356,46 @@ def run_reference(a):
         "budget_s_per_step": per_step_budget,
     }
     print(json.dumps(line), flush=True)
+
+
+def host_edges_report(G, H, torch, source, pr_iters=5):
+    """Edge arrays in mapped host memory (the paper's way to process graphs larger than the
+    GPU's memory): BFS, near-far SSSP and FP32 PageRank iterations with the edge arrays of
+    partition 0, then of both partitions and the input CSR, in page-locked host memory read
+    over the host link, against device-resident edges; the placement is restored after."""
+    def times():
+        out = {}
+        calls = (("bfs_ms", lambda: G.bfs(H, source, want_parents=False)),
+                 ("sssp_ms", lambda: G.sssp(H, source, delta=64)),
+                 ("pagerank_ms_per_iter",
+                  lambda: G.pagerank(H, max_iter=pr_iters, precision="fp32")))
+        for name, fn in calls:
+            fn()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t) * 1e3
+            out[name] = round(ms / (pr_iters if name.startswith("pagerank") else 1), 3)
+        return out
+    rep = {"device": times()}
+    info = G.graph_get_partition_info(H)
+    t = time.perf_counter()
+    G.graph_set_edge_memory(H, "part0", "host")
+    rep["move_part0_s"] = round(time.perf_counter() - t, 3)
+    rep["part0_host"] = times()
+    G.graph_set_edge_memory(H, ["part1", "input"], "host")
+    rep["all_host"] = times()
+    G.graph_set_edge_memory(H, ["part0", "part1", "input"], "device")
+    e0, e = info["ne"][0], info["ne"][0] + info["ne"][1]
+    rate = lambda b, ms: round(4 * b / (max(ms, 1e-6) / 1e3) / 1e9, 1)
+    rep["pagerank_link_gbs"] = {
+        "part0_host": rate(e0, rep["part0_host"]["pagerank_ms_per_iter"]),
+        "all_host": rate(e, rep["all_host"]["pagerank_ms_per_iter"])}
+    rep["note"] = ("wall-clock per call after a warm-up call; pagerank_link_gbs: the "
+                   "host-resident edge ids (4 B per entry) read per iteration over the "
+                   "measured time")
+    return rep
 
 
 def hybrid_report(G, H, m, torch, shares=(0.05, 0.25), iters=5, source=None):
@@ -933,6 +975,7 @@ def main():
         cpu_omp["vs_gpu_value"] = round(value / cpu_omp["value"], 2)
     precision = None if a.no_precision else precision_report(G, H, g, ref,
                                                              iters_step=a.pr_iters)
+    host_edges = None if a.no_host_edges else host_edges_report(G, H, torch, int(srcs[0]))
     # Last, because it re-partitions the graph.
     hybrid = None if a.no_hybrid else hybrid_report(G, H, m, torch, source=srcs[0])
     nproc = os.cpu_count()
@@ -979,6 +1022,7 @@ def main():
         "bc_cc": more,
         "pagerank_precision": precision,
         "hybrid_pagerank": hybrid,
+        "host_edges": host_edges,
         "gpu_launches": launches,
         "clocks": clk,
         "preprocess_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),

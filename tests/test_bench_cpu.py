@@ -160,3 +160,39 @@ def test_hybrid_report_fields():
     assert p["exchange_ms_per_iter"] == 0.5 and p["messages_per_iter"] == 70
     assert abs(p["l1_vs_gpu_only"] - 1e-9) < 1e-15
     assert p["hybrid_ms_per_iter"] >= 0 and p["gpu_only_ms_per_iter"] >= 0
+
+
+def test_host_edges_report_fields_and_restores_placement():
+    """The host-edges object: device, partition-0-on-host and all-on-host timings, the link
+    rate of the PageRank iterations, and the placement moved back to the device."""
+    bench = _bench_module()
+    calls = []
+
+    class FakeTorch:
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+    class FakeLib:
+        def graph_get_partition_info(self, H):
+            return {"ne": [3000, 1000]}
+
+        def graph_set_edge_memory(self, H, which, mem):
+            calls.append((which, mem))
+
+        def bfs(self, H, s, want_parents):
+            return None
+
+        def sssp(self, H, s, delta):
+            return None
+
+        def pagerank(self, H, max_iter, precision):
+            return None
+
+    rep = bench.host_edges_report(FakeLib(), object(), FakeTorch, 5, pr_iters=5)
+    for k in ("device", "part0_host", "all_host"):
+        assert set(rep[k]) == {"bfs_ms", "sssp_ms", "pagerank_ms_per_iter"}
+    assert set(rep["pagerank_link_gbs"]) == {"part0_host", "all_host"}
+    assert calls[0] == ("part0", "host")
+    assert calls[-1] == (["part0", "part1", "input"], "device")
