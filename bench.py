@@ -670,7 +670,8 @@ def main():
     for name, (b, ms, launches_k) in kern.items():
         ach = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
         rl[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                    "frac_vs_nominal_8tbs": round(ach / 8000.0, 4), "traffic": None,
                     "launches": launches_k, "avg_launch_ms": round(ms / max(launches_k, 1), 4),
                     "peak_kind": peak_kind}
     # DRAM traffic per launch from the committed ncu summary of the current kernel source;
