@@ -230,31 +230,55 @@ k_sssp_relax(const __grid_constant__ Plan plan, const __grid_constant__ SsspArgs
   flush_ssp(insp, 0, ovf, A.ctr);
 }
 
+// A warp's 32 bitmap words (one per lane) are walked in one of two orders. Bit order: every
+// lane walks its own word's set bits, one per step, so a step's 32 loads fall on 32
+// different lines; that takes as many steps as the fullest word has bits. Word order: the
+// warp walks its non-empty words, one per step, lane b looking at bit b of the word, so a
+// step's loads fall on one 128-byte line; that takes one step per non-empty word. Word
+// order wins where the words are dense (the large middle rounds), bit order where they
+// are sparse; the choice is made per warp.
+__device__ __forceinline__ bool word_order(uint32_t nz, uint32_t bits) {
+  return (uint32_t)__popc(nz) <= 2u * __reduce_max_sync(kFull, (uint32_t)__popc(bits));
+}
+
 // Communication phase: apply the dirty outbox slots of p to their owners in q.
+__device__ __forceinline__ void exchange_slot(const SsspSide& S, const SsspSide& Q, uint32_t idx,
+                                              unsigned long long& msgs) {
+  const uint32_t u = S.P.outbox[idx];
+  const uint32_t val = S.omsg[idx];
+  msgs++;
+  if (val < Q.dist[u]) {
+    red_min(&Q.dist[u], val);
+    red_or(&Q.touched[u >> 5], 1u << (u & 31u));
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constant__ SsspArgs A,
                                                             uint32_t words0) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = i < words0 ? 0 : 1;
+  const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
   const SsspSide& S = A.side[p];
   const SsspSide& Q = A.side[1 - p];
   unsigned long long msgs = 0;
+  uint32_t bits = 0;
   if (word * 32 < S.P.nout) {
-    uint32_t bits = S.odirty[word];
-    if (bits) {
-      S.odirty[word] = 0;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const uint32_t idx = word * 32 + b;
-        const uint32_t u = S.P.outbox[idx];
-        const uint32_t val = S.omsg[idx];
-        msgs++;
-        if (val < Q.dist[u]) {
-          red_min(&Q.dist[u], val);
-          red_or(&Q.touched[u >> 5], 1u << (u & 31u));
-        }
-      }
+    bits = S.odirty[word];
+    if (bits) S.odirty[word] = 0;
+  }
+  const uint32_t nz = __ballot_sync(kFull, bits != 0);
+  if (nz && word_order(nz, bits)) {
+    const uint32_t w0 = word - lane_id();
+    for (uint32_t r = nz; r; r &= r - 1) {
+      const int l = __ffs(r) - 1;
+      const uint32_t wb = __shfl_sync(kFull, bits, l);
+      if ((wb >> lane_id()) & 1u) exchange_slot(S, Q, (w0 + l) * 32 + lane_id(), msgs);
+    }
+  } else {
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      exchange_slot(S, Q, word * 32 + b, msgs);
     }
   }
   flush_ssp(0, msgs, false, A.ctr);
@@ -262,8 +286,23 @@ __global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constan
 
 // Filter: touched vertices whose distance dropped below the value they were last relaxed
 // with form the next active set, when that distance is below tau; the others stay touched
-// (pending) and are counted, with their smallest distance. One lane per bitmap word; lanes
-// walk their set bits in step so that appends stay warp-aggregated.
+// (pending) and are counted, with their smallest distance. One lane per bitmap word, the
+// warp's words walked in bit or word order; every step appends warp-aggregated.
+__device__ __forceinline__ bool filter_vertex(const SsspSide& S, uint32_t x, uint32_t tau,
+                                              bool& far, uint32_t& nfar, uint32_t& key) {
+  const uint32_t d = S.dist[x];
+  if (d < S.snap[x]) {
+    if (d < tau) {
+      S.snap[x] = d;  // queued with d
+      return true;
+    }
+    far = true;
+    nfar++;
+    key = max(key, ~d);
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant__ SsspArgs A,
                                                           uint32_t words0, uint32_t words,
                                                           uint32_t tau) {
@@ -276,27 +315,35 @@ __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant_
     bits = S.touched[word];
     if (bits) S.touched[word] = 0;
   }
-  while (__any_sync(kFull, bits != 0)) {
-    bool act = false;
-    uint32_t x = 0;
-    if (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      x = word * 32 + b;
-      const uint32_t d = S.dist[x];
-      if (d < S.snap[x]) {
-        if (d < tau) {
-          S.snap[x] = d;  // queued with d
-          act = true;
-        } else {
-          keep |= 1u << b;
-          nfar++;
-          key = max(key, ~d);
-        }
-      }
+  const uint32_t nz = __ballot_sync(kFull, bits != 0);
+  if (!nz) return;
+  if (word_order(nz, bits)) {
+    const uint32_t w0 = word - lane_id();
+    for (uint32_t r = nz; r; r &= r - 1) {
+      const int l = __ffs(r) - 1;
+      const uint32_t wb = __shfl_sync(kFull, bits, l);
+      const uint32_t x = (w0 + l) * 32 + lane_id();
+      bool far = false, act = false;
+      if ((wb >> lane_id()) & 1u) act = filter_vertex(S, x, tau, far, nfar, key);
+      const uint32_t km = __ballot_sync(kFull, far);
+      if ((int)lane_id() == l) keep = km;
+      warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                           S.nhubq);
     }
-    warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
-                         S.nhubq);
+  } else {
+    while (__any_sync(kFull, bits != 0)) {
+      bool act = false, far = false;
+      uint32_t x = 0;
+      if (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        x = word * 32 + b;
+        act = filter_vertex(S, x, tau, far, nfar, key);
+        if (far) keep |= 1u << b;
+      }
+      warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                           S.nhubq);
+    }
   }
   if (keep) S.touched[word] = keep;
   nfar = warp_sum(nfar);

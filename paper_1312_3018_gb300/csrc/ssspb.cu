@@ -296,34 +296,55 @@ k_sb_relax_dev(const Plan* plan, const __grid_constant__ SbArgs A) {
   sb_relax(sp, A);
 }
 
+// A warp's 32 bitmap words (one per lane) are walked in bit order (every lane its own
+// word's set bits, a step's rows on 32 different lines) or in word order (the warp's
+// non-empty words one per step, lane b on bit b, a step's rows contiguous); word order
+// where the words are dense, bit order where they are sparse, chosen per warp.
+__device__ __forceinline__ bool sb_word_order(uint32_t nz, uint32_t bits) {
+  return (uint32_t)__popc(nz) <= 2u * __reduce_max_sync(kFull, (uint32_t)__popc(bits));
+}
+
 // Communication phase: apply the dirty outbox rows of p to their owners in q.
+__device__ __forceinline__ void sb_exchange_slot(const SbSide& S, const SbSide& Q, uint32_t idx,
+                                                 unsigned long long& msgs, bool& ovf) {
+  const uint32_t u = S.P.outbox[idx];
+  const Row mv = load_row(S.omsg + (size_t)idx * kSbLanes);
+  msgs++;
+  uint32_t fin = 0;  // lanes that carry a message
+  #pragma unroll
+  for (int l = 0; l < kSbLanes; ++l) fin |= (mv.d[l] != kInf ? 1u : 0u) << l;
+  const uint32_t low = relax_row(Q.dist + (size_t)u * kSbLanes, mv.d, fin, 0u, ovf);
+  if (low) sb_red_or(&Q.tbits[u >> 5], 1u << (u & 31u));
+}
+
 __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant__ SbArgs A,
                                                           uint32_t words0) {
   if (sb_skip(A)) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = i < words0 ? 0 : 1;
+  const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
   const SbSide& S = A.side[p];
   const SbSide& Q = A.side[1 - p];
   unsigned long long msgs = 0;
   bool ovf = false;
+  uint32_t bits = 0;
   if (word * 32 < S.P.nout) {
-    uint32_t bits = S.odirty[word];
-    if (bits) {
-      S.odirty[word] = 0;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const uint32_t idx = word * 32 + b;
-        const uint32_t u = S.P.outbox[idx];
-        const Row mv = load_row(S.omsg + (size_t)idx * kSbLanes);
-        msgs++;
-        uint32_t fin = 0;  // lanes that carry a message
-        #pragma unroll
-        for (int l = 0; l < kSbLanes; ++l) fin |= (mv.d[l] != kInf ? 1u : 0u) << l;
-        const uint32_t low = relax_row(Q.dist + (size_t)u * kSbLanes, mv.d, fin, 0u, ovf);
-        if (low) sb_red_or(&Q.tbits[u >> 5], 1u << (u & 31u));
-      }
+    bits = S.odirty[word];
+    if (bits) S.odirty[word] = 0;
+  }
+  const uint32_t nz = __ballot_sync(kFull, bits != 0);
+  if (nz && sb_word_order(nz, bits)) {
+    const uint32_t w0 = word - lane_id();
+    for (uint32_t r = nz; r; r &= r - 1) {
+      const int l = __ffs(r) - 1;
+      const uint32_t wb = __shfl_sync(kFull, bits, l);
+      if ((wb >> lane_id()) & 1u) sb_exchange_slot(S, Q, (w0 + l) * 32 + lane_id(), msgs, ovf);
+    }
+  } else {
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      sb_exchange_slot(S, Q, word * 32 + b, msgs, ovf);
     }
   }
   sb_flush(0, msgs, ovf, A.ctr);
@@ -331,8 +352,30 @@ __global__ void __launch_bounds__(kThreads) k_sb_exchange(const __grid_constant_
 
 // Filter: a touched vertex is queued for the lanes whose distance is below their queued
 // value (which then becomes that distance) and below tau; lanes at or above tau keep the
-// vertex touched and are counted with their smallest distance. One lane per bitmap word;
-// lanes walk their set bits in step so that appends stay warp-aggregated.
+// vertex touched and are counted with their smallest distance. One lane per bitmap word,
+// the warp's words walked in bit or word order; every step appends warp-aggregated.
+__device__ __forceinline__ bool sb_filter_vertex(const SbSide& S, uint32_t x, uint32_t tau,
+                                                 bool& wait, uint32_t& nfar, uint32_t& key) {
+  const Row d = load_row(S.dist + (size_t)x * kSbLanes);
+  uint32_t* sp = S.snap + (size_t)x * kSbLanes;
+  const Row q = load_row(sp);
+  uint32_t am = 0;
+  #pragma unroll
+  for (int l = 0; l < kSbLanes; ++l) {
+    if (!(d.d[l] < q.d[l])) continue;
+    if (d.d[l] < tau) {
+      sp[l] = d.d[l];
+      am |= 1u << l;
+    } else {
+      wait = true;
+      nfar++;
+      key = max(key, ~d.d[l]);
+    }
+  }
+  if (am) S.amask[x] = am;
+  return am != 0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ SbArgs A,
                                                         uint32_t words0, uint32_t words,
                                                         uint32_t tau) {
@@ -347,38 +390,35 @@ __global__ void __launch_bounds__(kThreads) k_sb_filter(const __grid_constant__ 
     bits = S.tbits[word];
     if (bits) S.tbits[word] = 0;
   }
-  while (__any_sync(kFull, bits != 0)) {
-    bool act = false;
-    uint32_t x = 0;
-    if (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      x = word * 32 + b;
-      const Row d = load_row(S.dist + (size_t)x * kSbLanes);
-      uint32_t* sp = S.snap + (size_t)x * kSbLanes;
-      const Row q = load_row(sp);
-      uint32_t am = 0;
-      bool wait = false;
-      #pragma unroll
-      for (int l = 0; l < kSbLanes; ++l) {
-        if (!(d.d[l] < q.d[l])) continue;
-        if (d.d[l] < tau) {
-          sp[l] = d.d[l];
-          am |= 1u << l;
-        } else {
-          wait = true;
-          nfar++;
-          key = max(key, ~d.d[l]);
-        }
-      }
-      if (wait) keep |= 1u << b;
-      if (am) {
-        S.amask[x] = am;
-        act = true;
-      }
+  const uint32_t nz = __ballot_sync(kFull, bits != 0);
+  if (!nz) return;
+  if (sb_word_order(nz, bits)) {
+    const uint32_t w0 = word - lane_id();
+    for (uint32_t r = nz; r; r &= r - 1) {
+      const int l = __ffs(r) - 1;
+      const uint32_t wb = __shfl_sync(kFull, bits, l);
+      const uint32_t x = (w0 + l) * 32 + lane_id();
+      bool wait = false, act = false;
+      if ((wb >> lane_id()) & 1u) act = sb_filter_vertex(S, x, tau, wait, nfar, key);
+      const uint32_t km = __ballot_sync(kFull, wait);
+      if ((int)lane_id() == l) keep = km;
+      warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                           S.nhubq);
     }
-    warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
-                         S.nhubq);
+  } else {
+    while (__any_sync(kFull, bits != 0)) {
+      bool act = false, wait = false;
+      uint32_t x = 0;
+      if (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        x = word * 32 + b;
+        act = sb_filter_vertex(S, x, tau, wait, nfar, key);
+        if (wait) keep |= 1u << b;
+      }
+      warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
+                           S.nhubq);
+    }
   }
   if (keep) S.tbits[word] = keep;
   nfar = warp_sum(nfar);
