@@ -76,7 +76,8 @@ def parse():
                     help="skip the query-server (continuous batching) measurement")
     ap.add_argument("--serve-scale", type=int, default=23)
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the batched BFS and many-graph PageRank measurements")
+                    help="skip the batched BFS / SSSP, many-graph PageRank, betweenness and "
+                         "connected-components measurements")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the hybrid (host + GPU) PageRank measurement")
