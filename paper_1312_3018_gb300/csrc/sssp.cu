@@ -38,13 +38,18 @@ namespace gg {
 struct SsspCounters {
   uint32_t tail[2][kNBucket];  // next-round work: [0] hub chunks, [1..3] vertices
   uint32_t overflow;
-  uint32_t far;                // improved vertices left pending at or above the threshold
-  uint32_t far_key;            // max of ~dist over them (so zero-initialised counters work)
+  uint32_t clamped;                   // a final distance equals the saturation value
   unsigned long long inspected;
   unsigned long long messages;
   unsigned long long reached_degree;  // filled by the final reduction
-  uint32_t clamped;                   // a final distance equals the saturation value
+  // Near-far, kept across rounds and cleared at a threshold move, after which the rescan
+  // of the waiting set sets them exactly: far is nonzero when a vertex joined the waiting
+  // set since (so zero only when the set is empty), far_key the max of ~dist over them.
+  uint32_t far;
+  uint32_t far_key;
 };
+// Bytes a round clears: everything but the near-far fields.
+constexpr size_t kRoundCounterBytes = offsetof(SsspCounters, far);
 
 // Host side of sssp_hybrid: partition 0's CSR, weights and ids (host copies made once per
 // partition), its search state and outbox minima, and pinned message arrays.
@@ -61,7 +66,7 @@ struct HsspHost {
 };
 
 struct SsspWs {
-  DevBuf dist[2], snap[2], touched[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
+  DevBuf dist[2], snap[2], touched[2], farb[2], queue[2][2], hubq[2][2], omsg[2], odirty[2];
   size_t words[2] = {0, 0}, owords[2] = {0, 0};
   HsspHost* hyb = nullptr;
 };
@@ -83,9 +88,9 @@ void free_sssp(graph* g) {
   SsspWs* w = g->sssp;
   free_hsssp(g, w);
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->touched[p], &w->queue[p][0],
-                     &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1], &w->omsg[p],
-                     &w->odirty[p]};
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],    &w->touched[p], &w->farb[p],
+                     &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0], &w->hubq[p][1],
+                     &w->omsg[p],     &w->odirty[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
   delete w;
@@ -99,6 +104,7 @@ struct SsspSide {
   uint32_t* dist;
   uint32_t* snap;     // distance each vertex was last relaxed with (INF: never)
   uint32_t* touched;  // vertices lowered this round
+  uint32_t* farb;     // near-far waiting set: improved vertices at or above the threshold
   uint32_t* nqueue;   // next active queue (bucketed)
   uint32_t* nhubq;    // next hub chunk list
   uint32_t* omsg;     // outbox minima
@@ -285,8 +291,12 @@ __global__ void __launch_bounds__(kThreads) k_sssp_exchange(const __grid_constan
 }
 
 // Filter: touched vertices whose distance dropped below the value they were last relaxed
-// with form the next active set, when that distance is below tau; the others stay touched
-// (pending) and are counted, with their smallest distance. One lane per bitmap word, the
+// with form the next active set, when that distance is below tau; the others join the
+// waiting set (the far bitmap) and are counted, with their smallest distance. After a
+// threshold move the same kernel rescans the waiting set instead (from_far): its vertices
+// below the new tau are queued, those still above stay, and those queued since they
+// joined (distance equal to the value they were queued with) leave it. So a round's
+// filter reads only the vertices lowered in that round. One lane per bitmap word, the
 // warp's words walked in bit or word order; every step appends warp-aggregated.
 __device__ __forceinline__ bool filter_vertex(const SsspSide& S, uint32_t x, uint32_t tau,
                                               bool& far, uint32_t& nfar, uint32_t& key) {
@@ -305,15 +315,16 @@ __device__ __forceinline__ bool filter_vertex(const SsspSide& S, uint32_t x, uin
 
 __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant__ SsspArgs A,
                                                           uint32_t words0, uint32_t words,
-                                                          uint32_t tau) {
+                                                          uint32_t tau, int from_far) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = i < words0 ? 0 : 1;  // warps never straddle: words0 is a multiple of 32
   const uint32_t word = p == 0 ? i : i - words0;
   const SsspSide& S = A.side[p];
+  uint32_t* src = from_far ? S.farb : S.touched;
   uint32_t bits = 0, keep = 0, nfar = 0, key = 0;
   if (i < words) {
-    bits = S.touched[word];
-    if (bits) S.touched[word] = 0;
+    bits = src[word];
+    if (bits) src[word] = 0;
   }
   const uint32_t nz = __ballot_sync(kFull, bits != 0);
   if (!nz) return;
@@ -345,11 +356,11 @@ __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant_
                            S.nhubq);
     }
   }
-  if (keep) S.touched[word] = keep;
+  if (keep) S.farb[word] |= keep;  // the word's only writer in this kernel
   nfar = warp_sum(nfar);
   key = __reduce_max_sync(kFull, key);
   if (lane_id() == 0 && nfar) {
-    atomicAdd(&A.ctr->far, nfar);
+    if (!*(volatile uint32_t*)&A.ctr->far) A.ctr->far = 1u;  // every writer stores 1
     atomicMax(&A.ctr->far_key, key);
   }
 }
@@ -476,6 +487,7 @@ graph_status alloc_ws_into(graph* g, SsspWs* w) {
     GG_TRY(dalloc(g, w->dist[p], 4ull * P.nv));
     GG_TRY(dalloc(g, w->snap[p], 4ull * P.nv));
     GG_TRY(dalloc(g, w->touched[p], 4 * w->words[p]));
+    GG_TRY(dalloc(g, w->farb[p], 4 * w->words[p]));
     GG_TRY(dalloc(g, w->queue[p][0], 4ull * P.nv));
     GG_TRY(dalloc(g, w->queue[p][1], 4ull * P.nv));
     GG_TRY(dalloc(g, w->hubq[p][0], 4ull * P.nchunk));
@@ -488,9 +500,9 @@ graph_status alloc_ws_into(graph* g, SsspWs* w) {
 
 void free_ws_buffers(graph* g, SsspWs* w) {
   for (int p = 0; p < 2; ++p) {
-    DevBuf* all[] = {&w->dist[p],     &w->snap[p],     &w->touched[p], &w->queue[p][0],
-                     &w->queue[p][1], &w->hubq[p][0],  &w->hubq[p][1], &w->omsg[p],
-                     &w->odirty[p]};
+    DevBuf* all[] = {&w->dist[p],     &w->snap[p],    &w->touched[p], &w->farb[p],
+                     &w->queue[p][0], &w->queue[p][1], &w->hubq[p][0], &w->hubq[p][1],
+                     &w->omsg[p],     &w->odirty[p]};
     for (DevBuf* b : all) dfree(g, *b);
   }
 }
@@ -523,6 +535,7 @@ SsspArgs make_args(graph* g, SsspWs* w, SsspCounters* ctr, int cur) {
     S.dist = (uint32_t*)w->dist[p].p;
     S.snap = (uint32_t*)w->snap[p].p;
     S.touched = (uint32_t*)w->touched[p].p;
+    S.farb = (uint32_t*)w->farb[p].p;
     S.nqueue = (uint32_t*)w->queue[p][1 - cur].p;
     S.nhubq = (uint32_t*)w->hubq[p][1 - cur].p;
     S.omsg = (uint32_t*)w->omsg[p].p;
@@ -540,6 +553,7 @@ graph_status launch_start(graph* g, SsspWs* w, SsspCounters* ctr, uint32_t sourc
     GG_CUDA(cudaMemsetAsync(w->dist[p].p, 0xFF, 4ull * P.nv, st));
     GG_CUDA(cudaMemsetAsync(w->snap[p].p, 0xFF, 4ull * P.nv, st));
     GG_CUDA(cudaMemsetAsync(w->touched[p].p, 0, 4 * w->words[p], st));
+    GG_CUDA(cudaMemsetAsync(w->farb[p].p, 0, 4 * w->words[p], st));
     GG_CUDA(cudaMemsetAsync(w->omsg[p].p, 0xFF, 4ull * P.nout, st));
     GG_CUDA(cudaMemsetAsync(w->odirty[p].p, 0, 4 * w->owords[p], st));
   }
@@ -563,7 +577,7 @@ uint64_t active_count(const SsspCounters& c) {
 graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCounters& c,
                           int cur, cudaStream_t st, PhaseTimer* timer, int64_t* launches,
                           bool cc = false, uint32_t tau = kInf) {
-  GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
+  GG_CUDA(cudaMemsetAsync(ctr, 0, kRoundCounterBytes, st));
   const SsspArgs A = make_args(g, w, ctr, cur);
   Plan pl;
   memset(&pl, 0, sizeof(pl));
@@ -589,7 +603,7 @@ graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCoun
   if (owords) k_sssp_exchange<<<grid_for(owords, kThreads), kThreads, 0, st>>>(A, owords0);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(1);
-  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
+  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau, 0);
   GG_CUDA(cudaGetLastError());
   if (timer) timer->mark(0);
   *launches += 1 + (owords ? 1 : 0) + (pl.nblocks ? 1 : 0);
@@ -597,8 +611,8 @@ graph_status launch_round(graph* g, SsspWs* w, SsspCounters* ctr, const SsspCoun
 }
 
 // Near-far: the active set is empty but improved vertices wait at or above the threshold.
-// The next threshold is their smallest distance + delta; the filter alone then queues
-// those below it for the round that reads queues `cur`.
+// The next threshold is their smallest distance + delta; the filter alone then rescans
+// the waiting set and queues those below it for the round that reads queues `cur`.
 uint32_t next_threshold(const SsspCounters& c, uint32_t delta) {
   const uint64_t t = (uint64_t)(~c.far_key) + delta;
   return t >= kInf ? kInf : (uint32_t)t;
@@ -609,7 +623,7 @@ graph_status launch_refilter(graph* g, SsspWs* w, SsspCounters* ctr, int cur, ui
   GG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(SsspCounters), st));
   const SsspArgs A = make_args(g, w, ctr, 1 - cur);  // appends into queues `cur`
   const uint32_t words0 = (uint32_t)w->words[0], words = words0 + (uint32_t)w->words[1];
-  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau);
+  k_sssp_filter<<<grid_for(words, kThreads), kThreads, 0, st>>>(A, words0, words, tau, 1);
   GG_CUDA(cudaGetLastError());
   *launches += 1;
   return GRAPH_OK;
@@ -1191,7 +1205,7 @@ extern "C" graph_status sssp_hybrid(graph_t* g, uint32_t source, uint32_t* dist,
     // Filter: partition 1 on the device (its words only), partition 0 on the host.
     {
       SsspArgs F = A;
-      k_sssp_filter<<<grid_for(words1, kThreads), kThreads, 0, st>>>(F, 0u, words1, kInf);
+      k_sssp_filter<<<grid_for(words1, kThreads), kThreads, 0, st>>>(F, 0u, words1, kInf, 0);
       launches++;
     }
     GG_CUDA(cudaGetLastError());
