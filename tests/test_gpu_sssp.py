@@ -144,3 +144,38 @@ def test_sssp_near_far_multi_chunk_hub_and_path(gpu):
     d, st = gpu.sssp(H, n - 1, out="host", delta=100)
     assert np.array_equal(d, np.concatenate([np.cumsum(w[::-1])[::-1], [0]]).astype(np.uint32))
     H.free()
+
+
+@pytest.mark.parametrize("delta", [0, 100])
+def test_sssp_long_path(gpu, delta):
+    """A 2,500-vertex path: 2,499 rounds of one vertex each, with threshold moves in near-far
+    order; distances are the prefix sums."""
+    n = 2500
+    w = np.random.default_rng(4).integers(1, 256, n - 1)
+    g = synth.from_edges(n, [(i, i + 1) for i in range(n - 1)], w=w)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(n, 0.5, 9))
+    d, st = gpu.sssp(H, 0, out="host", delta=delta)
+    assert np.array_equal(d, np.concatenate([[0], np.cumsum(w)]).astype(np.uint32))
+    assert st["supersteps"] >= n - 1
+    H.free()
+
+
+@pytest.mark.parametrize("timing", [False, True])
+@pytest.mark.parametrize("delta", [0, 2])
+def test_sssp_cap_boundary(gpu, timing, delta):
+    """The number of rounds a search needs is enough as a cap and one fewer is not, with and
+    without phase timing."""
+    g = synth.from_edges(12, [(i, i + 1) for i in range(11)], w=[1] * 11)
+    H = gpu.graph_load_csr(g.offsets, g.cols, g.weights)
+    gpu.graph_partition(H, "explicit", assignment=synth.random_assignment(g.n, 0.5, 5))
+    for s in (0, 3, 6):
+        ref = np.abs(np.arange(12) - s).astype(np.uint32)
+        d, st = gpu.sssp(H, s, out="host", delta=delta, timing=timing)
+        assert np.array_equal(d, ref)
+        r = st["supersteps"]
+        d, _ = gpu.sssp(H, s, out="host", delta=delta, timing=timing, max_supersteps=r)
+        assert np.array_equal(d, ref)
+        with pytest.raises(gpu.GraphError, match="cap"):
+            gpu.sssp(H, s, delta=delta, timing=timing, max_supersteps=r - 1)
+    H.free()
