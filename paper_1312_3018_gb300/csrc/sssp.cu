@@ -18,9 +18,9 @@
 //    while it waits in the current round is relaxed with its newest distance and not
 //    re-queued, the paper's same-round activation.
 //  - optional near-far order (delta > 0): only improved vertices with distance below a
-//    threshold are activated; the others keep their touched mark and wait. When the
-//    active set runs dry the threshold moves to the smallest waiting distance + delta and
-//    the filter runs again. Every improved vertex is still relaxed with its final
+//    threshold are activated; the others wait in a far bitmap. When the active set runs
+//    dry the threshold moves to the smallest waiting distance + delta and the filter
+//    rescans the far bitmap. Every improved vertex is still relaxed with its final
 //    distance, so the distances are the same; fewer relaxations are wasted on distances
 //    that later improve.
 // Distances are uint32; a relaxation saturates at 0xFFFFFFFE and flags an overflow.
