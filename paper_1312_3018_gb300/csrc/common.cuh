@@ -163,6 +163,38 @@ __device__ __forceinline__ void warp_append_bucketed(bool has, uint32_t item, in
   }
 }
 
+// warp_append_bucketed for U items per lane (has[u], item[u], bucket[u]) at once: one
+// atomic per (warp, bucket) for all of them. All 32 lanes must call it.
+template <int U>
+__device__ __forceinline__ void warp_append_bucketed_n(const bool* has, const uint32_t* item,
+                                                       const int* bucket, uint32_t* tails,
+                                                       uint32_t* queue, const PartView& P,
+                                                       uint32_t* hubq) {
+  #pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (has[u] && bucket[u] == 0) append_hub_chunks(P, item[u], &tails[0], hubq);
+  #pragma unroll
+  for (int b = 1; b < kNBucket; ++b) {
+    unsigned m[U];
+    uint32_t tot = 0;
+    #pragma unroll
+    for (int u = 0; u < U; ++u) {
+      m[u] = __ballot_sync(kFull, has[u] && bucket[u] == b);
+      tot += (uint32_t)__popc(m[u]);
+    }
+    if (tot) {
+      uint32_t base = 0;
+      if (lane_id() == 0) base = atomicAdd(&tails[b], tot);
+      uint32_t at = P.bstart[b] + __shfl_sync(kFull, base, 0);
+      #pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (has[u] && bucket[u] == b) queue[at + __popc(m[u] & lanemask_lt())] = item[u];
+        at += (uint32_t)__popc(m[u]);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void warp_append(bool has, uint32_t item, uint32_t* tail,
                                             uint32_t* list) {
   const unsigned m = __ballot_sync(kFull, has);

@@ -329,17 +329,44 @@ __global__ void __launch_bounds__(kThreads) k_sssp_filter(const __grid_constant_
   const uint32_t nz = __ballot_sync(kFull, bits != 0);
   if (!nz) return;
   if (word_order(nz, bits)) {
+    // kU non-empty words per step: their distance and snapshot loads are in flight
+    // together, and one append (one atomic per bucket) serves all of them.
+    constexpr int kU = 4;
     const uint32_t w0 = word - lane_id();
-    for (uint32_t r = nz; r; r &= r - 1) {
-      const int l = __ffs(r) - 1;
-      const uint32_t wb = __shfl_sync(kFull, bits, l);
-      const uint32_t x = (w0 + l) * 32 + lane_id();
-      bool far = false, act = false;
-      if ((wb >> lane_id()) & 1u) act = filter_vertex(S, x, tau, far, nfar, key);
-      const uint32_t km = __ballot_sync(kFull, far);
-      if ((int)lane_id() == l) keep = km;
-      warp_append_bucketed(act, x, act ? bucket_of(S.P, x) : 0, A.ctr->tail[p], S.nqueue, S.P,
-                           S.nhubq);
+    for (uint32_t r = nz; r;) {
+      uint32_t x[kU], d[kU], q[kU];
+      int lw[kU], bk[kU];
+      bool sel[kU], act[kU];
+      #pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        lw[u] = r ? __ffs(r) - 1 : -1;  // warp-uniform
+        r &= r - 1;
+        const int l = lw[u] < 0 ? 0 : lw[u];
+        const uint32_t wb = __shfl_sync(kFull, bits, l);
+        x[u] = (w0 + l) * 32 + lane_id();
+        sel[u] = lw[u] >= 0 && ((wb >> lane_id()) & 1u);
+        d[u] = sel[u] ? S.dist[x[u]] : 0u;
+        q[u] = sel[u] ? S.snap[x[u]] : 0u;
+      }
+      #pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        bool far = false;
+        act[u] = false;
+        if (sel[u] && d[u] < q[u]) {
+          if (d[u] < tau) {
+            S.snap[x[u]] = d[u];  // queued with d
+            act[u] = true;
+          } else {
+            far = true;
+            nfar++;
+            key = max(key, ~d[u]);
+          }
+        }
+        const uint32_t km = __ballot_sync(kFull, far);
+        if ((int)lane_id() == lw[u]) keep = km;
+        bk[u] = act[u] ? bucket_of(S.P, x[u]) : 0;
+      }
+      warp_append_bucketed_n<kU>(act, x, bk, A.ctr->tail[p], S.nqueue, S.P, S.nhubq);
     }
   } else {
     while (__any_sync(kFull, bits != 0)) {
